@@ -1,0 +1,204 @@
+/*
+ * gs.h -- C ABI of libgs, a GB300 (sm_103a) engine for the data-parallel hot path
+ * of single-event-upset (SEU) fault injection into 3D Gaussian splatting models
+ * (arXiv 2606.21791, "Single-Event Upsets in 3D Gaussian Splatting Rendering").
+ *
+ * Every call returns a gs_status and never aborts; gs_last_error() gives a
+ * thread-local message for the last failure.  Unless stated otherwise a pointer
+ * argument named dev_* is CUDA device memory owned by the caller and must stay
+ * valid until the work queued on `stream` completes; host_* is host memory read
+ * before the call returns.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream).  Calls on one scene are stream-ordered: issue them on one stream, or
+ * synchronise between streams.  A scene is not thread-safe.
+ *
+ * Parameter layout (Sec. 3 "Parameter layout"): a primitive stores mean (words
+ * 0-2), logarithmic scale (3-5), quaternion w,x,y,z (6-9), opacity logit (10),
+ * SH DC colour (11-13) and higher-order SH coefficients coefficient-major,
+ * 3 channels each (14..): 14 words at SH degree 0, 59 at degree 3.  Scenes are
+ * structure-of-arrays planes [word][primitive] in the storage format.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,      /* invalid argument (null pointer, size, format, site out of range) */
+    GS_ERR_OOM = 2,      /* device allocation failed */
+    GS_ERR_CUDA = 3,     /* a CUDA call failed; the message names it */
+    GS_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    GS_ERR_BUSY = 5,     /* admission refused (serving budget) or queue full */
+    GS_ERR_STATE = 6,    /* call out of order (e.g. no views set, unknown ticket) */
+    GS_ERR_CAPACITY = 7  /* an internal buffer was too small; the call can be retried */
+} gs_status;
+
+/* Storage format of the parameter words (Sec. 3 "Single-bit upset model"):
+ * fp32 (sign 31, exponent 23-30, mantissa 0-22), fp16, bf16.  Math is fp32. */
+typedef enum { GS_FP32 = 0, GS_FP16 = 1, GS_BF16 = 2 } gs_format;
+
+/* Guard box modes (Algorithm 1): FIELD = one [lo, hi] per word index over all
+ * primitives (the Algorithm 1 precompute); PRIM = per-primitive boxes. */
+typedef enum { GS_GUARD_OFF = -1, GS_GUARD_FIELD = 0, GS_GUARD_PRIM = 1 } gs_guard_mode;
+
+/* One single-bit upset site (Sec. 3: a fault site is (field, primitive,
+ * component, bit)); `word` is the field/component word index, `bit` counts from
+ * the least significant bit of the stored word (< 32 for fp32, < 16 otherwise). */
+typedef struct {
+    uint32_t prim;
+    uint16_t word;
+    uint8_t bit;
+    uint8_t pad;
+} gs_flip;
+
+/* Pinhole camera: camera-space p = R * world + t (R row-major; x right, y down,
+ * z forward); pixel (i, j) has centre (i + 0.5, j + 0.5); a point projects to
+ * (fx x/z + cx, fy y/z + cy).  Primitives with z outside (znear, zfar) are culled. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear, zfar;
+} gs_camera;
+
+/* Per (variant, view) comparison against the clean frame (Definitions 1 and 2,
+ * Sec. 3 "Metrics and severity"): images clamped to [0,1] (NaN counts as 0);
+ * sse = sum of squared channel differences; maxabs = peak |difference|;
+ * footprint = pixels whose max channel |difference| exceeds 1/255; nonfinite =
+ * pixels of the corrupted render with a non-finite channel; clamps = guard
+ * clamps applied to the variant (0 with the guard off). */
+typedef struct {
+    double sse;
+    float maxabs;
+    uint32_t footprint;
+    uint32_t nonfinite;
+    uint32_t clamps;
+} gs_result;
+
+/* One preprocessed primitive (debug/stage entry points): projected mean,
+ * conic (inverse 2D covariance [[ca, cb], [cb, cc]]), colour, sigmoid opacity,
+ * camera depth, half-open tile rect, pixel radius, visible flag. */
+typedef struct {
+    float mx, my, ca, cb, cc, r, g, b, opac, depth;
+    int32_t x0, y0, x1, y1, radius, visible;
+} gs_record;
+
+typedef struct gs_scene gs_scene;
+
+GS_API const char* gs_last_error(void);
+GS_API const char* gs_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Scenes.
+ * gs_load_scene copies `n` primitives of `nwords(sh_degree)` storage words,
+ * planes [word][prim] (uint32 words for fp32, uint16 for fp16/bf16), from host
+ * or device memory (`src_on_device`) into a library-owned device scene, and runs
+ * the Algorithm 1 precompute (per-word min/max box).  sh_degree 0..3.
+ * ------------------------------------------------------------------------- */
+GS_API gs_status gs_load_scene(const void* planes, int src_on_device, uint64_t n, int sh_degree, gs_format fmt,
+                        gs_scene** out);
+GS_API gs_status gs_free_scene(gs_scene* scene);
+GS_API gs_status gs_scene_info(const gs_scene* scene, uint64_t* n, int* sh_degree, int* fmt, int* nwords);
+/* Device pointer to the scene's resident planes (library-owned; valid until free). */
+GS_API gs_status gs_scene_planes(gs_scene* scene, void** dev_planes);
+/* Copy the planes back into `dst` (host or device per `dst_on_device`). */
+GS_API gs_status gs_read_planes(gs_scene* scene, void* dst, int dst_on_device, void* stream);
+
+/* Read and clear the scene's sticky device error flags (bit 0: a flip site was
+ * out of range and skipped).  Synchronises the device. */
+GS_API gs_status gs_scene_errors(gs_scene* scene, uint32_t* host_flags);
+
+/* ---------------------------------------------------------------------------
+ * (a) Injection (Sec. 3 "Single-bit upset model"): XOR one bit of each listed
+ * stored word, in place, persistently (the resident model keeps the upsets, as
+ * in an upset storm).  Duplicate sites cancel pairwise, as sequential XOR does.
+ * ------------------------------------------------------------------------- */
+GS_API gs_status gs_apply_flips(gs_scene* scene, const gs_flip* dev_flips, int64_t count, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * (f) Support guard (Algorithm 1; Theorems 1-2).  For every primitive and every
+ * word w with bit w of `word_mask` set, a stored value that is non-finite or
+ * outside [lo, hi] is replaced by the nearer endpoint's storage word (NaN goes
+ * to lo) and counted; the count is ADDED to *dev_clamps (uint64, caller-owned,
+ * may be NULL).  Writes happen only where a clamp fires.
+ * gs_field_box reads the FIELD box (storage words widened to uint32).
+ * gs_set_prim_box installs per-primitive boxes: planes [nbox_words][n] of
+ * storage words (nbox_words <= nwords), host or device; PRIM mode may only
+ * guard words < nbox_words.
+ * ------------------------------------------------------------------------- */
+GS_API gs_status gs_field_box(gs_scene* scene, uint32_t* host_lo, uint32_t* host_hi);
+GS_API gs_status gs_set_prim_box(gs_scene* scene, const void* lo, const void* hi, int src_on_device, int nbox_words);
+GS_API gs_status gs_guard(gs_scene* scene, int mode, uint64_t word_mask, uint64_t* dev_clamps, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * (b)-(d) Forward render of the scene as it is now (3DGS forward pass: EWA
+ * projection, tile binning with a radix sort of (tile, depth) keys, front-to-
+ * back blending over white with the 1/255 alpha and 1e-4 transmittance
+ * cutoffs).  K views, each written as H*W*3 float32 (row-major, RGB) into
+ * dev_rgb at offset sum_{k'<k} H_k' W_k' 3.  tile 16x16.
+ * ------------------------------------------------------------------------- */
+GS_API gs_status gs_render(gs_scene* scene, const gs_camera* host_cams, int K, float* dev_rgb, void* stream);
+
+/* (e) Comparison of K image pairs (layout as gs_render), one gs_result each
+ * (clamps = 0).  dev_out: K records. */
+GS_API gs_status gs_compare(const float* dev_a, const float* dev_b, int H, int W, int K, gs_result* dev_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Injection campaign (Sec. 3 "Parallel injection engine").
+ * gs_set_views renders the clean frame of each view and keeps its state
+ * resident (preprocessed records, sorted tile lists, clean image); the scene
+ * must be clean (no persistent upsets) while a campaign runs.
+ * gs_inject_and_render evaluates B variants: variant b is the clean scene with
+ * flips [b*fpv, (b+1)*fpv) XOR-ed in (fpv = flips_per_variant), then guarded
+ * when guard_mode >= 0, rendered in every view and compared with the clean
+ * frame; dev_out gets B*K records [b][k].  Single-flip variants run on the
+ * batched dirty-tile engine (only tiles the flipped primitive covers before or
+ * after the upset are re-blended; bit-identical to a full re-render);
+ * multi-flip variants are re-rendered in full.  The scene is left unchanged.
+ * gs_inject_and_render_full is the plain loop: one variant at a time, in place,
+ * full preprocess + sort + blend + compare per view, then restore.
+ * ------------------------------------------------------------------------- */
+GS_API gs_status gs_set_views(gs_scene* scene, const gs_camera* host_cams, int K, void* stream);
+GS_API gs_status gs_clean_image(gs_scene* scene, int k, float* dev_rgb, void* stream);
+GS_API gs_status gs_inject_and_render(gs_scene* scene, const gs_flip* dev_flips, int B, int flips_per_variant,
+                               int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
+GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_flips, int B, int flips_per_variant,
+                                    int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
+/* Enable (default) or disable CUDA-graph replay of the batched dirty-tile step. */
+GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points (for stage-isolated checks).
+ * gs_preprocess: records of every primitive for one camera (dev_out: n).
+ * gs_bin_tiles: per-tile lists front to back.  Input per primitive: depth
+ * (float, > 0) and tile rect x0,y0,x1,y1 (int32, half open, already clipped to
+ * the grid; empty = not binned).  Output: dev_offsets [tiles_x*tiles_y + 1]
+ * exclusive prefix of list lengths and dev_ids [*host_total] primitive indices,
+ * sorted by (tile, depth, primitive) via a stable LSD radix sort.  If the total
+ * exceeds ids_cap, *host_total is set and GS_ERR_CAPACITY returned.  Blocks
+ * until done.
+ * gs_blend_lists: blend given records and lists into H*W*3 float32.
+ * ------------------------------------------------------------------------- */
+GS_API gs_status gs_preprocess(gs_scene* scene, const gs_camera* host_cam, gs_record* dev_out, void* stream);
+GS_API gs_status gs_bin_tiles(const float* dev_depth, const int32_t* dev_rects, uint64_t n, int tiles_x, int tiles_y,
+                       uint32_t* dev_offsets, uint32_t* dev_ids, uint64_t ids_cap, uint64_t* host_total,
+                       void* stream);
+GS_API gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uint32_t* dev_offsets, const uint32_t* dev_ids,
+                         int W, int H, float* dev_rgb, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,585 @@
+// C ABI of libgs: scene lifetime, the full render pipeline, the batched
+// dirty-tile injection campaign (captured in CUDA graphs), the plain
+// one-variant-at-a-time loop, and stage entry points.  All device work is done
+// by the kernels in k_*.cu; this file only orchestrates.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+// implemented in the kernel translation units
+gs_status launch_apply_flips(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int64_t count,
+                             unsigned int* err, cudaStream_t st);
+gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects, uint32_t* keys,
+                            uint32_t* vals, gs_record* dbg, cudaStream_t st);
+gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,
+                             int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects, DirtyDesc* desc,
+                             uint32_t* item_off, CmpAcc* acc, unsigned int* queue, cudaStream_t st);
+gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, uint32_t** ids_out, cudaStream_t st);
+gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* offsets, const unsigned long long* total,
+                                   cudaStream_t st);
+gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
+gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
+                             CmpAcc* acc, unsigned int* queue, cudaStream_t st);
+size_t view_ptrs_size();
+void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const float* clean,
+                    int W, int H);
+gs_status launch_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges, cudaStream_t st);
+uint32_t key_to_bits(uint32_t key, int fmt);
+int dirty_grid();
+
+static thread_local std::string g_last_error;
+
+gs_status set_error(gs_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+gs_status cuda_error(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return set_error(GS_ERR_OOM, m);
+    return set_error(GS_ERR_CUDA, m);
+}
+
+namespace {
+
+__global__ void k_move_clamps(unsigned long long* ctr, CmpAcc* acc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        acc->clamps = (unsigned int)(*ctr < 0xffffffffull ? *ctr : 0xffffffffull);
+        *ctr = 0ull;
+    }
+}
+
+gs_status dmalloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(GS_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return GS_OK;
+}
+
+bool valid_camera(const gs_camera& c) {
+    return c.width > 0 && c.height > 0 && c.width <= 65535 * kTile && c.height <= 65535 * kTile && c.fx > 0 &&
+           c.fy > 0 && std::isfinite(c.fx) && std::isfinite(c.fy);
+}
+
+// Full render pipeline of one view on scratch `w`: preprocess, depth sort,
+// pair emission, tile sort, ranges.  Leaves records in w.recs, lists in *ids.
+gs_status render_lists(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, cudaStream_t st) {
+    GS_TRY(launch_preprocess(s, cam, w.recs, w.rects, w.dkey[0], w.dval[0], nullptr, st));
+    return build_tile_lists(w, s->n, cam.tiles_x, cam.tiles_y, ids, st);
+}
+
+// Like render_lists but grows the pair capacity until the lists fit (host sync).
+gs_status render_lists_sized(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, uint64_t* npairs,
+                             cudaStream_t st) {
+    int ntiles = cam.tiles_x * cam.tiles_y;
+    uint64_t cap = std::max<uint64_t>(w.cap_pairs, std::max<uint64_t>(s->n * 2, 1024));
+    for (int attempt = 0; attempt < 4; attempt++) {
+        GS_TRY(alloc_render_work(w, s->n, cap, ntiles));
+        GS_TRY(render_lists(s, w, cam, ids, st));
+        GS_CUDA(cudaMemcpyAsync(w.host_total, w.total, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+        if (!w.host_total[1]) {
+            *npairs = w.host_total[0];
+            return GS_OK;
+        }
+        uint64_t need = w.host_total[2];
+        if (need >= 0xffffffffull) return set_error(GS_ERR_CAPACITY, "tile pair count exceeds 2^32");
+        cap = need + need / 4 + 1024;
+    }
+    return set_error(GS_ERR_CAPACITY, "could not size the tile pair buffers");
+}
+
+void destroy_graphs(gs_scene* s) {
+    for (auto& g : s->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    s->graphs.clear();
+}
+
+void free_views(gs_scene* s) {
+    destroy_graphs(s);
+    for (auto& v : s->views) {
+        cudaFree(v.recs);
+        cudaFree(v.rects);
+        cudaFree(v.ids);
+        cudaFree(v.ranges);
+        cudaFree(v.clean);
+    }
+    s->views.clear();
+    s->K = 0;
+    cudaFree(s->dev_cams);
+    cudaFree(s->dev_views);
+    cudaFree(s->dev_clean_rects);
+    s->dev_cams = nullptr;
+    s->dev_views = nullptr;
+    s->dev_clean_rects = nullptr;
+}
+
+gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
+    int K = std::max(s->K, 1);
+    if (B <= s->cap_B && fpv * B <= s->cap_flips) return GS_OK;
+    destroy_graphs(s);
+    cudaFree(s->flip_stage);
+    cudaFree(s->desc);
+    cudaFree(s->item_off);
+    cudaFree(s->acc);
+    cudaFree(s->res_stage);
+    cudaFree(s->queue);
+    cudaFree(s->saved);
+    int cb = std::max(B, s->cap_B);
+    int cf = std::max(fpv * B, s->cap_flips);
+    GS_TRY(dmalloc((void**)&s->flip_stage, sizeof(gs_flip) * cf));
+    GS_TRY(dmalloc((void**)&s->desc, sizeof(DirtyDesc) * cb * K));
+    GS_TRY(dmalloc((void**)&s->item_off, sizeof(uint32_t) * (cb * K + 1)));
+    GS_TRY(dmalloc((void**)&s->acc, sizeof(CmpAcc) * cb * K));
+    GS_TRY(dmalloc((void**)&s->res_stage, sizeof(gs_result) * cb * K));
+    GS_TRY(dmalloc((void**)&s->queue, sizeof(unsigned int) * 4));
+    GS_TRY(dmalloc((void**)&s->saved, sizeof(uint32_t) * cf));
+    s->cap_B = cb;
+    s->cap_flips = cf;
+    return GS_OK;
+}
+
+gs_status check_flip_args(gs_scene* s, const gs_flip* flips, int B, int fpv, int guard_mode, uint64_t mask) {
+    if (!s || (!flips && B > 0) || B < 0 || fpv < 1) return set_error(GS_ERR_ARG, "bad campaign arguments");
+    if (s->K == 0 || s->views.empty()) return set_error(GS_ERR_STATE, "gs_set_views was not called");
+    if (guard_mode < -1 || guard_mode > 1) return set_error(GS_ERR_ARG, "guard_mode must be -1, 0 or 1");
+    if (guard_mode == GS_GUARD_PRIM) {
+        if (!s->pbox_lo) return set_error(GS_ERR_STATE, "no per-primitive box set");
+        uint64_t allowed = s->nbox_words >= 64 ? ~0ull : ((1ull << s->nbox_words) - 1ull);
+        if (mask & ~allowed) return set_error(GS_ERR_ARG, "PRIM guard mask covers words without boxes");
+    }
+    return GS_OK;
+}
+
+// enqueue one dirty-tile batch (B <= cap_B, flips already in flip_stage)
+gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaStream_t st) {
+    int K = s->K;
+    GS_TRY(launch_inject_prep(s, s->dev_cams, K, s->flip_stage, B, guard_mode, mask,
+                              (const uint2* const*)s->dev_clean_rects, s->desc, s->item_off, s->acc, s->queue, st));
+    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->acc, s->queue, st));
+    GS_TRY(launch_finalize(s->acc, B * K, s->res_stage, st));
+    return GS_OK;
+}
+
+gs_status run_dirty_batch(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaStream_t st) {
+    if (!s->use_graphs) return enqueue_dirty(s, B, guard_mode, mask, st);
+    GraphEntry* ge = nullptr;
+    for (auto& g : s->graphs)
+        if (g.B == B && g.guard == guard_mode && g.mask == mask) ge = &g;
+    if (!ge) {
+        dirty_grid();   // occupancy query outside the capture
+        cudaStream_t cs;
+        GS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        GraphEntry g;
+        g.B = B;
+        g.guard = guard_mode;
+        g.mask = mask;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_error(e, "cudaStreamBeginCapture");
+        }
+        gs_status qs = enqueue_dirty(s, B, guard_mode, mask, cs);
+        e = cudaStreamEndCapture(cs, &g.graph);
+        cudaStreamDestroy(cs);
+        if (qs != GS_OK) {
+            if (g.graph) cudaGraphDestroy(g.graph);
+            return qs;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g.graph);
+            return cuda_error(e, "cudaGraphInstantiate");
+        }
+        s->graphs.push_back(g);
+        ge = &s->graphs.back();
+    }
+    GS_CUDA(cudaGraphLaunch(ge->exec, st));
+    return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+const char* gs_last_error(void) { return g_last_error.c_str(); }
+
+const char* gs_version(void) { return "libgs 0.1 (sm_103a)"; }
+
+gs_status gs_load_scene(const void* planes, int src_on_device, uint64_t n, int sh_degree, gs_format fmt,
+                        gs_scene** out) {
+    if (!out) return set_error(GS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (sh_degree < 0 || sh_degree > 3) return set_error(GS_ERR_ARG, "sh_degree must be 0..3");
+    if (fmt != GS_FP32 && fmt != GS_FP16 && fmt != GS_BF16) return set_error(GS_ERR_ARG, "unknown storage format");
+    if (n > 0xffffffffull) return set_error(GS_ERR_ARG, "at most 2^32 - 1 primitives");
+    if (n > 0 && !planes) return set_error(GS_ERR_ARG, "planes is NULL");
+    gs_scene* s = new gs_scene();
+    s->n = n;
+    s->sh_degree = sh_degree;
+    s->fmt = fmt;
+    s->nwords = words_for_degree(sh_degree);
+    size_t bytes = (size_t)n * s->nwords * word_bytes(fmt);
+    // rounded up to 16 bytes: 16-bit words are flipped with 32-bit atomics on
+    // the aligned word that contains them
+    gs_status st = dmalloc(&s->planes, (bytes + 15) & ~(size_t)15);
+    if (st == GS_OK) st = dmalloc((void**)&s->dev_box, sizeof(uint32_t) * 2 * kMaxWords);
+    if (st == GS_OK) st = dmalloc((void**)&s->dev_err, sizeof(unsigned int) * 4);
+    if (st == GS_OK) st = dmalloc((void**)&s->dev_clamps, sizeof(unsigned long long) * 2);
+    if (st != GS_OK) {
+        gs_free_scene(s);
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(s->planes, planes, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->dev_err, 0, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->dev_clamps, 0, sizeof(unsigned long long) * 2);
+    if (e != cudaSuccess) {
+        gs_free_scene(s);
+        return cuda_error(e, "gs_load_scene copy");
+    }
+    // Algorithm 1 precompute: per-word min/max box
+    st = launch_field_box(s->planes, fmt, n, s->nwords, s->dev_box, 0);
+    uint32_t keys[2 * kMaxWords];
+    if (st == GS_OK) {
+        e = cudaMemcpy(keys, s->dev_box, sizeof(keys), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_error(e, "field box readback");
+    }
+    if (st != GS_OK) {
+        gs_free_scene(s);
+        return st;
+    }
+    for (int w = 0; w < s->nwords; w++) {
+        if (keys[w] == 0xffffffffu && keys[kMaxWords + w] == 0u) {   // no finite... no non-NaN value
+            s->box_lo[w] = s->box_hi[w] = 0u;
+        } else {
+            s->box_lo[w] = key_to_bits(keys[w], fmt);
+            s->box_hi[w] = key_to_bits(keys[kMaxWords + w], fmt);
+        }
+        keys[w] = s->box_lo[w];
+        keys[kMaxWords + w] = s->box_hi[w];
+    }
+    e = cudaMemcpy(s->dev_box, keys, sizeof(keys), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        gs_free_scene(s);
+        return cuda_error(e, "field box upload");
+    }
+    *out = s;
+    return GS_OK;
+}
+
+gs_status gs_free_scene(gs_scene* s) {
+    if (!s) return GS_OK;
+    free_views(s);
+    free_render_work(s->work);
+    cudaFree(s->planes);
+    cudaFree(s->pbox_lo);
+    cudaFree(s->pbox_hi);
+    cudaFree(s->dev_box);
+    cudaFree(s->dev_err);
+    cudaFree(s->dev_clamps);
+    cudaFree(s->flip_stage);
+    cudaFree(s->desc);
+    cudaFree(s->item_off);
+    cudaFree(s->acc);
+    cudaFree(s->res_stage);
+    cudaFree(s->queue);
+    cudaFree(s->saved);
+    delete s;
+    return GS_OK;
+}
+
+gs_status gs_scene_info(const gs_scene* s, uint64_t* n, int* sh_degree, int* fmt, int* nwords) {
+    if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
+    if (n) *n = s->n;
+    if (sh_degree) *sh_degree = s->sh_degree;
+    if (fmt) *fmt = s->fmt;
+    if (nwords) *nwords = s->nwords;
+    return GS_OK;
+}
+
+gs_status gs_scene_planes(gs_scene* s, void** dev_planes) {
+    if (!s || !dev_planes) return set_error(GS_ERR_ARG, "NULL argument");
+    *dev_planes = s->planes;
+    return GS_OK;
+}
+
+gs_status gs_read_planes(gs_scene* s, void* dst, int dst_on_device, void* stream) {
+    if (!s || !dst) return set_error(GS_ERR_ARG, "NULL argument");
+    size_t bytes = (size_t)s->n * s->nwords * word_bytes(s->fmt);
+    GS_CUDA(cudaMemcpyAsync(dst, s->planes, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            (cudaStream_t)stream));
+    if (!dst_on_device) GS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return GS_OK;
+}
+
+gs_status gs_scene_errors(gs_scene* s, uint32_t* host_flags) {
+    if (!s || !host_flags) return set_error(GS_ERR_ARG, "NULL argument");
+    GS_CUDA(cudaMemcpy(host_flags, s->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemset(s->dev_err, 0, sizeof(uint32_t)));
+    return GS_OK;
+}
+
+gs_status gs_apply_flips(gs_scene* s, const gs_flip* dev_flips, int64_t count, void* stream) {
+    if (!s || (count > 0 && !dev_flips) || count < 0) return set_error(GS_ERR_ARG, "bad gs_apply_flips arguments");
+    return launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, dev_flips, count, s->dev_err, (cudaStream_t)stream);
+}
+
+gs_status gs_field_box(gs_scene* s, uint32_t* host_lo, uint32_t* host_hi) {
+    if (!s || !host_lo || !host_hi) return set_error(GS_ERR_ARG, "NULL argument");
+    memcpy(host_lo, s->box_lo, sizeof(uint32_t) * s->nwords);
+    memcpy(host_hi, s->box_hi, sizeof(uint32_t) * s->nwords);
+    return GS_OK;
+}
+
+gs_status gs_set_prim_box(gs_scene* s, const void* lo, const void* hi, int src_on_device, int nbox_words) {
+    if (!s || !lo || !hi || nbox_words < 1 || nbox_words > s->nwords)
+        return set_error(GS_ERR_ARG, "bad gs_set_prim_box arguments");
+    destroy_graphs(s);
+    cudaFree(s->pbox_lo);
+    cudaFree(s->pbox_hi);
+    s->pbox_lo = s->pbox_hi = nullptr;
+    size_t bytes = (size_t)s->n * nbox_words * word_bytes(s->fmt);
+    GS_TRY(dmalloc(&s->pbox_lo, (bytes + 15) & ~(size_t)15));
+    GS_TRY(dmalloc(&s->pbox_hi, (bytes + 15) & ~(size_t)15));
+    cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    GS_CUDA(cudaMemcpy(s->pbox_lo, lo, bytes, kind));
+    GS_CUDA(cudaMemcpy(s->pbox_hi, hi, bytes, kind));
+    s->nbox_words = nbox_words;
+    return GS_OK;
+}
+
+gs_status gs_guard(gs_scene* s, int mode, uint64_t word_mask, uint64_t* dev_clamps, void* stream) {
+    if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
+    if (mode != GS_GUARD_FIELD && mode != GS_GUARD_PRIM) return set_error(GS_ERR_ARG, "mode must be FIELD or PRIM");
+    return launch_guard(s, mode, word_mask, (unsigned long long*)dev_clamps, (cudaStream_t)stream);
+}
+
+gs_status gs_render(gs_scene* s, const gs_camera* host_cams, int K, float* dev_rgb, void* stream) {
+    if (!s || !host_cams || !dev_rgb || K < 1) return set_error(GS_ERR_ARG, "bad gs_render arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t off = 0;
+    for (int k = 0; k < K; k++) {
+        if (!valid_camera(host_cams[k])) return set_error(GS_ERR_ARG, "invalid camera");
+        DevCamera cam = make_dev_camera(host_cams[k]);
+        uint32_t* ids = nullptr;
+        uint64_t np = 0;
+        GS_TRY(render_lists_sized(s, s->work, cam, &ids, &np, st));
+        GS_TRY(launch_blend_image(s->work.recs, ids, s->work.ranges, cam.W, cam.H, dev_rgb + off, st));
+        off += (size_t)cam.W * cam.H * 3;
+    }
+    return GS_OK;
+}
+
+gs_status gs_compare(const float* dev_a, const float* dev_b, int H, int W, int K, gs_result* dev_out, void* stream) {
+    if (!dev_a || !dev_b || !dev_out || H < 1 || W < 1 || K < 1) return set_error(GS_ERR_ARG, "bad gs_compare arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    CmpAcc* acc = nullptr;
+    GS_CUDA(cudaMallocAsync((void**)&acc, sizeof(CmpAcc) * K, st));
+    gs_status rs = launch_zero_acc(acc, K, st);
+    size_t img = (size_t)H * W * 3;
+    for (int k = 0; k < K && rs == GS_OK; k++) rs = launch_compare(dev_a + k * img, dev_b + k * img, H, W, acc + k, st);
+    if (rs == GS_OK) rs = launch_finalize(acc, K, dev_out, st);
+    cudaFreeAsync(acc, st);
+    return rs;
+}
+
+gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* stream) {
+    if (!s || !host_cams || K < 1 || K > 16) return set_error(GS_ERR_ARG, "bad gs_set_views arguments (1 <= K <= 16)");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < K; k++)
+        if (!valid_camera(host_cams[k])) return set_error(GS_ERR_ARG, "invalid camera");
+    free_views(s);
+    s->views.resize(K);
+    s->K = K;
+    std::vector<DevCamera> dcams(K);
+    std::vector<char> vptrs(view_ptrs_size() * K);
+    std::vector<const uint2*> crects(K);
+    uint64_t max_pairs = 0;
+    int max_tiles = 0;
+    for (int k = 0; k < K; k++) {
+        ViewState& v = s->views[k];
+        v.cam = make_dev_camera(host_cams[k]);
+        dcams[k] = v.cam;
+        int ntiles = v.cam.tiles_x * v.cam.tiles_y;
+        uint32_t* ids = nullptr;
+        uint64_t np = 0;
+        GS_TRY(render_lists_sized(s, s->work, v.cam, &ids, &np, st));
+        GS_TRY(dmalloc((void**)&v.recs, sizeof(BlendRec) * std::max<uint64_t>(s->n, 1)));
+        GS_TRY(dmalloc((void**)&v.rects, sizeof(uint2) * std::max<uint64_t>(s->n, 1)));
+        GS_TRY(dmalloc((void**)&v.ids, sizeof(uint32_t) * std::max<uint64_t>(np, 1)));
+        GS_TRY(dmalloc((void**)&v.ranges, sizeof(uint2) * ntiles));
+        GS_TRY(dmalloc((void**)&v.clean, sizeof(float) * (size_t)v.cam.W * v.cam.H * 3));
+        GS_CUDA(cudaMemcpyAsync(v.recs, s->work.recs, sizeof(BlendRec) * s->n, cudaMemcpyDeviceToDevice, st));
+        GS_CUDA(cudaMemcpyAsync(v.rects, s->work.rects, sizeof(uint2) * s->n, cudaMemcpyDeviceToDevice, st));
+        GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
+        GS_CUDA(cudaMemcpyAsync(v.ranges, s->work.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
+        GS_TRY(launch_blend_image(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, st));
+        v.npairs = np;
+        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.ranges, v.clean, v.cam.W, v.cam.H);
+        crects[k] = v.rects;
+        max_pairs = std::max(max_pairs, np);
+        max_tiles = std::max(max_tiles, ntiles);
+    }
+    GS_TRY(dmalloc((void**)&s->dev_cams, sizeof(DevCamera) * K));
+    GS_TRY(dmalloc(&s->dev_views, vptrs.size()));
+    GS_TRY(dmalloc((void**)&s->dev_clean_rects, sizeof(uint2*) * K));
+    GS_CUDA(cudaMemcpyAsync(s->dev_cams, dcams.data(), sizeof(DevCamera) * K, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(s->dev_views, vptrs.data(), vptrs.size(), cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(s->dev_clean_rects, crects.data(), sizeof(uint2*) * K, cudaMemcpyHostToDevice, st));
+    // the plain loop re-renders a single-flip variant: at most one primitive
+    // changes, adding at most one grid's worth of pairs
+    s->full_cap_pairs = max_pairs + (uint64_t)max_tiles + 1024;
+    s->max_tiles = max_tiles;
+    // buffers for the dirty engine
+    s->cap_B = 0;
+    s->cap_flips = 0;
+    GS_TRY(ensure_batch_buffers(s, 64, 1));
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+gs_status gs_clean_image(gs_scene* s, int k, float* dev_rgb, void* stream) {
+    if (!s || !dev_rgb || k < 0 || k >= s->K) return set_error(GS_ERR_ARG, "bad gs_clean_image arguments");
+    const ViewState& v = s->views[k];
+    GS_CUDA(cudaMemcpyAsync(dev_rgb, v.clean, sizeof(float) * (size_t)v.cam.W * v.cam.H * 3, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    return GS_OK;
+}
+
+gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int flips_per_variant, int guard_mode,
+                               uint64_t word_mask, gs_result* dev_out, void* stream) {
+    GS_TRY(check_flip_args(s, dev_flips, B, flips_per_variant, guard_mode, word_mask));
+    if (!dev_out && B > 0) return set_error(GS_ERR_ARG, "dev_out is NULL");
+    if (flips_per_variant != 1)
+        return gs_inject_and_render_full(s, dev_flips, B, flips_per_variant, guard_mode, word_mask, dev_out, stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = s->K;
+    const int chunk = std::max(1, std::min(64, 1024 / K));
+    GS_TRY(ensure_batch_buffers(s, chunk, 1));
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        int nb = std::min(chunk, B - b0);
+        GS_CUDA(cudaMemcpyAsync(s->flip_stage, dev_flips + b0, sizeof(gs_flip) * nb, cudaMemcpyDeviceToDevice, st));
+        GS_TRY(run_dirty_batch(s, nb, guard_mode, word_mask, st));
+        GS_CUDA(cudaMemcpyAsync(dev_out + (size_t)b0 * K, s->res_stage, sizeof(gs_result) * nb * K,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    return GS_OK;
+}
+
+gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B, int flips_per_variant,
+                                    int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream) {
+    GS_TRY(check_flip_args(s, dev_flips, B, flips_per_variant, guard_mode, word_mask));
+    if (!dev_out && B > 0) return set_error(GS_ERR_ARG, "dev_out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = s->K;
+    const int fpv = flips_per_variant;
+    GS_TRY(ensure_batch_buffers(s, 1, fpv));
+    uint64_t cap = s->full_cap_pairs + (uint64_t)(fpv - 1) * s->max_tiles;
+    GS_TRY(alloc_render_work(s->work, s->n, cap, s->max_tiles));
+    for (int b = 0; b < B; b++) {
+        const gs_flip* f = dev_flips + (size_t)b * fpv;
+        GS_TRY(launch_zero_acc(s->acc, K, st));
+        GS_TRY(launch_save_sites(s->planes, s->fmt, s->n, f, fpv, s->saved, st));
+        GS_TRY(launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->dev_err, st));
+        if (guard_mode >= 0) {
+            GS_TRY(launch_guard(s, guard_mode, word_mask, s->dev_clamps, st));
+            k_move_clamps<<<1, 32, 0, st>>>(s->dev_clamps, s->acc);
+            GS_CUDA(cudaGetLastError());
+        }
+        for (int k = 0; k < K; k++) {
+            const ViewState& v = s->views[k];
+            uint32_t* ids = nullptr;
+            GS_TRY(render_lists(s, s->work, v.cam, &ids, st));
+            GS_TRY(launch_blend_compare(s->work.recs, ids, s->work.ranges, v.cam.W, v.cam.H, v.clean, s->acc + k, st));
+        }
+        GS_TRY(launch_restore_sites(s->planes, s->fmt, s->n, f, fpv, s->saved, st));
+        GS_TRY(launch_finalize(s->acc, K, dev_out + (size_t)b * K, st));
+    }
+    return GS_OK;
+}
+
+gs_status gs_preprocess(gs_scene* s, const gs_camera* host_cam, gs_record* dev_out, void* stream) {
+    if (!s || !host_cam || !dev_out) return set_error(GS_ERR_ARG, "bad gs_preprocess arguments");
+    if (!valid_camera(*host_cam)) return set_error(GS_ERR_ARG, "invalid camera");
+    DevCamera cam = make_dev_camera(*host_cam);
+    return launch_preprocess(s, cam, nullptr, nullptr, nullptr, nullptr, dev_out, (cudaStream_t)stream);
+}
+
+gs_status gs_bin_tiles(const float* dev_depth, const int32_t* dev_rects, uint64_t n, int tiles_x, int tiles_y,
+                       uint32_t* dev_offsets, uint32_t* dev_ids, uint64_t ids_cap, uint64_t* host_total,
+                       void* stream) {
+    if ((!dev_depth || !dev_rects) && n > 0) return set_error(GS_ERR_ARG, "NULL input");
+    if (!dev_offsets || !host_total || tiles_x < 1 || tiles_y < 1 || tiles_x > 65535 || tiles_y > 65535)
+        return set_error(GS_ERR_ARG, "bad gs_bin_tiles arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    int ntiles = tiles_x * tiles_y;
+    RenderWork w;
+    gs_status rs = alloc_render_work(w, n, std::max<uint64_t>(ids_cap, 1), ntiles);
+    if (rs == GS_OK) rs = launch_rects_to_keys(dev_depth, dev_rects, n, w.dkey[0], w.dval[0], w.rects, st);
+    uint32_t* ids = nullptr;
+    if (rs == GS_OK) rs = build_tile_lists(w, n, tiles_x, tiles_y, &ids, st);
+    if (rs == GS_OK) rs = launch_ranges_to_offsets(w.ranges, ntiles, dev_offsets, w.total, st);
+    if (rs == GS_OK) {
+        cudaError_t e = cudaMemcpyAsync(w.host_total, w.total, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rs = cuda_error(e, "gs_bin_tiles readback");
+    }
+    if (rs == GS_OK) {
+        *host_total = w.host_total[2];
+        if (w.host_total[1]) {
+            rs = set_error(GS_ERR_CAPACITY, "ids_cap too small");
+        } else if (*host_total > 0) {
+            if (!dev_ids) {
+                rs = set_error(GS_ERR_ARG, "dev_ids is NULL");
+            } else {
+                cudaError_t e = cudaMemcpyAsync(dev_ids, ids, sizeof(uint32_t) * (*host_total), cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) rs = cuda_error(e, "gs_bin_tiles copy");
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    free_render_work(w);
+    return rs;
+}
+
+gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uint32_t* dev_offsets, const uint32_t* dev_ids,
+                         int W, int H, float* dev_rgb, void* stream) {
+    if (!dev_offsets || !dev_rgb || W < 1 || H < 1 || (n > 0 && !dev_recs)) return set_error(GS_ERR_ARG, "bad gs_blend_lists arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    int ntiles = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+    BlendRec* recs = nullptr;
+    uint2* ranges = nullptr;
+    GS_CUDA(cudaMallocAsync((void**)&recs, sizeof(BlendRec) * std::max<uint64_t>(n, 1), st));
+    GS_CUDA(cudaMallocAsync((void**)&ranges, sizeof(uint2) * ntiles, st));
+    gs_status rs = launch_records_to_blend(dev_recs, n, recs, st);
+    if (rs == GS_OK) rs = launch_offsets_to_ranges(dev_offsets, ntiles, ranges, st);
+    if (rs == GS_OK) rs = launch_blend_image(recs, dev_ids, ranges, W, H, dev_rgb, st);
+    cudaFreeAsync(recs, st);
+    cudaFreeAsync(ranges, st);
+    return rs;
+}
+
+gs_status gs_set_graphs(gs_scene* s, int enable) {
+    if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
+    s->use_graphs = enable != 0;
+    if (!enable) destroy_graphs(s);
+    return GS_OK;
+}
+
+}  // extern "C"

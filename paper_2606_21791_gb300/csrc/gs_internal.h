@@ -1,0 +1,197 @@
+// Internal declarations shared by the libgs translation units (GPU path only).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kTile = 16;             // render tile edge (pixels)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kMaxWords = 59;
+constexpr int kSseFracBits = 39;      // fixed-point scale of per-tile squared-error sums
+
+// ----------------------------------------------------------------------------
+// error reporting
+// ----------------------------------------------------------------------------
+gs_status set_error(gs_status st, const std::string& msg);
+gs_status cuda_error(cudaError_t e, const char* what);
+#define GS_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return gs::cuda_error(_e, #call); \
+    } while (0)
+#define GS_TRY(call)                          \
+    do {                                      \
+        gs_status _s = (call);                \
+        if (_s != GS_OK) return _s;           \
+    } while (0)
+
+inline int words_for_degree(int d) { return 14 + ((d + 1) * (d + 1) - 1) * 3; }
+inline int word_bytes(int fmt) { return fmt == GS_FP32 ? 4 : 2; }
+inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// ----------------------------------------------------------------------------
+// device-side records
+// ----------------------------------------------------------------------------
+// Blend record of one primitive in one view (48 B, 16-B aligned).  ex, ey are
+// the half extents (pixels) of a box that contains every pixel centre where the
+// primitive's alpha can reach 1/255 (NaN if the opacity is NaN: never culled;
+// negative if it can never reach 1/255).
+struct __align__(16) BlendRec {
+    float mx, my, ca, cb;
+    float cc, opac, ex, ey;
+    float r, g, b, depth;
+};
+
+// Camera with the per-view constants the preprocess needs.
+struct DevCamera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int W, H;
+    float znear, zfar;
+    int tiles_x, tiles_y;
+};
+
+// Per (variant, view) comparison accumulator (integer/ordered atomics only, so
+// the result does not depend on the order in which tiles finish).
+struct CmpAcc {
+    unsigned long long sse_fx;  // sum of per-tile float SSE, fixed point 2^-kSseFracBits
+    unsigned int maxabs_bits;   // float bits of the max |diff| (non-negative floats order as uints)
+    unsigned int footprint;
+    unsigned int nonfinite;
+    unsigned int clamps;
+};
+
+// Dirty-tile work descriptor of one (variant, view).
+struct DirtyDesc {
+    BlendRec rec;          // corrupted primitive's record
+    uint32_t prim;
+    int32_t new_vis;       // corrupted primitive binned?
+    int32_t old_vis;       // clean primitive binned?
+    uint32_t n_items;      // dirty tiles
+    uint16_t nx0, ny0, nx1, ny1;   // corrupted rect
+    uint16_t ox0, oy0, ox1, oy1;   // clean rect
+};
+
+// ----------------------------------------------------------------------------
+// per-view clean state and scratch
+// ----------------------------------------------------------------------------
+struct ViewState {
+    DevCamera cam{};
+    BlendRec* recs = nullptr;        // [n]
+    uint2* rects = nullptr;          // [n] (x0 | y0 << 16, x1 | y1 << 16)
+    uint32_t* ids = nullptr;         // [npairs] sorted tile lists
+    uint2* ranges = nullptr;         // [ntiles] (start, end)
+    float* clean = nullptr;          // [H*W*3]
+    uint64_t npairs = 0;
+    uint64_t cap_pairs = 0;
+};
+
+// Scratch of the full render pipeline for one view.
+struct RenderWork {
+    uint64_t n = 0;
+    uint64_t cap_pairs = 0;
+    int ntiles_cap = 0;
+    BlendRec* recs = nullptr;
+    uint2* rects = nullptr;
+    uint32_t* dkey[2] = {nullptr, nullptr};    // depth keys (ping-pong)
+    uint32_t* dval[2] = {nullptr, nullptr};    // primitive ids (ping-pong)
+    uint32_t* cnt = nullptr;                    // tiles per primitive, in depth order
+    uint32_t* off = nullptr;                    // exclusive scan of cnt
+    uint32_t* pkey[2] = {nullptr, nullptr};    // pair tile keys
+    uint32_t* pval[2] = {nullptr, nullptr};    // pair primitive ids
+    uint32_t* hist = nullptr;                   // radix histograms
+    uint32_t* scan_tmp = nullptr;               // block sums for scans
+    uint2* ranges = nullptr;
+    unsigned long long* total = nullptr;        // [0] pair count, [1] overflow flag
+    unsigned long long* host_total = nullptr;   // pinned mirror
+};
+
+struct GraphEntry {
+    int B = 0;
+    int guard = -2;
+    uint64_t mask = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace gs
+
+struct gs_scene {
+    uint64_t n = 0;
+    int sh_degree = 0;
+    int fmt = 0;
+    int nwords = 0;
+    void* planes = nullptr;                 // [nwords][n]
+    uint32_t box_lo[gs::kMaxWords] = {};    // FIELD box (storage words)
+    uint32_t box_hi[gs::kMaxWords] = {};
+    void* pbox_lo = nullptr;                // PRIM box planes [nbox][n]
+    void* pbox_hi = nullptr;
+    int nbox_words = 0;
+    uint32_t* dev_box = nullptr;            // FIELD box on device: lo[59], hi[59]
+    unsigned int* dev_err = nullptr;        // sticky device error flags (bit 0: bad flip site)
+    unsigned long long* dev_clamps = nullptr;
+
+    // clean per-view state of the campaign
+    int K = 0;
+    std::vector<gs::ViewState> views;
+    gs::DevCamera* dev_cams = nullptr;
+    void* dev_views = nullptr;              // ViewPtrs[K]
+    void* dev_clean_rects = nullptr;        // const uint2*[K]
+    uint64_t full_cap_pairs = 0;
+    int max_tiles = 0;
+    gs::RenderWork work;                    // scratch of the full render pipeline
+
+    // batch buffers (dirty engine and plain loop)
+    int cap_B = 0;
+    int cap_flips = 0;
+    gs_flip* flip_stage = nullptr;
+    gs::DirtyDesc* desc = nullptr;
+    uint32_t* item_off = nullptr;
+    gs::CmpAcc* acc = nullptr;
+    gs_result* res_stage = nullptr;
+    unsigned int* queue = nullptr;
+    uint32_t* saved = nullptr;
+    bool use_graphs = true;
+    std::vector<gs::GraphEntry> graphs;
+};
+
+namespace gs {
+
+// k_guard.cu
+int num_sms();
+gs_status launch_field_box(const void* planes, int fmt, uint64_t n, int nwords, uint32_t* dev_keys, cudaStream_t st);
+gs_status launch_guard(gs_scene* s, int mode, uint64_t mask, unsigned long long* dev_clamps, cudaStream_t st);
+gs_status launch_save_sites(const void* planes, int fmt, uint64_t n, const gs_flip* flips, int count, uint32_t* saved,
+                            cudaStream_t st);
+gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, const gs_flip* flips, int count,
+                               const uint32_t* saved, cudaStream_t st);
+
+// k_preprocess.cu
+DevCamera make_dev_camera(const gs_camera& c);
+
+// k_sort.cu
+gs_status alloc_render_work(RenderWork& w, uint64_t n, uint64_t cap_pairs, int ntiles);
+void free_render_work(RenderWork& w);
+gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, uint32_t* keys, uint32_t* vals,
+                               uint2* prects, cudaStream_t st);
+
+// k_blend.cu
+gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+                             float* img, cudaStream_t st);
+gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+                               const float* clean, CmpAcc* acc, cudaStream_t st);
+gs_status launch_compare(const float* a, const float* b, int H, int W, CmpAcc* acc, cudaStream_t st);
+gs_status launch_finalize(const CmpAcc* acc, int count, gs_result* out, cudaStream_t st);
+gs_status launch_records_to_blend(const gs_record* in, uint64_t n, BlendRec* out, cudaStream_t st);
+
+}  // namespace gs

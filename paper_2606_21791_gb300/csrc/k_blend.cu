@@ -1,0 +1,483 @@
+// (d) front-to-back alpha blending and (e) comparison against the clean frame.
+//
+// Blend (3DGS forward pass, composited over white as in Sec. 3 "Metrics and
+// severity"): one 256-thread block per 16x16 tile, one thread per pixel.  The
+// tile's sorted list is staged through shared memory 256 records at a time.
+// Each warp owns an 8x4 pixel block and skips, warp-uniformly, every staged
+// primitive whose alpha >= 1/255 box (BlendRec::ex/ey, conservative) misses the
+// block.  Per pixel: power = -(a dx^2 + c dy^2)/2 - b dx dy; skip power > 0;
+// alpha = opacity exp(power); skip alpha < 1/255; alpha capped at 0.99; stop
+// before the primitive that would take T below 1e-4; C += colour alpha T.
+// The block leaves as soon as all of its pixels have stopped.
+//
+// Compare (Definitions 1-2): per tile, squared differences of [0,1]-clamped
+// images (NaN counts as 0) are summed in a fixed reduction tree, turned into a
+// fixed-point integer and added atomically, so a (variant, view) record does not
+// depend on which tiles ran or in what order: a dirty-tile re-blend and a full
+// re-render give identical records.
+//
+// Dirty-tile engine: a persistent kernel takes (variant, view, dirty tile) work
+// items from an atomic queue.  A dirty tile is re-blended from the clean sorted
+// list with the flipped primitive's clean entry removed and its corrupted record
+// merged in at its (depth, index) position, and compared on the fly.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kBT = 256;
+
+struct Stage {
+    float mx[kBT], my[kBT], ca[kBT], cb[kBT], cc[kBT], op[kBT], ex[kBT], ey[kBT], r[kBT], g[kBT], b[kBT];
+};
+
+__device__ __forceinline__ void stage_put(Stage& s, int j, const BlendRec& q) {
+    s.mx[j] = q.mx;
+    s.my[j] = q.my;
+    s.ca[j] = q.ca;
+    s.cb[j] = q.cb;
+    s.cc[j] = q.cc;
+    s.op[j] = q.opac;
+    s.ex[j] = q.ex;
+    s.ey[j] = q.ey;
+    s.r[j] = q.r;
+    s.g[j] = q.g;
+    s.b[j] = q.b;
+}
+
+__device__ __forceinline__ BlendRec load_rec(const BlendRec* recs, uint32_t id) {
+    const float4* p = reinterpret_cast<const float4*>(recs + id);
+    float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    BlendRec q;
+    q.mx = a.x;
+    q.my = a.y;
+    q.ca = a.z;
+    q.cb = a.w;
+    q.cc = b.x;
+    q.opac = b.y;
+    q.ex = b.z;
+    q.ey = b.w;
+    q.r = c.x;
+    q.g = c.y;
+    q.b = c.z;
+    q.depth = c.w;
+    return q;
+}
+
+struct Pix {
+    float T, c0, c1, c2;
+    bool done;
+};
+
+// Pixel geometry of thread `tid` in a tile: warp w covers an 8x4 block.
+struct PixGeo {
+    int px, py;
+    float pxc, pyc;
+    float wx0, wx1, wy0, wy1;   // pixel-centre bounds of the warp's block
+    bool inside;
+};
+
+__device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int W, int H) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    PixGeo g;
+    int bx = tile_x * kTile + (warp & 1) * 8;
+    int by = tile_y * kTile + (warp >> 1) * 4;
+    g.px = bx + (lane & 7);
+    g.py = by + (lane >> 3);
+    g.pxc = (float)g.px + 0.5f;
+    g.pyc = (float)g.py + 0.5f;
+    g.wx0 = (float)bx + 0.5f;
+    g.wx1 = (float)bx + 7.5f;
+    g.wy0 = (float)by + 0.5f;
+    g.wy1 = (float)by + 3.5f;
+    g.inside = g.px < W && g.py < H;
+    return g;
+}
+
+__device__ __forceinline__ void blend_batch(const Stage& s, int cnt, const PixGeo& g, Pix& p) {
+    if (__all_sync(0xffffffffu, p.done)) return;
+    for (int j = 0; j < cnt; j++) {
+        // warp-uniform cull against the conservative alpha box (NaN never culls)
+        const float mx = s.mx[j], ex = s.ex[j];
+        if (mx + ex < g.wx0 || mx - ex > g.wx1) continue;
+        const float my = s.my[j], ey = s.ey[j];
+        if (my + ey < g.wy0 || my - ey > g.wy1) continue;
+        if (p.done) continue;
+        const float dx = mx - g.pxc, dy = my - g.pyc;
+        const float power = -0.5f * (s.ca[j] * dx * dx + s.cc[j] * dy * dy) - s.cb[j] * dx * dy;
+        if (power > 0.0f) continue;
+        float alpha = s.op[j] * __expf(power);
+        if (alpha < 1.0f / 255.0f) continue;
+        if (alpha > 0.99f) alpha = 0.99f;
+        const float Tn = p.T * (1.0f - alpha);
+        if (Tn < 1e-4f) {
+            p.done = true;
+            continue;
+        }
+        p.c0 = p.c0 + s.r[j] * alpha * p.T;
+        p.c1 = p.c1 + s.g[j] * alpha * p.T;
+        p.c2 = p.c2 + s.b[j] * alpha * p.T;
+        p.T = Tn;
+    }
+}
+
+__device__ __forceinline__ float clamp01(float v) { return v > 0.0f ? (v < 1.0f ? v : 1.0f) : 0.0f; }
+
+// Compare this tile's pixels with the clean image and add to *acc.
+__device__ __forceinline__ void compare_tile(const PixGeo& g, float v0, float v1, float v2, const float* clean, int W,
+                                             CmpAcc* acc) {
+    __shared__ float wsse[kBT / 32];
+    __shared__ float wmax[kBT / 32];
+    float sq = 0.0f, m = 0.0f;
+    bool foot = false, nonfin = false;
+    if (g.inside) {
+        const float* c = clean + ((size_t)g.py * W + g.px) * 3;
+        float d0 = clamp01(v0) - clamp01(c[0]);
+        float d1 = clamp01(v1) - clamp01(c[1]);
+        float d2 = clamp01(v2) - clamp01(c[2]);
+        sq = d0 * d0 + d1 * d1 + d2 * d2;
+        m = fmaxf(fmaxf(fabsf(d0), fabsf(d1)), fabsf(d2));   // differences are finite
+        foot = m > 1.0f / 255.0f;
+        nonfin = !(isfinite(v0) && isfinite(v1) && isfinite(v2));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        wsse[warp] = sq;
+        wmax[warp] = m;
+    }
+    int nfoot = __syncthreads_count(foot);
+    int nbad = __syncthreads_count(nonfin);
+    if (threadIdx.x == 0) {
+        float t = 0.0f, mm = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kBT / 32; w++) {
+            t += wsse[w];
+            mm = fmaxf(mm, wmax[w]);
+        }
+        if (t > 0.0f) atomicAdd(&acc->sse_fx, __float2ull_rn(t * 549755813888.0f));   // 2^kSseFracBits
+        if (mm > 0.0f) atomicMax(&acc->maxabs_bits, __float_as_uint(mm));
+        if (nfoot) atomicAdd(&acc->footprint, (unsigned)nfoot);
+        if (nbad) atomicAdd(&acc->nonfinite, (unsigned)nbad);
+    }
+}
+
+template <int MODE>   // 0: write the image, 1: compare with the clean image
+__global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
+                                                   const uint2* __restrict__ ranges, int W, int H, int tiles_x,
+                                                   float* __restrict__ img, const float* __restrict__ clean,
+                                                   CmpAcc* acc) {
+    __shared__ Stage s;
+    const int tile = blockIdx.x;
+    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
+    Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside};
+    const uint2 rg = ranges[tile];
+    for (uint32_t base = rg.x; base < rg.y; base += kBT) {
+        int cnt = (int)min((uint32_t)kBT, rg.y - base);
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) stage_put(s, threadIdx.x, load_rec(recs, ids[base + threadIdx.x]));
+        __syncthreads();
+        blend_batch(s, cnt, g, p);
+        if (__syncthreads_count(p.done) == kBT) break;
+    }
+    const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
+    if (MODE == 0) {
+        if (g.inside) {
+            float* o = img + ((size_t)g.py * W + g.px) * 3;
+            o[0] = v0;
+            o[1] = v1;
+            o[2] = v2;
+        }
+    } else {
+        compare_tile(g, v0, v1, v2, clean, W, acc);
+    }
+}
+
+__global__ __launch_bounds__(kBT) void k_compare(const float* __restrict__ a, const float* __restrict__ b, int W, int H,
+                                                int tiles_x, CmpAcc* acc) {
+    const int tile = blockIdx.x;
+    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
+    float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+    if (g.inside) {
+        const float* q = a + ((size_t)g.py * W + g.px) * 3;
+        v0 = q[0];
+        v1 = q[1];
+        v2 = q[2];
+    }
+    compare_tile(g, v0, v1, v2, b, W, acc);
+}
+
+__global__ void k_finalize(const CmpAcc* acc, int count, gs_result* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    CmpAcc a = acc[i];
+    gs_result r;
+    r.sse = (double)a.sse_fx * (1.0 / 549755813888.0);
+    r.maxabs = __uint_as_float(a.maxabs_bits);
+    r.footprint = a.footprint;
+    r.nonfinite = a.nonfinite;
+    r.clamps = a.clamps;
+    out[i] = r;
+}
+
+__global__ void k_zero_acc(CmpAcc* acc, int count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u};
+}
+
+// ---------------------------------------------------------------------------
+// dirty-tile persistent kernel
+// ---------------------------------------------------------------------------
+struct ViewPtrs {
+    const BlendRec* recs;
+    const uint32_t* ids;
+    const uint2* ranges;
+    const float* clean;
+    int W, H, tiles_x, pad;
+};
+
+// lexicographic (depth, id) < (d, p)
+__device__ __forceinline__ bool key_less(float dj, uint32_t ij, float d, uint32_t p) {
+    return dj < d || (dj == d && ij < p);
+}
+
+__global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
+                                              const uint32_t* __restrict__ item_off, int BK, int K,
+                                              CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue) {
+    __shared__ Stage s;
+    __shared__ BlendRec nrec;
+    __shared__ int sh_item_ok, sh_bk, sh_tx, sh_ty, sh_has_old, sh_has_new;
+    __shared__ uint32_t sh_s, sh_e, sh_pp, sh_ins;
+    const uint32_t total = item_off[BK];
+    while (true) {
+        if (threadIdx.x == 0) {
+            uint32_t item = atomicAdd(&queue[0], 1u);
+            sh_item_ok = item < total;
+            if (item < total) {
+                // (variant, view) of this item: last bk with item_off[bk] <= item
+                int lo = 0, hi = BK - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                const int bk = lo;
+                const DirtyDesc& d = desc[bk];
+                uint32_t j = item - item_off[bk];
+                int tx = 0, ty = 0;
+                uint32_t wn = (uint32_t)d.nx1 - d.nx0;
+                uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
+                if (j < an) {
+                    tx = d.nx0 + (int)(j % wn);
+                    ty = d.ny0 + (int)(j / wn);
+                } else {
+                    // tiles of the clean rect that are not in the corrupted rect, row-major
+                    uint32_t r = j - an;
+                    for (int y = d.oy0; y < d.oy1; y++) {
+                        int ex0 = d.ox0, ex1 = d.ox0;   // excluded x range of this row
+                        if (d.new_vis && y >= d.ny0 && y < d.ny1) {
+                            ex0 = max((int)d.ox0, (int)d.nx0);
+                            ex1 = min((int)d.ox1, (int)d.nx1);
+                            if (ex1 < ex0) ex1 = ex0;
+                        }
+                        uint32_t left = (uint32_t)(ex0 - d.ox0);
+                        uint32_t row = (uint32_t)(d.ox1 - d.ox0) - (uint32_t)(ex1 - ex0);
+                        if (r < row) {
+                            ty = y;
+                            tx = r < left ? d.ox0 + (int)r : ex1 + (int)(r - left);
+                            break;
+                        }
+                        r -= row;
+                    }
+                }
+                const int k = bk % K;
+                const ViewPtrs v = views[k];
+                const int tile = ty * v.tiles_x + tx;
+                const uint2 rg = v.ranges[tile];
+                const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
+                const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
+                uint32_t pp = 0, ins = 0;
+                if (has_old) {
+                    const float dold = v.recs[d.prim].depth;
+                    uint32_t a = rg.x, b = rg.y;
+                    while (a < b) {
+                        uint32_t m = (a + b) >> 1;
+                        uint32_t id = v.ids[m];
+                        if (key_less(v.recs[id].depth, id, dold, d.prim)) a = m + 1; else b = m;
+                    }
+                    pp = a - rg.x;
+                }
+                if (has_new) {
+                    uint32_t a = rg.x, b = rg.y;
+                    while (a < b) {
+                        uint32_t m = (a + b) >> 1;
+                        uint32_t id = v.ids[m];
+                        if (key_less(v.recs[id].depth, id, d.rec.depth, d.prim)) a = m + 1; else b = m;
+                    }
+                    ins = a - rg.x;
+                    if (has_old && pp < ins) ins -= 1;
+                    nrec = d.rec;
+                }
+                sh_bk = bk;
+                sh_tx = tx;
+                sh_ty = ty;
+                sh_s = rg.x;
+                sh_e = rg.y;
+                sh_pp = pp;
+                sh_ins = ins;
+                sh_has_old = has_old;
+                sh_has_new = has_new;
+            }
+        }
+        __syncthreads();
+        if (!sh_item_ok) break;
+        const int bk = sh_bk, k = bk % K;
+        const ViewPtrs v = views[k];
+        const PixGeo g = pix_geo(sh_tx, sh_ty, v.W, v.H);
+        const uint32_t s0 = sh_s, pp = sh_pp, ins = sh_ins;
+        const bool has_old = sh_has_old, has_new = sh_has_new;
+        const uint32_t L = (sh_e - sh_s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
+        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside};
+        for (uint32_t base = 0; base < L; base += kBT) {
+            int cnt = (int)min((uint32_t)kBT, L - base);
+            __syncthreads();
+            if ((int)threadIdx.x < cnt) {
+                uint32_t m = base + threadIdx.x;
+                if (has_new && m == ins) {
+                    stage_put(s, threadIdx.x, nrec);
+                } else {
+                    uint32_t j = (has_new && m > ins) ? m - 1 : m;
+                    uint32_t ci = (has_old && j >= pp) ? j + 1 : j;
+                    stage_put(s, threadIdx.x, load_rec(v.recs, v.ids[s0 + ci]));
+                }
+            }
+            __syncthreads();
+            blend_batch(s, cnt, g, p);
+            if (__syncthreads_count(p.done) == kBT) break;
+        }
+        const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
+        compare_tile(g, v0, v1, v2, v.clean, v.W, &acc[bk]);
+        __syncthreads();
+    }
+}
+
+__global__ void k_records_to_blend(const gs_record* in, uint64_t n, BlendRec* out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gs_record r = in[i];
+    BlendRec q;
+    q.mx = r.mx;
+    q.my = r.my;
+    q.ca = r.ca;
+    q.cb = r.cb;
+    q.cc = r.cc;
+    q.opac = r.opac;
+    q.r = r.r;
+    q.g = r.g;
+    q.b = r.b;
+    q.depth = r.depth;
+    // records from outside carry no alpha box: never cull
+    q.ex = NAN;
+    q.ey = NAN;
+    out[i] = q;
+}
+
+__global__ void k_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) ranges[t] = make_uint2(offsets[t], offsets[t + 1]);
+}
+
+}  // namespace
+
+gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H, float* img,
+                             cudaStream_t st) {
+    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    if (tx * ty == 0) return GS_OK;
+    k_blend_full<0><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+                               const float* clean, CmpAcc* acc, cudaStream_t st) {
+    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    if (tx * ty == 0) return GS_OK;
+    k_blend_full<1><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_compare(const float* a, const float* b, int H, int W, CmpAcc* acc, cudaStream_t st) {
+    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    if (tx * ty == 0) return GS_OK;
+    k_compare<<<tx * ty, kBT, 0, st>>>(a, b, W, H, tx, acc);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st) {
+    if (count <= 0) return GS_OK;
+    k_zero_acc<<<(count + 255) / 256, 256, 0, st>>>(acc, count);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_finalize(const CmpAcc* acc, int count, gs_result* out, cudaStream_t st) {
+    if (count <= 0) return GS_OK;
+    k_finalize<<<(count + 255) / 256, 256, 0, st>>>(acc, count, out);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+int dirty_grid() {
+    static int blocks = 0;
+    if (!blocks) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dirty, kBT, 0);
+        if (per_sm < 1) per_sm = 1;
+        blocks = per_sm * num_sms();
+    }
+    return blocks;
+}
+
+gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
+                             CmpAcc* acc, unsigned int* queue, cudaStream_t st) {
+    k_dirty<<<dirty_grid(), kBT, 0, st>>>((const ViewPtrs*)dev_views, desc, item_off, BK, K, acc, queue);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+size_t view_ptrs_size() { return sizeof(ViewPtrs); }
+
+void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const float* clean,
+                    int W, int H) {
+    ViewPtrs v;
+    v.recs = recs;
+    v.ids = ids;
+    v.ranges = ranges;
+    v.clean = clean;
+    v.W = W;
+    v.H = H;
+    v.tiles_x = (W + kTile - 1) / kTile;
+    v.pad = 0;
+    memcpy(host_dst, &v, sizeof(v));
+}
+
+gs_status launch_records_to_blend(const gs_record* in, uint64_t n, BlendRec* out, cudaStream_t st) {
+    if (n == 0) return GS_OK;
+    k_records_to_blend<<<(unsigned)div_up(n, 256), 256, 0, st>>>(in, n, out);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges, cudaStream_t st) {
+    if (ntiles <= 0) return GS_OK;
+    k_offsets_to_ranges<<<(ntiles + 255) / 256, 256, 0, st>>>(offsets, ntiles, ranges);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,468 @@
+// (b) preprocess: the activations of Sec. 3 "Parameter layout" (exp of the
+// log-scale, normalised quaternion, logistic opacity, SH colour up to degree 3)
+// and the EWA projection of the 3DGS forward pass, one thread per primitive.
+//
+// This translation unit is compiled with -fmad=false: every product and sum is
+// rounded on its own, in a fixed order, so the geometry that decides binning
+// (depth, projected mean, radius, tile rect) is reproducible bit for bit between
+// the full preprocess, the dirty-tile injector below, and any fp32 evaluation
+// with the same operation order.
+//
+// Conventions fixed here (the paper defers its renderer to an external library):
+// quaternion (w, x, y, z); 2D covariance + 0.3 on the diagonal; tx/z, ty/z
+// clamped to +-1.3 half-FOV tangents; radius = ceil(3 sqrt(lambda_max)) with
+// lambda_max = mid + sqrt(max(0.1, mid^2 - det)); tile rect = tiles meeting
+// [mx - r, mx + r] x [my - r, my + r]; colour = SH(normalize(mean - camera
+// centre)) + 0.5 clamped at 0 from below; non-finite geometry culls, non-finite
+// appearance propagates.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+// real SH basis constants (closed forms)
+constexpr float kC0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+constexpr float kC1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kC2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float kC2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float kC2c = 0.54627421529603959f;  // sqrt(15/pi)/4
+constexpr float kC3a = 0.59004358992664352f;  // sqrt(35/(2 pi))/4
+constexpr float kC3b = 2.8906114426405538f;   // sqrt(105/pi)/2
+constexpr float kC3c = 0.45704579946446572f;  // sqrt(21/(2 pi))/4
+constexpr float kC3d = 0.37317633259011546f;  // sqrt(7/pi)/4
+constexpr float kC3e = 1.4453057213202769f;   // sqrt(105/pi)/4
+
+template <int FMT>
+__device__ __forceinline__ float decode(uint32_t b) {
+    if (FMT == GS_FP32) return __uint_as_float(b);
+    if (FMT == GS_FP16) return __half2float(__ushort_as_half((unsigned short)b));
+    return __uint_as_float(b << 16);
+}
+
+template <int FMT>
+__device__ __forceinline__ uint32_t load_bits(const void* planes, uint64_t n, int w, uint64_t i) {
+    if (FMT == GS_FP32) return __ldg((const uint32_t*)planes + (uint64_t)w * n + i);
+    return __ldg((const unsigned short*)planes + (uint64_t)w * n + i);
+}
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) {
+    return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// Conservative half extents of the region where alpha = opac * exp(-q/2) can
+// reach 1/255, for 2D covariance diagonal (a, c); see BlendRec.  Margins (1e-3
+// relative on the quadratic form plus 0.01 px) dwarf fp32 rounding of the
+// blend's own alpha, so culling against the box never changes a pixel.
+__device__ __forceinline__ void cull_extent(float a, float c, float opac, float* ex, float* ey) {
+    float lim = logf(255.0f * opac);   // alpha >= 1/255 needs q <= 2 lim
+    if (lim < -1e-3f) {
+        *ex = -INFINITY;
+        *ey = -INFINITY;
+        return;
+    }
+    if (lim < 0.0f) lim = 0.0f;       // NaN passes through and disables culling
+    float q = 2.0f * lim * 1.001f + 1e-3f;
+    *ex = sqrtf(q * a) + 0.01f;
+    *ey = sqrtf(q * c) + 0.01f;
+}
+
+// Preprocess one primitive.  `src(w)` returns the float value of word w.
+// Returns false when the primitive is culled (not binned).
+template <typename Src>
+__device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const DevCamera& cam, BlendRec& rec,
+                                                uint2& rect, float& radius) {
+    const float* R = cam.R;
+    const float* t = cam.t;
+    float mu0 = src(0), mu1 = src(1), mu2 = src(2);
+    float p0 = R[0] * mu0 + R[1] * mu1 + R[2] * mu2 + t[0];
+    float p1 = R[3] * mu0 + R[4] * mu1 + R[5] * mu2 + t[1];
+    float z = R[6] * mu0 + R[7] * mu1 + R[8] * mu2 + t[2];
+    if (!finite3(p0, p1, z)) return false;
+    if (!(z > cam.znear) || !(z < cam.zfar)) return false;
+
+    float s0 = expf(src(3)), s1 = expf(src(4)), s2 = expf(src(5));
+
+    float qw = src(6), qx = src(7), qy = src(8), qz = src(9);
+    float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    if (!(qn2 > 0.0f) || !isfinite(qn2)) return false;
+    float qn = sqrtf(qn2);
+    qw = qw / qn;
+    qx = qx / qn;
+    qy = qy / qn;
+    qz = qz / qn;
+    float r00 = 1.0f - 2.0f * (qy * qy + qz * qz);
+    float r01 = 2.0f * (qx * qy - qw * qz);
+    float r02 = 2.0f * (qx * qz + qw * qy);
+    float r10 = 2.0f * (qx * qy + qw * qz);
+    float r11 = 1.0f - 2.0f * (qx * qx + qz * qz);
+    float r12 = 2.0f * (qy * qz - qw * qx);
+    float r20 = 2.0f * (qx * qz - qw * qy);
+    float r21 = 2.0f * (qy * qz + qw * qx);
+    float r22 = 1.0f - 2.0f * (qx * qx + qy * qy);
+
+    // M = Rq diag(s); Sigma = M M^T (symmetric: compute all 9 in a fixed order)
+    float m00 = r00 * s0, m01 = r01 * s1, m02 = r02 * s2;
+    float m10 = r10 * s0, m11 = r11 * s1, m12 = r12 * s2;
+    float m20 = r20 * s0, m21 = r21 * s1, m22 = r22 * s2;
+    float S[9];
+    S[0] = m00 * m00 + m01 * m01 + m02 * m02;
+    S[1] = m00 * m10 + m01 * m11 + m02 * m12;
+    S[2] = m00 * m20 + m01 * m21 + m02 * m22;
+    S[3] = m10 * m00 + m11 * m01 + m12 * m02;
+    S[4] = m10 * m10 + m11 * m11 + m12 * m12;
+    S[5] = m10 * m20 + m11 * m21 + m12 * m22;
+    S[6] = m20 * m00 + m21 * m01 + m22 * m02;
+    S[7] = m20 * m10 + m21 * m11 + m22 * m12;
+    S[8] = m20 * m20 + m21 * m21 + m22 * m22;
+
+    // camera covariance V = R Sigma R^T
+    float RS[9], V[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) RS[3 * r + c] = R[3 * r + 0] * S[c] + R[3 * r + 1] * S[3 + c] + R[3 * r + 2] * S[6 + c];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            V[3 * r + c] = RS[3 * r + 0] * R[3 * c + 0] + RS[3 * r + 1] * R[3 * c + 1] + RS[3 * r + 2] * R[3 * c + 2];
+
+    // perspective Jacobian at the mean, with the view-frustum clamp
+    float limx = 1.3f * (0.5f * (float)cam.W / cam.fx);
+    float limy = 1.3f * (0.5f * (float)cam.H / cam.fy);
+    float ux = p0 / z, uy = p1 / z;
+    if (ux < -limx) ux = -limx;
+    if (ux > limx) ux = limx;
+    if (uy < -limy) uy = -limy;
+    if (uy > limy) uy = limy;
+    float tx = ux * z, ty = uy * z;
+    float j00 = cam.fx / z, j02 = -(cam.fx * tx) / (z * z);
+    float j11 = cam.fy / z, j12 = -(cam.fy * ty) / (z * z);
+    float jv00 = j00 * V[0] + j02 * V[6];
+    float jv01 = j00 * V[1] + j02 * V[7];
+    float jv02 = j00 * V[2] + j02 * V[8];
+    float jv11 = j11 * V[4] + j12 * V[7];
+    float jv12 = j11 * V[5] + j12 * V[8];
+    float a = jv00 * j00 + jv02 * j02 + 0.3f;
+    float b = jv01 * j11 + jv02 * j12;
+    float c = jv11 * j11 + jv12 * j12 + 0.3f;
+
+    float det = a * c - b * b;
+    if (!(det > 0.0f) || !isfinite(det)) return false;
+    float ca = c / det, cb = -b / det, cc = a / det;
+    if (!finite3(ca, cb, cc)) return false;
+    float mid = 0.5f * (a + c);
+    float disc = mid * mid - det;
+    if (disc < 0.1f) disc = 0.1f;
+    float lmax = mid + sqrtf(disc);
+    float rad = ceilf(3.0f * sqrtf(lmax));
+    if (!(rad > 0.0f) || !isfinite(rad)) return false;
+    radius = rad;
+
+    float mx = cam.fx * (p0 / z) + cam.cx;
+    float my = cam.fy * (p1 / z) + cam.cy;
+    if (!isfinite(mx) || !isfinite(my)) return false;
+
+    const float tw = (float)kTile;
+    const float ftx = (float)cam.tiles_x, fty = (float)cam.tiles_y;
+    float fx0 = floorf((mx - rad) / tw), fx1 = floorf((mx + rad) / tw) + 1.0f;
+    float fy0 = floorf((my - rad) / tw), fy1 = floorf((my + rad) / tw) + 1.0f;
+    fx0 = fminf(fmaxf(fx0, 0.0f), ftx);   // operands finite here
+    fy0 = fminf(fmaxf(fy0, 0.0f), fty);
+    fx1 = fminf(fmaxf(fx1, 0.0f), ftx);
+    fy1 = fminf(fmaxf(fy1, 0.0f), fty);
+    int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
+    if (x1 <= x0 || y1 <= y0) return false;
+
+    // colour: SH at the viewing direction
+    float cp0 = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+    float cp1 = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+    float cp2 = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+    float d0 = mu0 - cp0, d1 = mu1 - cp1, d2 = mu2 - cp2;
+    float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    float x = d0 / dn, y = d1 / dn, zz_ = d2 / dn;
+    float Y[16];
+    Y[0] = kC0;
+    int ncoef = 1;
+    if (sh_degree >= 1) {
+        Y[1] = -kC1 * y;
+        Y[2] = kC1 * zz_;
+        Y[3] = -kC1 * x;
+        ncoef = 4;
+    }
+    if (sh_degree >= 2) {
+        float xx = x * x, yy = y * y, zz = zz_ * zz_;
+        float xy = x * y, yz = y * zz_, xz = x * zz_;
+        Y[4] = kC2a * xy;
+        Y[5] = -kC2a * yz;
+        Y[6] = kC2b * (2.0f * zz - xx - yy);
+        Y[7] = -kC2a * xz;
+        Y[8] = kC2c * (xx - yy);
+        ncoef = 9;
+        if (sh_degree >= 3) {
+            Y[9] = -kC3a * y * (3.0f * xx - yy);
+            Y[10] = kC3b * xy * zz_;
+            Y[11] = -kC3c * y * (4.0f * zz - xx - yy);
+            Y[12] = kC3d * zz_ * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -kC3c * x * (4.0f * zz - xx - yy);
+            Y[14] = kC3e * zz_ * (xx - yy);
+            Y[15] = -kC3a * x * (xx - 3.0f * yy);
+            ncoef = 16;
+        }
+    }
+    float rgb[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float acc = Y[0] * src(11 + ch);
+        for (int j = 1; j < ncoef; j++) acc = acc + Y[j] * src(14 + 3 * (j - 1) + ch);
+        acc = acc + 0.5f;
+        rgb[ch] = (acc < 0.0f) ? 0.0f : acc;
+    }
+    float o = src(10);
+    float opac = 1.0f / (1.0f + expf(-o));
+
+    rec.mx = mx;
+    rec.my = my;
+    rec.ca = ca;
+    rec.cb = cb;
+    rec.cc = cc;
+    rec.opac = opac;
+    cull_extent(a, c, opac, &rec.ex, &rec.ey);
+    rec.r = rgb[0];
+    rec.g = rgb[1];
+    rec.b = rgb[2];
+    rec.depth = z;
+    rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+    return true;
+}
+
+template <int FMT>
+struct PlaneSrc {
+    const void* planes;
+    uint64_t n, i;
+    __device__ float operator()(int w) const { return decode<FMT>(load_bits<FMT>(planes, n, w, i)); }
+};
+
+// full preprocess: records, packed rects, depth-sort keys (invisible: 0xffffffff)
+template <int FMT>
+__global__ __launch_bounds__(256) void k_preprocess(const void* planes, uint64_t n, int sh_degree, DevCamera cam,
+                                                    BlendRec* recs, uint2* rects, uint32_t* keys, uint32_t* vals,
+                                                    gs_record* dbg) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    BlendRec rec;
+    uint2 rect = make_uint2(0, 0);
+    float rad = 0.0f;
+    bool vis = preprocess_core(PlaneSrc<FMT>{planes, n, i}, sh_degree, cam, rec, rect, rad);
+    if (!vis) {
+        rec = BlendRec{0, 0, 0, 0, 0, 0, -INFINITY, -INFINITY, 0, 0, 0, 0};
+        rect = make_uint2(0, 0);
+    }
+    if (recs) recs[i] = rec;
+    if (rects) rects[i] = rect;
+    if (keys) {
+        keys[i] = vis ? __float_as_uint(rec.depth) : 0xffffffffu;
+        vals[i] = (uint32_t)i;
+    }
+    if (dbg) {
+        gs_record g;
+        memset(&g, 0, sizeof(g));
+        if (vis) {
+            g.mx = rec.mx;
+            g.my = rec.my;
+            g.ca = rec.ca;
+            g.cb = rec.cb;
+            g.cc = rec.cc;
+            g.r = rec.r;
+            g.g = rec.g;
+            g.b = rec.b;
+            g.opac = rec.opac;
+            g.depth = rec.depth;
+            g.x0 = rect.x & 0xffff;
+            g.y0 = rect.x >> 16;
+            g.x1 = rect.y & 0xffff;
+            g.y1 = rect.y >> 16;
+            g.radius = (int32_t)rad;
+            g.visible = 1;
+        }
+        dbg[i] = g;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dirty-tile injector: thread (b, k) gathers the flipped primitive's words,
+// XORs the upset in the storage format, optionally guards them (Algorithm 1
+// applied to the only primitive that can leave its box), preprocesses the
+// corrupted primitive for view k and describes the dirty tiles: the union of
+// its clean and corrupted tile rects.  One block; then a block-wide exclusive
+// scan gives each (b, k) its range of work items.  Also zeroes the comparison
+// accumulators and the work-queue counter.
+// ---------------------------------------------------------------------------
+struct WordSrc {
+    const float* v;
+    __device__ float operator()(int w) const { return v[w]; }
+};
+
+template <int FMT>
+__global__ __launch_bounds__(1024) void k_inject_prep(const void* planes, uint64_t n, int nwords, int sh_degree,
+                                                      const DevCamera* cams, int K, const gs_flip* flips, int B,
+                                                      int guard_mode, uint64_t mask, const uint32_t* box,
+                                                      const void* pblo, const void* pbhi, int nbox,
+                                                      const uint2* const* clean_rects, DirtyDesc* desc,
+                                                      uint32_t* item_off, CmpAcc* acc, unsigned int* queue) {
+    const int tid = threadIdx.x;
+    const int total = B * K;
+    uint32_t items = 0;
+    if (tid < total) {
+        const int b = tid / K, k = tid % K;
+        gs_flip f = flips[b];
+        const int nbits = FMT == GS_FP32 ? 32 : 16;
+        bool ok = f.prim < n && f.word < nwords && f.bit < nbits;
+        uint32_t p = ok ? f.prim : 0u;
+        float v[kMaxWords];
+        unsigned int clamps = 0;
+        for (int w = 0; w < nwords; w++) {
+            uint32_t bits = load_bits<FMT>(planes, n, w, p);
+            if (ok && w == f.word) bits ^= (1u << f.bit);
+            float x = decode<FMT>(bits);
+            if (guard_mode >= 0 && ((mask >> w) & 1ull)) {
+                uint32_t lb, hb;
+                if (guard_mode == GS_GUARD_FIELD) {
+                    lb = box[w];
+                    hb = box[kMaxWords + w];
+                } else {
+                    lb = w < nbox ? load_bits<FMT>(pblo, n, w, p) : 0u;
+                    hb = w < nbox ? load_bits<FMT>(pbhi, n, w, p) : 0u;
+                }
+                float lo = decode<FMT>(lb), hi = decode<FMT>(hb);
+                if (!(x >= lo && x <= hi)) {
+                    clamps++;
+                    x = (x > hi) ? hi : lo;
+                }
+            }
+            v[w] = x;
+        }
+        DirtyDesc d;
+        d.prim = p;
+        uint2 rect = make_uint2(0, 0);
+        float rad = 0.0f;
+        bool nv = ok && preprocess_core(WordSrc{v}, sh_degree, cams[k], d.rec, rect, rad);
+        uint2 orect = ok ? clean_rects[k][p] : make_uint2(0, 0);
+        uint32_t ox0 = orect.x & 0xffff, oy0 = orect.x >> 16, ox1 = orect.y & 0xffff, oy1 = orect.y >> 16;
+        bool ov = ox1 > ox0 && oy1 > oy0;
+        uint32_t nx0 = rect.x & 0xffff, ny0 = rect.x >> 16, nx1 = rect.y & 0xffff, ny1 = rect.y >> 16;
+        if (!nv) nx0 = ny0 = nx1 = ny1 = 0;
+        uint32_t an = nv ? (nx1 - nx0) * (ny1 - ny0) : 0u;
+        uint32_t ao = ov ? (ox1 - ox0) * (oy1 - oy0) : 0u;
+        uint32_t ix = 0, iy = 0;
+        if (nv && ov) {
+            int lx = max((int)nx0, (int)ox0), hx = min((int)nx1, (int)ox1);
+            int ly = max((int)ny0, (int)oy0), hy = min((int)ny1, (int)oy1);
+            ix = hx > lx ? (uint32_t)(hx - lx) : 0u;
+            iy = hy > ly ? (uint32_t)(hy - ly) : 0u;
+        }
+        items = an + ao - ix * iy;
+        d.new_vis = nv;
+        d.old_vis = ov;
+        d.n_items = items;
+        d.nx0 = (uint16_t)nx0;
+        d.ny0 = (uint16_t)ny0;
+        d.nx1 = (uint16_t)nx1;
+        d.ny1 = (uint16_t)ny1;
+        d.ox0 = (uint16_t)ox0;
+        d.oy0 = (uint16_t)oy0;
+        d.ox1 = (uint16_t)ox1;
+        d.oy1 = (uint16_t)oy1;
+        if (!nv) d.rec = BlendRec{0, 0, 0, 0, 0, 0, -INFINITY, -INFINITY, 0, 0, 0, 0};
+        desc[tid] = d;
+        CmpAcc z;
+        z.sse_fx = 0ull;
+        z.maxabs_bits = 0u;
+        z.footprint = 0u;
+        z.nonfinite = 0u;
+        z.clamps = (k == 0) ? clamps : 0u;   // clamps reported once per variant, on view 0
+        acc[tid] = z;
+    }
+    // block-wide exclusive scan of the item counts
+    __shared__ uint32_t wsum[32];
+    const int lane = tid & 31, wid = tid >> 5;
+    uint32_t x = items;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    uint32_t incl = x + (wid > 0 ? wsum[wid - 1] : 0u);
+    if (tid < total) item_off[tid] = incl - items;
+    if (tid == total - 1) item_off[total] = incl;
+    if (tid == 0) {
+        queue[0] = 0u;
+        queue[1] = 0u;
+    }
+}
+
+}  // namespace
+
+DevCamera make_dev_camera(const gs_camera& c) {
+    DevCamera d;
+    memcpy(d.R, c.R, sizeof(d.R));
+    memcpy(d.t, c.t, sizeof(d.t));
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    d.W = c.width;
+    d.H = c.height;
+    d.znear = c.znear;
+    d.zfar = c.zfar;
+    d.tiles_x = (c.width + kTile - 1) / kTile;
+    d.tiles_y = (c.height + kTile - 1) / kTile;
+    return d;
+}
+
+gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects, uint32_t* keys,
+                            uint32_t* vals, gs_record* dbg, cudaStream_t st) {
+    if (s->n == 0) return GS_OK;
+    unsigned blocks = (unsigned)div_up(s->n, 256);
+    if (s->fmt == GS_FP32)
+        k_preprocess<GS_FP32><<<blocks, 256, 0, st>>>(s->planes, s->n, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+    else if (s->fmt == GS_FP16)
+        k_preprocess<GS_FP16><<<blocks, 256, 0, st>>>(s->planes, s->n, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+    else
+        k_preprocess<GS_BF16><<<blocks, 256, 0, st>>>(s->planes, s->n, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,
+                             int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects, DirtyDesc* desc,
+                             uint32_t* item_off, CmpAcc* acc, unsigned int* queue, cudaStream_t st) {
+    if (B * K > 1024) return set_error(GS_ERR_ARG, "B * K must be <= 1024");
+    int threads = ((B * K + 31) / 32) * 32;
+#define GS_PREP(F)                                                                                          \
+    k_inject_prep<F><<<1, threads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, dev_cams, K, flips, B, \
+                                            guard_mode, mask, s->dev_box, s->pbox_lo, s->pbox_hi,            \
+                                            s->nbox_words, dev_clean_rects, desc, item_off, acc, queue)
+    if (s->fmt == GS_FP32)
+        GS_PREP(GS_FP32);
+    else if (s->fmt == GS_FP16)
+        GS_PREP(GS_FP16);
+    else
+        GS_PREP(GS_BF16);
+#undef GS_PREP
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // namespace gs

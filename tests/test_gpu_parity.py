@@ -1,0 +1,412 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: flipped words, guard outputs and clamp counts, field boxes, tile
+lists from the same (depth, rect) input, footprint counts from the same images.
+Floating point: pixels within 2e-3 absolute on >= 99.9% of pixels, PSNR within
+0.05 dB."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_21791_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 2e-3
+PIX_FRAC = 0.999
+PSNR_TOL = 0.05
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    import paper_2606_21791_gb300 as P
+    P.build()
+    from paper_2606_21791_gb300 import gs
+    gs.load_library()
+    torch.cuda.init()
+    return gs
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _load(G, scene):
+    return G.gs_load_scene(scene.planes, scene.n, scene.sh_degree, scene.fmt)
+
+
+def _read(G, h, scene):
+    out = np.empty_like(scene.planes)
+    G.gs_read_planes(h, out)
+    return out
+
+
+def _render_gpu(G, h, cams):
+    torch = _torch()
+    cams = np.atleast_1d(cams)
+    tot = sum(int(c["width"]) * int(c["height"]) * 3 for c in cams)
+    buf = torch.empty(tot, dtype=torch.float32, device="cuda")
+    G.gs_render(h, cams, buf)
+    torch.cuda.synchronize()
+    out, off = [], 0
+    for c in cams:
+        H, W = int(c["height"]), int(c["width"])
+        out.append(buf[off:off + H * W * 3].cpu().numpy().reshape(H, W, 3))
+        off += H * W * 3
+    return out
+
+
+def _pix_agree(a, b):
+    both_nan = np.isnan(a) & np.isnan(b)
+    d = np.abs(a.astype(np.float64) - b.astype(np.float64))
+    ok = (d <= PIX_TOL) | both_nan
+    return ok.all(axis=-1).mean()
+
+
+def _psnr(sse, npx):
+    return O.psnr(float(sse), npx)
+
+
+# ---------------------------------------------------------------------------
+# (a) injection, (f) guard: bit exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+def test_apply_flips_bit_exact(G, fmt):
+    torch = _torch()
+    sc = S.make_scene(3001, 3, fmt, 50, layout="clusters")
+    flips = S.flips_stratified(4000, sc.n, sc.nwords, fmt, 51)
+    flips = np.concatenate([flips, flips[:17]])        # duplicates cancel
+    h = _load(G, sc)
+    try:
+        d = G.to_device(flips)
+        G.gs_apply_flips(h, d, len(flips))
+        torch.cuda.synchronize()
+        assert np.array_equal(_read(G, h, sc), O.apply_flips(sc.planes, fmt, flips))
+        assert G.gs_scene_errors(h) == 0
+        bad = S.flips_at(np.array([sc.n]), 0, 0)       # out-of-range site: skipped and flagged
+        G.gs_apply_flips(h, G.to_device(bad), 1)
+        torch.cuda.synchronize()
+        assert G.gs_scene_errors(h) == 1
+    finally:
+        G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+def test_field_box_bit_exact(G, fmt):
+    sc = S.make_scene(20011, 3, fmt, 52, layout="clusters")
+    v = sc.planes.copy()
+    v[5, 7] = S.encode(np.array([np.nan], np.float32), fmt)[0]   # NaN words are ignored
+    sc = S.Scene(v, fmt, 3)
+    h = _load(G, sc)
+    try:
+        lo, hi = G.gs_field_box(h, sc.nwords)
+        olo, ohi = O.field_box(sc.planes, fmt)
+        assert np.array_equal(lo, olo) and np.array_equal(hi, ohi)
+    finally:
+        G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mask", [S.GUARD_WORDS_DEFAULT, S.GUARD_WORDS_SELECTIVE, (1 << 59) - 1])
+def test_guard_bit_exact(G, fmt, mode, mask):
+    torch = _torch()
+    n = 40_003   # ragged against every vector width
+    clean = S.make_scene(n, 3, fmt, 53, layout="clusters")
+    nbox = 59 if mask == (1 << 59) - 1 else 14
+    if mode == 0:
+        lo, hi = O.field_box(clean.planes, fmt)
+    else:
+        lo, hi = S.prim_boxes(clean, nbox, 54)
+    rng = np.random.default_rng(55)
+    fl = S.flips_at(rng.integers(0, n, size=5000), 0, 0)
+    fl["word"] = rng.integers(0, 59, size=5000)
+    fl["bit"] = rng.integers(0, S.FORMAT_BITS[fmt], size=5000)
+    bad_planes = O.apply_flips(clean.planes, fmt, fl)
+    ref, nref = O.guard(bad_planes, fmt, mask, mode, lo, hi)
+    # the GPU scene's FIELD box is computed from what it loads: load clean, then flip
+    h = _load(G, clean)
+    try:
+        if mode == 1:
+            G.gs_set_prim_box(h, lo, hi, nbox)
+        G.gs_apply_flips(h, G.to_device(fl), len(fl))
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        G.gs_guard(h, mode, mask, cnt)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == nref and nref > 0
+        assert np.array_equal(_read(G, h, clean), ref)
+        # guarding again finds nothing (Theorem 1(i) on the guarded model)
+        cnt.zero_()
+        G.gs_guard(h, mode, mask, cnt)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == 0
+    finally:
+        G.gs_free_scene(h)
+
+
+# ---------------------------------------------------------------------------
+# (b) preprocess
+# ---------------------------------------------------------------------------
+def _gpu_records(G, h, cam, n):
+    torch = _torch()
+    buf = G.device_bytes(n * G.RECORD_DTYPE.itemsize)
+    G.gs_preprocess(h, cam, buf)
+    torch.cuda.synchronize()
+    return G.from_device(buf, G.RECORD_DTYPE)[:n]
+
+
+@pytest.mark.parametrize("fmt,degree,layout,n", [(S.FP32, 0, "cube", 5000), (S.FP32, 3, "clusters", 30000),
+                                                 (S.FP16, 3, "clusters", 30000), (S.BF16, 3, "clusters", 30000)])
+def test_preprocess_parity(G, fmt, degree, layout, n):
+    sc = S.make_scene(n, degree, fmt, 56, layout=layout)
+    cams = S.ring_cameras(2, 320, 208)
+    h = _load(G, sc)
+    try:
+        for cam in cams:
+            g = _gpu_records(G, h, cam, sc.n)
+            o = O.preprocess(sc.planes, fmt, degree, cam)
+            vis = o["visible"] == 1
+            assert np.array_equal(g["visible"], o["visible"])
+            for f in ("x0", "y0", "x1", "y1", "radius"):
+                assert np.array_equal(g[f][vis], o[f][vis]), f
+            # depth and projected mean: identical operation order, no contraction
+            for f in ("depth", "mx", "my", "r", "g", "b"):
+                assert np.array_equal(g[f][vis].view(np.uint32), o[f][vis].view(np.uint32)), f
+            # conic and opacity go through exp: CUDA's expf and the C library's may
+            # differ by one ulp, which the 2x2 inverse amplifies (det cancellation)
+            for f in ("ca", "cb", "cc", "opac"):
+                np.testing.assert_allclose(g[f][vis], o[f][vis], rtol=1e-4, atol=1e-6, err_msg=f)
+                same = (g[f][vis].view(np.uint32) == o[f][vis].view(np.uint32)).mean()
+                assert same >= 0.99, (f, same)
+    finally:
+        G.gs_free_scene(h)
+
+
+# ---------------------------------------------------------------------------
+# (c) binning + radix sort: bit exact from the same per-primitive input
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["tiny", "clusters", "ties_and_giants"])
+def test_bin_tiles_bit_exact(G, case):
+    torch = _torch()
+    if case == "tiny":
+        sc = S.make_scene(5000, 0, S.FP32, 57)
+        cam = S.ring_cameras(1, 256, 256)[0]
+        recs = O.preprocess(sc.planes, S.FP32, 0, cam)
+    else:
+        sc = S.make_scene(60000, 0, S.FP32, 58, layout="clusters")
+        cam = S.ring_cameras(1, 800, 600)[0]
+        recs = O.preprocess(sc.planes, S.FP32, 0, cam)
+        if case == "ties_and_giants":
+            rng = np.random.default_rng(3)
+            vis = np.nonzero(recs["visible"])[0]
+            recs["depth"][vis[:5000]] = np.float32(12.5)     # many exact depth ties
+            g = vis[5000:5010]                               # primitives covering most of the grid
+            recs["x0"][g], recs["y0"][g] = 0, 0
+            recs["x1"][g], recs["y1"][g] = 50, 38
+            recs["depth"][g] = rng.uniform(5, 25, size=len(g)).astype(np.float32)
+    W, H = int(cam["width"]), int(cam["height"])
+    tx, ty = -(-W // 16), -(-H // 16)
+    off_o, ids_o = O.bin_tiles(recs, W, H)
+    rects = np.stack([recs["x0"], recs["y0"], recs["x1"], recs["y1"]], axis=1).astype(np.int32)
+    rects[recs["visible"] == 0] = 0
+    d_depth = torch.from_numpy(recs["depth"].copy()).cuda()
+    d_rects = torch.from_numpy(rects.reshape(-1).copy()).cuda()
+    d_off = torch.zeros(tx * ty + 1, dtype=torch.int32, device="cuda")
+    cap = len(ids_o) + 10
+    d_ids = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    total = G.gs_bin_tiles(d_depth, d_rects, sc.n, tx, ty, d_off, d_ids, cap)
+    assert total == len(ids_o)
+    assert np.array_equal(d_off.cpu().numpy().view(np.uint32), off_o)
+    assert np.array_equal(d_ids.cpu().numpy().view(np.uint32)[:total], ids_o)
+    # too-small capacity is reported, not overrun
+    with pytest.raises(G.GsError) as e:
+        G.gs_bin_tiles(d_depth, d_rects, sc.n, tx, ty, d_off, d_ids, max(total // 2, 1))
+    assert e.value.status == G.GS_ERR_CAPACITY
+
+
+# ---------------------------------------------------------------------------
+# (d) blend from the same records and lists; (e) compare from the same images
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("W,H", [(256, 256), (200, 136)])
+def test_blend_lists_parity(G, W, H):
+    torch = _torch()
+    sc = S.make_scene(8000, 0, S.FP32, 59)
+    v = sc.values().copy()
+    v[3:6, :3] = 2.0          # a few exploded primitives
+    v[10, 3] = np.nan         # non-finite opacity propagates
+    planes = S.encode(v, S.FP32)
+    cam = S.look_at_camera((1.0, 2.0, 14.0), width=W, height=H)
+    recs = O.preprocess(planes, S.FP32, 0, cam)
+    off, ids = O.bin_tiles(recs, W, H)
+    ref = O.blend(recs, off, ids, W, H)
+    d_recs = G.to_device(recs.astype(G.RECORD_DTYPE))
+    d_off = torch.from_numpy(off.view(np.int32).copy()).cuda()
+    d_ids = torch.from_numpy(ids.view(np.int32).copy()).cuda()
+    img = torch.empty(H * W * 3, dtype=torch.float32, device="cuda")
+    G.gs_blend_lists(d_recs, len(recs), d_off, d_ids, W, H, img)
+    torch.cuda.synchronize()
+    out = img.cpu().numpy().reshape(H, W, 3)
+    assert _pix_agree(out, ref) >= PIX_FRAC
+    assert np.array_equal(np.isnan(out), np.isnan(ref))
+
+
+def test_compare_exact_counts(G):
+    torch = _torch()
+    rng = np.random.default_rng(7)
+    K, H, W = 3, 67, 91
+    a = rng.uniform(-0.2, 1.2, size=(K, H, W, 3)).astype(np.float32)
+    b = a + rng.normal(0, 0.01, size=a.shape).astype(np.float32) * (rng.uniform(size=a.shape) < 0.3)
+    a[0, 3, 4, 1] = np.nan
+    a[1, 5, 6, 0] = np.inf
+    b[2, 10, 10, 2] = a[2, 10, 10, 2] - np.float32(1 / 255)
+    da = torch.from_numpy(a.reshape(-1).copy()).cuda()
+    db = torch.from_numpy(b.reshape(-1).copy()).cuda()
+    out = G.device_bytes(K * 24)
+    G.gs_compare(da, db, H, W, K, out)
+    torch.cuda.synchronize()
+    r = G.from_device(out, G.RESULT_DTYPE)
+    for k in range(K):
+        o = O.compare(a[k], b[k])
+        assert r[k]["footprint"] == o["footprint"] and r[k]["nonfinite"] == o["nonfinite"]
+        assert r[k]["maxabs"] == o["maxabs"]
+        assert abs(r[k]["sse"] - o["sse"]) <= 1e-6 * o["sse"] + 1e-9
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+def test_render_tiny_matches_oracle(G):
+    sc, cams, _ = S.tiny_workload()
+    h = _load(G, sc)
+    try:
+        g = _render_gpu(G, h, cams)[0]
+        o = O.render(sc.planes, S.FP32, 0, cams[0])
+        assert _pix_agree(g, o) >= PIX_FRAC
+        assert np.abs(g - o).max() < 1e-4
+    finally:
+        G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+def test_render_degree3_clusters_matches_oracle(G, fmt):
+    sc = S.make_scene(40000, 3, fmt, 60, layout="clusters")
+    cams = S.ring_cameras(2, 400, 272)
+    h = _load(G, sc)
+    try:
+        gi = _render_gpu(G, h, cams)
+        for k in range(2):
+            o = O.render(sc.planes, fmt, 3, cams[k])
+            assert _pix_agree(gi[k], o) >= PIX_FRAC
+    finally:
+        G.gs_free_scene(h)
+
+
+def _campaign_gpu(G, h, flips, K, fpv=1, guard=-1, mask=S.GUARD_WORDS_DEFAULT, full=False):
+    torch = _torch()
+    nvar = len(flips) // fpv
+    out = G.device_bytes(nvar * K * 24)
+    d = G.to_device(flips)
+    fn = G.gs_inject_and_render_full if full else G.gs_inject_and_render
+    fn(h, d, nvar, fpv, guard, mask, out)
+    torch.cuda.synchronize()
+    return G.from_device(out, G.RESULT_DTYPE).reshape(nvar, K)
+
+
+def test_campaign_tiny_matches_oracle(G):
+    sc, cams, flips = S.tiny_workload()
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        g = _campaign_gpu(G, h, flips, 1)
+        o, _, _ = O.campaign(sc.planes, S.FP32, 0, cams, flips, nthreads=O.max_threads())
+        npx = 256 * 256 * 3
+        gp = np.array([_psnr(x, npx) for x in g["sse"].ravel()])
+        op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
+        assert np.abs(gp - op).max() <= PSNR_TOL
+        assert np.array_equal(g["nonfinite"] > 0, o["nonfinite"] > 0)
+        assert (g["footprint"] == o["footprint"]).mean() >= 0.99
+    finally:
+        G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+@pytest.mark.parametrize("guard", [-1, 0, 1])
+def test_dirty_tile_equals_full_rerender(G, fmt, guard):
+    """Batched dirty-tile records are bit-identical to one-variant-at-a-time full
+    re-renders of the same variants (guard off, FIELD, PRIM)."""
+    sc = S.make_scene(30000, 3, fmt, 61, layout="clusters")
+    cams = S.ring_cameras(2, 320, 240)
+    flips = S.flips_stratified(59 * S.FORMAT_BITS[fmt], sc.n, sc.nwords, fmt, 62)
+    h = _load(G, sc)
+    try:
+        if guard == 1:
+            lo, hi = S.prim_boxes(sc, 14, 63)
+            G.gs_set_prim_box(h, lo, hi, 14)
+        G.gs_set_views(h, cams)
+        a = _campaign_gpu(G, h, flips, 2, guard=guard)
+        b = _campaign_gpu(G, h, flips, 2, guard=guard, full=True)
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert np.array_equal(a[f], b[f]), f
+        assert (a["footprint"] > 0).any()
+        # the scene is left unchanged by both
+        assert np.array_equal(_read(G, h, sc), sc.planes)
+    finally:
+        G.gs_free_scene(h)
+
+
+def test_campaign_batching_guard_matches_oracle(G):
+    """fp16 storage, degree-3 clusters, PRIM guard on: GPU campaign vs oracle."""
+    fmt = S.FP16
+    sc = S.make_scene(20000, 3, fmt, 64, layout="clusters")
+    cams = S.ring_cameras(1, 240, 240)
+    flips = S.flips_stratified(59 * 16, sc.n, sc.nwords, fmt, 65)[::4]
+    lo, hi = S.prim_boxes(sc, 14, 66)
+    h = _load(G, sc)
+    try:
+        G.gs_set_prim_box(h, lo, hi, 14)
+        G.gs_set_views(h, cams)
+        g = _campaign_gpu(G, h, flips, 1, guard=1)
+        o, cl, _ = O.campaign(sc.planes, fmt, 3, cams, flips, guard_mode=1, word_mask=S.GUARD_WORDS_DEFAULT,
+                              box_lo=lo, box_hi=hi, nthreads=O.max_threads())
+        assert np.array_equal(g["clamps"][:, 0], cl.astype(np.uint32))
+        npx = 240 * 240 * 3
+        gp = np.array([_psnr(x, npx) for x in g["sse"].ravel()])
+        op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
+        assert np.abs(gp - op).max() <= PSNR_TOL
+        assert (g["footprint"] == o["footprint"]).mean() >= 0.99
+    finally:
+        G.gs_free_scene(h)
+
+
+def test_multi_flip_variants_match_oracle(G):
+    sc, cams, _ = S.tiny_workload()
+    flips = S.flips_multi(40 * 25, sc.n, sc.nwords, S.FP32, 67)
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        g = _campaign_gpu(G, h, flips, 1, fpv=25)
+        o, _, _ = O.campaign(sc.planes, S.FP32, 0, cams, flips, flips_per_variant=25, nthreads=O.max_threads())
+        npx = 256 * 256 * 3
+        gp = np.array([_psnr(x, npx) for x in g["sse"].ravel()])
+        op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
+        assert np.abs(gp - op).max() <= PSNR_TOL
+        assert np.array_equal(g["nonfinite"] > 0, o["nonfinite"] > 0)
+    finally:
+        G.gs_free_scene(h)
+
+
+def test_graphs_on_and_off_identical(G):
+    sc, cams, flips = S.tiny_workload()
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        a = _campaign_gpu(G, h, flips, 1)
+        G.gs_set_graphs(h, False)
+        b = _campaign_gpu(G, h, flips, 1)
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    finally:
+        G.gs_free_scene(h)
