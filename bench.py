@@ -1,0 +1,427 @@
+"""Benchmark of the SEU-injection hot path on GB300.
+
+Default workload (one GPU): 2,000,000 Gaussians (4 clusters, SH degree 3, fp32
+storage), four 1600x1040 views on a ring, 20,000 single-bit upsets with 70% on
+bits 24-31 of log-scale and opacity.  A step is one launch of the batched
+dirty-tile engine over B variants (B picked by the library's autotuner from
+{8,16,32,64}), replayed as a CUDA graph: inject + guard-ready preprocess of the
+flipped primitives, dirty-tile re-blend fused with the comparison against the
+clean frames, finalisation of the per-(variant, view) records.  Reported beside
+it: the plain one-variant-per-launch full-render loop on the same flips, the
+end-to-end rate through host buffers, the support-guard clamp bandwidth on a
+66,000,000-Gaussian scene, and the CPU oracle on a bounded sample.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "injections/s and Mpix/s vs plain loop on 1 GB300; p99 frame latency; guard GB/s"
+UNIT = "injections/s"
+WORKLOAD = ("2M Gaussians (4 clusters, SH degree 3, fp32), 4 ring views 1600x1040, 20k upsets "
+            "(70% on bits 24-31 of log-scale/opacity); batched dirty-tile engine, CUDA graphs, guard off")
+FLOP_PER_EVAL = 20          # FP32 ops per pixel-primitive evaluation of the blend (FMA = 2)
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-guard-stress", action="store_true", help="skip the 66M-Gaussian guard measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--guard-n", type=int, default=66_000_000)
+    ap.add_argument("--gaussians", type=int, default=2_000_000,
+                    help="scene size (the 2M default is the benchmark; smaller only for profiling captures)")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def traffic_record():
+    """Per-launch DRAM bytes of kernels from the committed ncu summary (key value lines)."""
+    out = {}
+    try:
+        for line in open(TRAFFIC_FILE):
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(None, 1)
+            out[k] = v.strip()
+    except FileNotFoundError:
+        pass
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (rank 0, N = 1)
+# ---------------------------------------------------------------------------
+def cpu_baseline(scene, cams, flips, crop=None, variants=None):
+    """Times the oracle as it stands on the host cores: `variants` upsets (one per
+    core), each rendered in view 0 (optionally a centred crop of it) and compared
+    with the clean view; extrapolated to injections/s over all views."""
+    import oracle as O
+    from paper_2606_21791_gb300 import synth as S
+    cores = O.max_threads()
+    nvar = variants or cores
+    cam = np.array(cams[0:1], copy=True)
+    full_px = int(cams[0]["width"]) * int(cams[0]["height"])
+    if crop:
+        w, h = crop
+        cam["cx"] -= (int(cam["width"][0]) - w) / 2.0
+        cam["cy"] -= (int(cam["height"][0]) - h) / 2.0
+        cam["width"], cam["height"] = w, h
+    px = int(cam["width"][0]) * int(cam["height"][0])
+    t0 = time.perf_counter()
+    clean = [O.render(scene.planes, scene.fmt, scene.sh_degree, cam[0])]
+    t_clean = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.campaign(scene.planes, scene.fmt, scene.sh_degree, cam, flips[:nvar], clean_imgs=clean, nthreads=cores)
+    t = time.perf_counter() - t0
+    frac = px / (full_px * len(cams))
+    value = nvar * frac / t
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nvar} upsets x 1 of {len(cams)} views ({cam['width'][0]}x{cam['height'][0]} px), "
+                      f"{t:.1f} s on {cores} threads (OpenMP over upsets); extrapolated linearly in pixels "
+                      f"to all views; clean render {t_clean:.1f} s untimed"}
+
+
+def run_reference(args):
+    rank, local, world = dist_info()
+    if rank != 0:
+        return
+    from paper_2606_21791_gb300 import synth as S
+    import oracle as O
+    O.build()
+    scene, cams, flips = S.scale_workload()
+    cores = O.max_threads()
+    crop = (400, 260)
+    K, W = args.steps, args.warmup
+    times = []
+    for i in range(W + K):
+        sl = flips[(i * cores) % (len(flips) - cores):][:cores]
+        t0 = time.perf_counter()
+        cam = np.array(cams[0:1], copy=True)
+        cam["cx"] -= (int(cam["width"][0]) - crop[0]) / 2.0
+        cam["cy"] -= (int(cam["height"][0]) - crop[1]) / 2.0
+        cam["width"], cam["height"] = crop
+        if i == 0:
+            clean = [O.render(scene.planes, scene.fmt, scene.sh_degree, cam[0])]
+            t0 = time.perf_counter()
+        O.campaign(scene.planes, scene.fmt, scene.sh_degree, cam, sl, clean_imgs=clean, nthreads=cores)
+        if i >= W:
+            times.append(time.perf_counter() - t0)
+    frac = crop[0] * crop[1] / (1600 * 1040 * len(cams))
+    total = sum(times)
+    value = K * cores * frac / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": W,
+            "ms_per_step": 1000 * total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD if scene.n == 2_000_000 else f"profiling case: {scene.n} Gaussians, otherwise "
+                                                                      + WORKLOAD, "gaussians": scene.n, "views": len(cams), "resolution": "1600x1040"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step {cores} upsets x view 0 crop {crop[0]}x{crop[1]} (OpenMP over "
+                                       f"upsets), extrapolated linearly in pixels to 4 full views"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2606_21791_gb300 as P
+    P.build()
+    from paper_2606_21791_gb300 import gs as G
+    from paper_2606_21791_gb300 import synth as S
+
+    rank, local, world = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pk, pk_kind = peaks()
+
+    t_setup = time.perf_counter()
+    scene, cams, flips = S.scale_workload(n=args.gaussians)
+    K_views = len(cams)
+    Wd, Hd = int(cams[0]["width"]), int(cams[0]["height"])
+    h = G.gs_load_scene(scene.planes, scene.n, scene.sh_degree, scene.fmt)
+    G.gs_set_views(h, cams)
+    mask = S.GUARD_WORDS_DEFAULT
+    # each rank takes its own slice of the upset list (independent units, no collective)
+    d_flips = G.to_device(flips, dev)
+    nflips = len(flips)
+    B, us_per = G.gs_autotune(h, d_flips, 1024, G.GS_GUARD_OFF, mask)
+    log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned batch B={B} ({us_per:.1f} us/variant)")
+
+    out = G.device_bytes(B * K_views * 24, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def flips_at(i):
+        off = ((i * world + rank) * B) % (nflips - B)
+        return d_flips[off * 8:(off + B) * 8]
+
+    def step(i):
+        G.gs_inject_and_render(h, flips_at(i), B, 1, G.GS_GUARD_OFF, mask, out)
+
+    # work per step (untimed pass with counters on; the engine is deterministic)
+    G.gs_count_work(h, True)
+    for i in range(args.warmup, args.warmup + args.steps):
+        step(i)
+    work = G.gs_read_work(h)
+    G.gs_count_work(h, False)
+
+    G.gs_time_kernels(h, True)
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
+        wall0 = time.perf_counter()
+        for j in range(args.steps):
+            flush.zero_()
+            ev[j][0].record(stream)
+            step(args.warmup + j)
+            ev[j][1].record(stream)
+            kern_ms.append(G.gs_read_kernel_ms(h))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        torch.cuda.nvtx.range_pop()
+        if world > 1:
+            torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    G.gs_time_kernels(h, False)
+    t_total = sum(step_ms) / 1000.0
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    inj = B * args.steps * world
+    value = inj / t_total
+    lat = sorted(step_ms)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    host_flips = torch.from_numpy(flips.view(np.uint8).copy()).pin_memory()
+    host_out = torch.empty(B * K_views * 24, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(B * 8, dtype=torch.uint8, device=dev)
+    for i in range(2):
+        off = (i * B) % (nflips - B)
+        dbuf.copy_(host_flips[off * 8:(off + B) * 8], non_blocking=True)
+        G.gs_inject_and_render(h, dbuf, B, 1, G.GS_GUARD_OFF, mask, out)
+        host_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for j in range(args.steps):
+        off = (((args.warmup + j) * world + rank) * B) % (nflips - B)
+        dbuf.copy_(host_flips[off * 8:(off + B) * 8], non_blocking=True)
+        G.gs_inject_and_render(h, dbuf, B, 1, G.GS_GUARD_OFF, mask, out)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_t = time.perf_counter() - e0
+    e2e = {"value": B * args.steps * world / e2e_t, "unit": UNIT, "h2d_bytes_per_step": B * 8,
+           "d2h_bytes_per_step": B * K_views * 24,
+           "how": "per step: pinned host flips -> device, gs_inject_and_render, records -> pinned host, sync"}
+
+    # plain loop: one variant per launch, full preprocess + sort + blend + compare, no graphs
+    nplain = 16
+    G.gs_inject_and_render_full(h, d_flips[:8 * 2], 2, 1, G.GS_GUARD_OFF, mask, out)
+    torch.cuda.synchronize()
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_out = G.device_bytes(nplain * K_views * 24, dev)
+    pe0.record(stream)
+    G.gs_inject_and_render_full(h, flips_at(args.warmup)[: 8 * nplain] if B >= nplain else d_flips[:8 * nplain],
+                                nplain, 1, G.GS_GUARD_OFF, mask, plain_out)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = pe0.elapsed_time(pe1) / 1000.0
+    plain = {"value": nplain / plain_s, "unit": UNIT, "sample": f"{nplain} upsets, {K_views} views each",
+             "mpix_s": nplain * K_views * Wd * Hd / plain_s / 1e6}
+
+    # roofline of the dominant kernel (dirty-tile blend): FP32-pipe bound
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    kavg = sum(kern_ms) / len(kern_ms) / 1000.0
+    evals_per_launch = work["evaluations"] / args.steps
+    achieved = evals_per_launch * FLOP_PER_EVAL / kavg / 1e12
+    tr = traffic_record()
+    traffic = float(tr["k_dirty_bytes_per_launch"]) if "k_dirty_bytes_per_launch" in tr else None
+    roofline = {"kernel": "k_dirty (dirty-tile blend + compare)", "bound": "alu", "achieved": achieved,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x median SM clock {sm_mhz:.0f} MHz under load",
+                "work_per_launch": {"evaluations": evals_per_launch, "flop_per_eval": FLOP_PER_EVAL,
+                                    "tiles": work["tiles"] / args.steps, "entries": work["entries"] / args.steps},
+                "kernel_ms_avg": kavg * 1000.0, "kernel_share_of_step": kavg * 1000.0 / (sum(step_ms) / len(step_ms))}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if scene.n == 2_000_000 else f"profiling case: {scene.n} Gaussians, otherwise "
+                                                                      + WORKLOAD, "gaussians": scene.n, "sh_degree": 3, "storage": "fp32",
+                   "resolution": f"{Wd}x{Hd}", "views": K_views, "batch": B, "upsets": nflips,
+                   "l2": "256 MB buffer written between timed steps (outside the step events)",
+                   "parallelism": f"replicas x{world}, upset list sharded"},
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "mpix_s_effective": value * K_views * Wd * Hd / 1e6,
+        "plain_loop": plain,
+        "speedup_vs_plain_loop": value / plain["value"],
+        "batch_latency_ms": {"p50": p50, "p99": p99, "what": f"one launch of {B} variants x {K_views} views"},
+        "wall_s_timed_region": wall,
+        "roofline": roofline,
+        "clocks": clocks,
+        "peaks": {"source": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
+    }
+    G.gs_free_scene(h)
+    del d_flips, flush
+    torch.cuda.empty_cache()
+
+    if not args.no_guard_stress:
+        line["guard"] = guard_stress(args, G, S, dev, pk, pk_kind)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(scene, cams, flips)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def guard_stress(args, G, S, dev, pk, pk_kind):
+    """Support-guard clamp (Algorithm 1) over a 66M-Gaussian SH-3 fp32 scene:
+    FIELD boxes (56 B/primitive read) and per-primitive boxes (168 B read)."""
+    import torch
+    n = args.guard_n
+    t0 = time.perf_counter()
+    planes = S.make_scene_torch(n, 3, S.FP32, S.SEED_BASE + 4, device=dev)
+    h = G.gs_load_scene(planes, n, 3, S.FP32)
+    lo, hi = S.prim_boxes_torch(planes, S.FP32, 14, S.SEED_BASE + 5)
+    del planes
+    torch.cuda.empty_cache()
+    G.gs_set_prim_box(h, lo, hi, 14)
+    del lo, hi
+    torch.cuda.empty_cache()
+    log(f"[bench] guard scene {n} ready in {time.perf_counter() - t0:.1f}s")
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {"gaussians": n, "words_guarded": 14, "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk_kind}
+    for mode, name, bytes_per in ((0, "field", 14 * 4), (1, "prim", 14 * 4 * 3)):
+        for _ in range(3):
+            G.gs_guard(h, mode, S.GUARD_WORDS_DEFAULT, cnt)
+        reps = 10
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.nvtx.range_push(f"guard_{name}")
+        for a, b in evs:
+            a.record(stream)
+            G.gs_guard(h, mode, S.GUARD_WORDS_DEFAULT, cnt)
+            b.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        t = statistics.median(ms) / 1000.0
+        gbs = n * bytes_per / t / 1e9
+        res[name] = {"ms": t * 1000, "gb_s": gbs, "frac": gbs / pk["hbm_gbs"], "bytes_per_launch": n * bytes_per,
+                     "clamps": int(cnt.item())}
+    G.gs_free_scene(h)
+    torch.cuda.empty_cache()
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,25 @@ GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_f
                                     int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
 /* Enable (default) or disable CUDA-graph replay of the batched dirty-tile step. */
 GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
+/* Work counters for measurement: while enabled, the blend kernels count
+ * pixel-primitive evaluations, tiles blended and list entries staged (graphs
+ * are bypassed).  gs_read_work copies [evaluations, tiles, entries] and
+ * resets them (synchronises). */
+GS_API gs_status gs_count_work(gs_scene* scene, int enable);
+GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
+/* Kernel timing for measurement: while enabled, CUDA events bracket the
+ * dirty-tile kernel of each batch on the caller's stream (also inside the
+ * captured graph); gs_read_kernel_ms returns the last batch's kernel time. */
+GS_API gs_status gs_time_kernels(gs_scene* scene, int enable);
+GS_API gs_status gs_read_kernel_ms(gs_scene* scene, float* ms);
+/* Variants per dirty-tile launch (0 = largest allowed, min(64, 1024 / K)). */
+GS_API gs_status gs_set_batch(gs_scene* scene, int batch);
+/* Autotuner: times the campaign over dev_flips[0, count) at batch sizes
+ * 8, 16, 32, 64 (those <= 1024 / K), keeps the fastest for this scene and
+ * returns it (and its time per variant in microseconds, may be NULL).
+ * Synchronises the stream. */
+GS_API gs_status gs_autotune(gs_scene* scene, const gs_flip* dev_flips, int count, int guard_mode, uint64_t word_mask,
+                             int* best_batch, float* best_us_per_variant, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points (for stage-isolated checks).
@@ -197,6 +216,62 @@ GS_API gs_status gs_bin_tiles(const float* dev_depth, const int32_t* dev_rects, 
                        void* stream);
 GS_API gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uint32_t* dev_offsets, const uint32_t* dev_ids,
                          int W, int H, float* dev_rgb, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop (continuous batching).  A server owns `slots` worker slots, each
+ * a CUDA stream with its own host thread and render scratch.  Scenes (owned by
+ * the caller, already loaded; campaign scenes with gs_set_views done) are
+ * registered with their resident device bytes, which must fit the HBM budget.
+ * Requests:
+ *   RENDER   render `cam` of the scene into dev_rgb (H*W*3 float32, may be
+ *            NULL); with guard_mode >= 0 the guard (Algorithm 1) is applied to
+ *            the resident scene first and its clamp count stored in *dev_clamps.
+ *   CAMPAIGN nflips single-flip variants through gs_inject_and_render;
+ *            dev_results gets nflips*K records.
+ *   STORM    one frame of an upset storm: the nflips upsets are XOR-ed into the
+ *            resident scene (they accumulate), then guard (if on) and render.
+ * A free slot takes the first queued request whose scene allows it (guarded
+ * renders and storm frames run alone on their scene; one campaign per scene)
+ * and whose render scratch fits the budget; so requests that arrive while
+ * others run are admitted as slots and memory free up, and run concurrently on
+ * separate streams.  A request larger than the budget left after the resident
+ * scenes is refused with GS_ERR_BUSY.  Device buffers in a request must stay
+ * valid until gs_server_wait returns for it.  Times are host milliseconds since
+ * the server was created; `arrival_ms` < 0 means "now".
+ * ------------------------------------------------------------------------- */
+typedef struct gs_server gs_server;
+typedef enum { GS_REQ_RENDER = 0, GS_REQ_CAMPAIGN = 1, GS_REQ_STORM = 2 } gs_req_kind;
+typedef struct {
+    int32_t kind;
+    int32_t scene;
+    gs_camera cam;
+    int32_t guard_mode;
+    int32_t nflips;
+    uint64_t word_mask;
+    const gs_flip* dev_flips;
+    float* dev_rgb;
+    gs_result* dev_results;
+    uint64_t* dev_clamps;
+} gs_request;
+typedef struct {
+    uint64_t ticket;
+    int32_t status;   /* gs_status of the finished request */
+    int32_t slot;
+    double t_submit_ms, t_start_ms, t_done_ms;
+} gs_response;
+
+GS_API gs_status gs_server_create(uint64_t hbm_budget_bytes, int slots, gs_server** out);
+GS_API gs_status gs_server_add_scene(gs_server* server, gs_scene* scene, int* scene_id);
+GS_API gs_status gs_server_submit(gs_server* server, const gs_request* req, double arrival_ms, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a request; GS_ERR_TIMEOUT if not done
+ * (the ticket stays valid).  On return the ticket is released. */
+GS_API gs_status gs_server_wait(gs_server* server, uint64_t ticket, int timeout_ms, gs_response* out);
+/* Remove a request that has not started (GS_ERR_BUSY once it has). */
+GS_API gs_status gs_server_cancel(gs_server* server, uint64_t ticket);
+/* [budget, resident bytes, scratch bytes held, queued, completed] */
+GS_API gs_status gs_server_stats(gs_server* server, uint64_t* host_stats);
+/* Finishes every queued request, then stops the workers. */
+GS_API gs_status gs_server_destroy(gs_server* server);
 
 #ifdef __cplusplus
 }

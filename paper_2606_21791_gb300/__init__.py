@@ -11,5 +11,5 @@ __all__ = ["synth", "gs", "build"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .buildlib import build as _b
     return _b(force=force)

@@ -25,7 +25,7 @@ gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* of
                                    cudaStream_t st);
 gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             CmpAcc* acc, unsigned int* queue, cudaStream_t st);
+                             CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st);
 size_t view_ptrs_size();
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const float* clean,
                     int W, int H);
@@ -167,13 +167,16 @@ gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaS
     int K = s->K;
     GS_TRY(launch_inject_prep(s, s->dev_cams, K, s->flip_stage, B, guard_mode, mask,
                               (const uint2* const*)s->dev_clean_rects, s->desc, s->item_off, s->acc, s->queue, st));
-    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->acc, s->queue, st));
+    // external records: inside a stream capture they become event-record nodes of the graph
+    if (s->ev_k0) GS_CUDA(cudaEventRecordWithFlags(s->ev_k0, st, cudaEventRecordExternal));
+    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->acc, s->queue, s->work_ctr, st));
+    if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
     GS_TRY(launch_finalize(s->acc, B * K, s->res_stage, st));
     return GS_OK;
 }
 
 gs_status run_dirty_batch(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaStream_t st) {
-    if (!s->use_graphs) return enqueue_dirty(s, B, guard_mode, mask, st);
+    if (!s->use_graphs || s->work_ctr) return enqueue_dirty(s, B, guard_mode, mask, st);
     GraphEntry* ge = nullptr;
     for (auto& g : s->graphs)
         if (g.B == B && g.guard == guard_mode && g.mask == mask) ge = &g;
@@ -211,6 +214,12 @@ gs_status run_dirty_batch(gs_scene* s, int B, int guard_mode, uint64_t mask, cud
 }
 
 }  // namespace
+
+gs_status render_lists_sized_ext(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, uint64_t* npairs,
+                                 cudaStream_t st) {
+    return render_lists_sized(s, w, cam, ids, npairs, st);
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -299,6 +308,9 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->res_stage);
     cudaFree(s->queue);
     cudaFree(s->saved);
+    cudaFree(s->work_ctr);
+    if (s->ev_k0) cudaEventDestroy(s->ev_k0);
+    if (s->ev_k1) cudaEventDestroy(s->ev_k1);
     delete s;
     return GS_OK;
 }
@@ -469,7 +481,8 @@ gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int
         return gs_inject_and_render_full(s, dev_flips, B, flips_per_variant, guard_mode, word_mask, dev_out, stream);
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
-    const int chunk = std::max(1, std::min(64, 1024 / K));
+    const int max_chunk = std::max(1, std::min(64, 1024 / K));
+    const int chunk = s->batch > 0 ? std::min(s->batch, max_chunk) : max_chunk;
     GS_TRY(ensure_batch_buffers(s, chunk, 1));
     for (int b0 = 0; b0 < B; b0 += chunk) {
         int nb = std::min(chunk, B - b0);
@@ -505,7 +518,8 @@ gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B
             const ViewState& v = s->views[k];
             uint32_t* ids = nullptr;
             GS_TRY(render_lists(s, s->work, v.cam, &ids, st));
-            GS_TRY(launch_blend_compare(s->work.recs, ids, s->work.ranges, v.cam.W, v.cam.H, v.clean, s->acc + k, st));
+            GS_TRY(launch_blend_compare(s->work.recs, ids, s->work.ranges, v.cam.W, v.cam.H, v.clean, s->acc + k,
+                                        s->work_ctr, st));
         }
         GS_TRY(launch_restore_sites(s->planes, s->fmt, s->n, f, fpv, s->saved, st));
         GS_TRY(launch_finalize(s->acc, K, dev_out + (size_t)b * K, st));
@@ -573,6 +587,102 @@ gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uint32_t* 
     cudaFreeAsync(recs, st);
     cudaFreeAsync(ranges, st);
     return rs;
+}
+
+gs_status gs_set_batch(gs_scene* s, int batch) {
+    if (!s || batch < 0) return set_error(GS_ERR_ARG, "bad gs_set_batch arguments");
+    s->batch = batch;
+    return GS_OK;
+}
+
+gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guard_mode, uint64_t word_mask,
+                      int* best_batch, float* best_us_per_variant, void* stream) {
+    GS_TRY(check_flip_args(s, dev_flips, count, 1, guard_mode, word_mask));
+    if (count < 1 || !best_batch) return set_error(GS_ERR_ARG, "bad gs_autotune arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = s->K;
+    const int max_chunk = std::max(1, std::min(64, 1024 / K));
+    const int cands[4] = {8, 16, 32, 64};
+    gs_result* out = nullptr;
+    GS_CUDA(cudaMallocAsync((void**)&out, sizeof(gs_result) * (size_t)count * K, st));
+    cudaEvent_t e0, e1;
+    GS_CUDA(cudaEventCreate(&e0));
+    GS_CUDA(cudaEventCreate(&e1));
+    int best = max_chunk;
+    float best_t = 1e30f;
+    gs_status rs = GS_OK;
+    for (int c : cands) {
+        if (c > max_chunk) break;
+        s->batch = c;
+        // warm (graph capture), then time the whole list at this batch size
+        int warm = std::min(count, c);
+        rs = gs_inject_and_render(s, dev_flips, warm, 1, guard_mode, word_mask, out, stream);
+        if (rs != GS_OK) break;
+        cudaEventRecord(e0, st);
+        rs = gs_inject_and_render(s, dev_flips, count, 1, guard_mode, word_mask, out, stream);
+        cudaEventRecord(e1, st);
+        if (rs != GS_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        float per = ms * 1000.0f / count;
+        if (per < best_t) {
+            best_t = per;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    if (rs != GS_OK) return rs;
+    s->batch = best;
+    *best_batch = best;
+    if (best_us_per_variant) *best_us_per_variant = best_t;
+    return GS_OK;
+}
+
+gs_status gs_count_work(gs_scene* s, int enable) {
+    if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
+    if (enable && !s->work_ctr) {
+        GS_TRY(dmalloc((void**)&s->work_ctr, sizeof(unsigned long long) * 4));
+        GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 4));
+    }
+    if (!enable && s->work_ctr) {
+        cudaFree(s->work_ctr);
+        s->work_ctr = nullptr;
+    }
+    return GS_OK;
+}
+
+gs_status gs_read_work(gs_scene* s, uint64_t* host_counts) {
+    if (!s || !host_counts) return set_error(GS_ERR_ARG, "NULL argument");
+    if (!s->work_ctr) return set_error(GS_ERR_STATE, "work counting is off");
+    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 4));
+    return GS_OK;
+}
+
+gs_status gs_time_kernels(gs_scene* s, int enable) {
+    if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
+    destroy_graphs(s);   // the event records are part of the captured graph
+    if (enable && !s->ev_k0) {
+        GS_CUDA(cudaEventCreate(&s->ev_k0));
+        GS_CUDA(cudaEventCreate(&s->ev_k1));
+    }
+    if (!enable && s->ev_k0) {
+        cudaEventDestroy(s->ev_k0);
+        cudaEventDestroy(s->ev_k1);
+        s->ev_k0 = s->ev_k1 = nullptr;
+    }
+    return GS_OK;
+}
+
+gs_status gs_read_kernel_ms(gs_scene* s, float* ms) {
+    if (!s || !ms) return set_error(GS_ERR_ARG, "NULL argument");
+    if (!s->ev_k0) return set_error(GS_ERR_STATE, "kernel timing is off");
+    GS_CUDA(cudaEventSynchronize(s->ev_k1));
+    GS_CUDA(cudaEventElapsedTime(ms, s->ev_k0, s->ev_k1));
+    return GS_OK;
 }
 
 gs_status gs_set_graphs(gs_scene* s, int enable) {

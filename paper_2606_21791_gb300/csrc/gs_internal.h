@@ -162,6 +162,10 @@ struct gs_scene {
     unsigned int* queue = nullptr;
     uint32_t* saved = nullptr;
     bool use_graphs = true;
+    int batch = 0;                          // variants per dirty-tile launch (0: default)
+    unsigned long long* work_ctr = nullptr; // work counters, non-NULL while counting is on (no graphs then)
+    cudaEvent_t ev_k0 = nullptr;            // bracket the dirty-tile kernel of the last batch (timing on)
+    cudaEvent_t ev_k1 = nullptr;
     std::vector<gs::GraphEntry> graphs;
 };
 
@@ -189,7 +193,7 @@ gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_
 gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
                              float* img, cudaStream_t st);
 gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
-                               const float* clean, CmpAcc* acc, cudaStream_t st);
+                               const float* clean, CmpAcc* acc, unsigned long long* work, cudaStream_t st);
 gs_status launch_compare(const float* a, const float* b, int H, int W, CmpAcc* acc, cudaStream_t st);
 gs_status launch_finalize(const CmpAcc* acc, int count, gs_result* out, cudaStream_t st);
 gs_status launch_records_to_blend(const gs_record* in, uint64_t n, BlendRec* out, cudaStream_t st);

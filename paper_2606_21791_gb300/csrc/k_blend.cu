@@ -95,7 +95,10 @@ __device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int W, int H) 
     return g;
 }
 
-__device__ __forceinline__ void blend_batch(const Stage& s, int cnt, const PixGeo& g, Pix& p) {
+// Work counters (measurement builds of the kernels only): [0] pixel-primitive
+// evaluations, [1] tiles blended, [2] list entries staged.
+template <bool COUNT>
+__device__ __forceinline__ void blend_batch(const Stage& s, int cnt, const PixGeo& g, Pix& p, unsigned int& nev) {
     if (__all_sync(0xffffffffu, p.done)) return;
     for (int j = 0; j < cnt; j++) {
         // warp-uniform cull against the conservative alpha box (NaN never culls)
@@ -104,6 +107,7 @@ __device__ __forceinline__ void blend_batch(const Stage& s, int cnt, const PixGe
         const float my = s.my[j], ey = s.ey[j];
         if (my + ey < g.wy0 || my - ey > g.wy1) continue;
         if (p.done) continue;
+        if (COUNT) nev++;
         const float dx = mx - g.pxc, dy = my - g.pyc;
         const float power = -0.5f * (s.ca[j] * dx * dx + s.cc[j] * dy * dy) - s.cb[j] * dx * dy;
         if (power > 0.0f) continue;
@@ -166,24 +170,36 @@ __device__ __forceinline__ void compare_tile(const PixGeo& g, float v0, float v1
     }
 }
 
-template <int MODE>   // 0: write the image, 1: compare with the clean image
+__device__ __forceinline__ void add_work(unsigned long long* work, unsigned int nev, unsigned int staged) {
+    unsigned int w = __reduce_add_sync(0xffffffffu, nev);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&work[0], (unsigned long long)w);
+    if (threadIdx.x == 0) {
+        atomicAdd(&work[1], 1ull);
+        atomicAdd(&work[2], (unsigned long long)staged);
+    }
+}
+
+template <int MODE, bool COUNT>   // MODE 0: write the image, 1: compare with the clean image
 __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
                                                    const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                    float* __restrict__ img, const float* __restrict__ clean,
-                                                   CmpAcc* acc) {
+                                                   CmpAcc* acc, unsigned long long* work) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
     const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
     Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside};
     const uint2 rg = ranges[tile];
+    unsigned int nev = 0, staged = 0;
     for (uint32_t base = rg.x; base < rg.y; base += kBT) {
         int cnt = (int)min((uint32_t)kBT, rg.y - base);
         __syncthreads();
         if ((int)threadIdx.x < cnt) stage_put(s, threadIdx.x, load_rec(recs, ids[base + threadIdx.x]));
         __syncthreads();
-        blend_batch(s, cnt, g, p);
+        staged += cnt;
+        blend_batch<COUNT>(s, cnt, g, p, nev);
         if (__syncthreads_count(p.done) == kBT) break;
     }
+    if (COUNT) add_work(work, nev, staged);
     const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
     if (MODE == 0) {
         if (g.inside) {
@@ -245,9 +261,11 @@ __device__ __forceinline__ bool key_less(float dj, uint32_t ij, float d, uint32_
     return dj < d || (dj == d && ij < p);
 }
 
+template <bool COUNT>
 __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
                                               const uint32_t* __restrict__ item_off, int BK, int K,
-                                              CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue) {
+                                              CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
+                                              unsigned long long* work) {
     __shared__ Stage s;
     __shared__ BlendRec nrec;
     __shared__ int sh_item_ok, sh_bk, sh_tx, sh_ty, sh_has_old, sh_has_new;
@@ -341,6 +359,7 @@ __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ view
         const bool has_old = sh_has_old, has_new = sh_has_new;
         const uint32_t L = (sh_e - sh_s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside};
+        unsigned int nev = 0, staged = 0;
         for (uint32_t base = 0; base < L; base += kBT) {
             int cnt = (int)min((uint32_t)kBT, L - base);
             __syncthreads();
@@ -355,9 +374,11 @@ __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ view
                 }
             }
             __syncthreads();
-            blend_batch(s, cnt, g, p);
+            staged += cnt;
+            blend_batch<COUNT>(s, cnt, g, p, nev);
             if (__syncthreads_count(p.done) == kBT) break;
         }
+        if (COUNT) add_work(work, nev, staged);
         const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
         compare_tile(g, v0, v1, v2, v.clean, v.W, &acc[bk]);
         __syncthreads();
@@ -396,16 +417,19 @@ gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const ui
                              cudaStream_t st) {
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
-    k_blend_full<0><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr);
+    k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
 gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
-                               const float* clean, CmpAcc* acc, cudaStream_t st) {
+                               const float* clean, CmpAcc* acc, unsigned long long* work, cudaStream_t st) {
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
-    k_blend_full<1><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc);
+    if (work)
+        k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work);
+    else
+        k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -436,7 +460,7 @@ int dirty_grid() {
     static int blocks = 0;
     if (!blocks) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dirty, kBT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dirty<false>, kBT, 0);
         if (per_sm < 1) per_sm = 1;
         blocks = per_sm * num_sms();
     }
@@ -444,8 +468,12 @@ int dirty_grid() {
 }
 
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             CmpAcc* acc, unsigned int* queue, cudaStream_t st) {
-    k_dirty<<<dirty_grid(), kBT, 0, st>>>((const ViewPtrs*)dev_views, desc, item_off, BK, K, acc, queue);
+                             CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st) {
+    if (work)
+        k_dirty<true><<<dirty_grid(), kBT, 0, st>>>((const ViewPtrs*)dev_views, desc, item_off, BK, K, acc, queue, work);
+    else
+        k_dirty<false><<<dirty_grid(), kBT, 0, st>>>((const ViewPtrs*)dev_views, desc, item_off, BK, K, acc, queue,
+                                                     nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

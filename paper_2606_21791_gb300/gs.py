@@ -58,10 +58,31 @@ SIGNATURES = {
     "gs_inject_and_render": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_inject_and_render_full": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_set_graphs": (_i32, [_vp, _i32]),
+    "gs_set_batch": (_i32, [_vp, _i32]),
+    "gs_count_work": (_i32, [_vp, _i32]),
+    "gs_time_kernels": (_i32, [_vp, _i32]),
+    "gs_read_kernel_ms": (_i32, [_vp, _vp]),
+    "gs_read_work": (_i32, [_vp, _vp]),
+    "gs_autotune": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp]),
     "gs_preprocess": (_i32, [_vp, _vp, _vp, _vp]),
     "gs_bin_tiles": (_i32, [_vp, _vp, _u64, _i32, _i32, _vp, _vp, _u64, _vp, _vp]),
     "gs_blend_lists": (_i32, [_vp, _u64, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "gs_server_create": (_i32, [_u64, _i32, C.POINTER(_vp)]),
+    "gs_server_add_scene": (_i32, [_vp, _vp, _vp]),
+    "gs_server_submit": (_i32, [_vp, _vp, C.c_double, _vp]),
+    "gs_server_wait": (_i32, [_vp, _u64, _i32, _vp]),
+    "gs_server_cancel": (_i32, [_vp, _u64]),
+    "gs_server_stats": (_i32, [_vp, _vp]),
+    "gs_server_destroy": (_i32, [_vp]),
 }
+
+GS_REQ_RENDER, GS_REQ_CAMPAIGN, GS_REQ_STORM = 0, 1, 2
+REQUEST_DTYPE = np.dtype([("kind", "<i4"), ("scene", "<i4"), ("cam", CAMERA_DTYPE), ("guard_mode", "<i4"),
+                          ("nflips", "<i4"), ("word_mask", "<u8"), ("dev_flips", "<u8"), ("dev_rgb", "<u8"),
+                          ("dev_results", "<u8"), ("dev_clamps", "<u8")])
+RESPONSE_DTYPE = np.dtype([("ticket", "<u8"), ("status", "<i4"), ("slot", "<i4"), ("t_submit_ms", "<f8"),
+                           ("t_start_ms", "<f8"), ("t_done_ms", "<f8")])
+assert REQUEST_DTYPE.itemsize == 136 and RESPONSE_DTYPE.itemsize == 40
 
 _lock = threading.Lock()
 _lib = None
@@ -225,6 +246,38 @@ def gs_set_graphs(scene, enable: bool):
     _check(load_library().gs_set_graphs(scene, int(bool(enable))), "gs_set_graphs")
 
 
+def gs_count_work(scene, enable: bool):
+    _check(load_library().gs_count_work(scene, int(bool(enable))), "gs_count_work")
+
+
+def gs_read_work(scene):
+    c = np.zeros(3, dtype=np.uint64)
+    _check(load_library().gs_read_work(scene, _ptr(c)), "gs_read_work")
+    return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2])}
+
+
+def gs_time_kernels(scene, enable: bool):
+    _check(load_library().gs_time_kernels(scene, int(bool(enable))), "gs_time_kernels")
+
+
+def gs_read_kernel_ms(scene) -> float:
+    ms = C.c_float()
+    _check(load_library().gs_read_kernel_ms(scene, C.byref(ms)), "gs_read_kernel_ms")
+    return ms.value
+
+
+def gs_set_batch(scene, batch: int):
+    _check(load_library().gs_set_batch(scene, batch), "gs_set_batch")
+
+
+def gs_autotune(scene, dev_flips, count: int, guard_mode: int, word_mask: int, stream=None):
+    b = C.c_int()
+    us = C.c_float()
+    _check(load_library().gs_autotune(scene, _ptr(dev_flips), count, guard_mode, word_mask, C.byref(b), C.byref(us),
+                                      _stream(stream)), "gs_autotune")
+    return b.value, us.value
+
+
 def gs_preprocess(scene, cam, dev_out, stream=None):
     c = _cams(cam)
     _check(load_library().gs_preprocess(scene, _ptr(c), _ptr(dev_out), _stream(stream)), "gs_preprocess")
@@ -241,6 +294,56 @@ def gs_bin_tiles(dev_depth, dev_rects, n: int, tiles_x: int, tiles_y: int, dev_o
 def gs_blend_lists(dev_recs, n: int, dev_offsets, dev_ids, W: int, H: int, dev_rgb, stream=None):
     _check(load_library().gs_blend_lists(_ptr(dev_recs), n, _ptr(dev_offsets), _ptr(dev_ids), W, H, _ptr(dev_rgb),
                                          _stream(stream)), "gs_blend_lists")
+
+
+def gs_server_create(hbm_budget_bytes: int, slots: int):
+    h = C.c_void_p()
+    _check(load_library().gs_server_create(hbm_budget_bytes, slots, C.byref(h)), "gs_server_create")
+    return h.value
+
+
+def gs_server_add_scene(server, scene) -> int:
+    sid = np.zeros(1, dtype=np.int32)
+    _check(load_library().gs_server_add_scene(server, scene, _ptr(sid)), "gs_server_add_scene")
+    return int(sid[0])
+
+
+def make_request(kind: int, scene: int, cam=None, guard_mode: int = -1, word_mask: int = 0, dev_flips=None,
+                 nflips: int = 0, dev_rgb=None, dev_results=None, dev_clamps=None) -> np.ndarray:
+    r = np.zeros(1, dtype=REQUEST_DTYPE)
+    r["kind"], r["scene"], r["guard_mode"], r["nflips"], r["word_mask"] = kind, scene, guard_mode, nflips, word_mask
+    if cam is not None:
+        r["cam"] = np.asarray(cam, dtype=CAMERA_DTYPE)
+    for f, v in (("dev_flips", dev_flips), ("dev_rgb", dev_rgb), ("dev_results", dev_results),
+                 ("dev_clamps", dev_clamps)):
+        r[f] = _ptr(v) or 0
+    return r
+
+
+def gs_server_submit(server, request: np.ndarray, arrival_ms: float = -1.0) -> int:
+    t = np.zeros(1, dtype=np.uint64)
+    _check(load_library().gs_server_submit(server, _ptr(request), arrival_ms, _ptr(t)), "gs_server_submit")
+    return int(t[0])
+
+
+def gs_server_wait(server, ticket: int, timeout_ms: int = -1):
+    r = np.zeros(1, dtype=RESPONSE_DTYPE)
+    _check(load_library().gs_server_wait(server, ticket, timeout_ms, _ptr(r)), "gs_server_wait")
+    return r[0]
+
+
+def gs_server_cancel(server, ticket: int):
+    _check(load_library().gs_server_cancel(server, ticket), "gs_server_cancel")
+
+
+def gs_server_stats(server) -> dict:
+    st = np.zeros(5, dtype=np.uint64)
+    _check(load_library().gs_server_stats(server, _ptr(st)), "gs_server_stats")
+    return dict(zip(("budget", "resident", "scratch", "queued", "completed"), (int(x) for x in st)))
+
+
+def gs_server_destroy(server):
+    _check(load_library().gs_server_destroy(server), "gs_server_destroy")
 
 
 # ----------------------------------------------------------------------------

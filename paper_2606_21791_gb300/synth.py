@@ -358,6 +358,40 @@ def tiny_workload():
     return scene, cams, flips
 
 
+def scale_workload(n: int = 2_000_000, count: int = 20_000, width: int = 1600, height: int = 1040, views: int = 4):
+    """2,000,000 primitives in 4 clusters, SH degree 3, fp32, four 1600x1040 views
+    on a ring (90 deg apart, elevation 0), 20,000 upsets with 70% on bits 24-31 of
+    log-scale and opacity."""
+    scene = make_scene(n, 3, FP32, SEED_BASE + 2, layout="clusters")
+    cams = ring_cameras(views, width, height)
+    flips = flips_top_bits(count, scene.n, scene.nwords, SEED_BASE + 102)
+    return scene, cams, flips
+
+
+def prim_boxes_torch(planes, fmt: int, nbox_words: int, seed: int, width_frac: float = 0.2):
+    """Device version of ``prim_boxes`` for fp32 storage (multi-million-primitive
+    workloads): returns (lo, hi) int32 tensors [nbox_words, n] of storage bits."""
+    import torch
+    assert fmt == FP32
+    v = planes[:nbox_words].view(torch.float32)
+    g = torch.Generator(device=v.device)
+    g.manual_seed(seed)
+    lo = torch.empty_like(v)
+    hi = torch.empty_like(v)
+    for w in range(nbox_words):
+        x = v[w].double()
+        wdt = width_frac * (x.max() - x.min())
+        l64 = x - torch.rand(x.shape, generator=g, device=v.device, dtype=torch.float64) * wdt
+        h64 = x + torch.rand(x.shape, generator=g, device=v.device, dtype=torch.float64) * wdt
+        l32 = l64.float()
+        h32 = h64.float()
+        l32 = torch.where(l32.double() > l64, torch.nextafter(l32, torch.full_like(l32, -float("inf"))), l32)
+        h32 = torch.where(h32.double() < h64, torch.nextafter(h32, torch.full_like(h32, float("inf"))), h32)
+        lo[w] = l32
+        hi[w] = h32
+    return lo.view(torch.int32).contiguous(), hi.view(torch.int32).contiguous()
+
+
 def batching_workload(fmt: int, n: int = 134_826, count: int = 50_000):
     """134,826 primitives in 4 clusters, SH degree 3, one 800x800 view, campaign
     stratified over all 59 words and every bit of the format."""
