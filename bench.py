@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-guard-stress", action="store_true", help="skip the 66M-Gaussian guard measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--guard-n", type=int, default=66_000_000)
+    ap.add_argument("--only-guard", action="store_true", help="run only the guard measurement (profiling)")
     ap.add_argument("--gaussians", type=int, default=2_000_000,
                     help="scene size (the 2M default is the benchmark; smaller only for profiling captures)")
     return ap.parse_args()
@@ -227,6 +228,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     pk, pk_kind = peaks()
+    if args.only_guard:
+        print(json.dumps({"guard": guard_stress(args, G, S, dev, pk, pk_kind)}), flush=True)
+        return
 
     t_setup = time.perf_counter()
     scene, cams, flips = S.scale_workload(n=args.gaussians)

@@ -27,8 +27,11 @@ gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
                              CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st);
 size_t view_ptrs_size();
-void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const float* clean,
-                    int W, int H);
+void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
+                    const float* clean, const uint32_t* stop, int W, int H);
+gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+                                  float* img, uint32_t* stop, cudaStream_t st);
+gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_t n, uint32_t* dk, cudaStream_t st);
 gs_status launch_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges, cudaStream_t st);
 uint32_t key_to_bits(uint32_t key, int fmt);
 int dirty_grid();
@@ -112,8 +115,10 @@ void free_views(gs_scene* s) {
         cudaFree(v.recs);
         cudaFree(v.rects);
         cudaFree(v.ids);
+        cudaFree(v.dk);
         cudaFree(v.ranges);
         cudaFree(v.clean);
+        cudaFree(v.stop);
     }
     s->views.clear();
     s->K = 0;
@@ -434,15 +439,19 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
         GS_TRY(dmalloc((void**)&v.recs, sizeof(BlendRec) * std::max<uint64_t>(s->n, 1)));
         GS_TRY(dmalloc((void**)&v.rects, sizeof(uint2) * std::max<uint64_t>(s->n, 1)));
         GS_TRY(dmalloc((void**)&v.ids, sizeof(uint32_t) * std::max<uint64_t>(np, 1)));
+        GS_TRY(dmalloc((void**)&v.dk, sizeof(uint32_t) * std::max<uint64_t>(np, 1)));
         GS_TRY(dmalloc((void**)&v.ranges, sizeof(uint2) * ntiles));
         GS_TRY(dmalloc((void**)&v.clean, sizeof(float) * (size_t)v.cam.W * v.cam.H * 3));
+        GS_TRY(dmalloc((void**)&v.stop, sizeof(uint32_t) * (size_t)v.cam.W * v.cam.H));
         GS_CUDA(cudaMemcpyAsync(v.recs, s->work.recs, sizeof(BlendRec) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.rects, s->work.rects, sizeof(uint2) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ranges, s->work.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
-        GS_TRY(launch_blend_image(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, st));
+        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, st));
+        GS_TRY(launch_gather_depth(v.recs, v.ids, np, v.dk, st));
         v.npairs = np;
-        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.ranges, v.clean, v.cam.W, v.cam.H);
+        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.dk, v.ranges, v.clean, v.stop, v.cam.W,
+                       v.cam.H);
         crects[k] = v.rects;
         max_pairs = std::max(max_pairs, np);
         max_tiles = std::max(max_tiles, ntiles);

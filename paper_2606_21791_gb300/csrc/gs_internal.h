@@ -90,8 +90,10 @@ struct ViewState {
     BlendRec* recs = nullptr;        // [n]
     uint2* rects = nullptr;          // [n] (x0 | y0 << 16, x1 | y1 << 16)
     uint32_t* ids = nullptr;         // [npairs] sorted tile lists
+    uint32_t* dk = nullptr;          // [npairs] depth bits of ids[j]
     uint2* ranges = nullptr;         // [ntiles] (start, end)
     float* clean = nullptr;          // [H*W*3]
+    uint32_t* stop = nullptr;        // [H*W] list index that stopped each clean pixel
     uint64_t npairs = 0;
     uint64_t cap_pairs = 0;
 };

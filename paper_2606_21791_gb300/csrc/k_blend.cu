@@ -28,22 +28,24 @@ namespace {
 
 constexpr int kBT = 256;
 
+// Shared staging of one batch of list entries.  box = conservative alpha box
+// (x0, x1, y0, y1); q0 = (mean x, mean y, A, B), q1 = (C, opacity, r, g), qb = b,
+// with the conic pre-scaled so that A dx^2 + C dy^2 + B dx dy is the exponent
+// in base 2: A = -ca log2(e) / 2, B = -cb log2(e), C = -cc log2(e) / 2.
 struct Stage {
-    float mx[kBT], my[kBT], ca[kBT], cb[kBT], cc[kBT], op[kBT], ex[kBT], ey[kBT], r[kBT], g[kBT], b[kBT];
+    float4 box[kBT];
+    float4 q0[kBT];
+    float4 q1[kBT];
+    float qb[kBT];
 };
 
+constexpr float kLog2e = 1.4426950408889634f;
+
 __device__ __forceinline__ void stage_put(Stage& s, int j, const BlendRec& q) {
-    s.mx[j] = q.mx;
-    s.my[j] = q.my;
-    s.ca[j] = q.ca;
-    s.cb[j] = q.cb;
-    s.cc[j] = q.cc;
-    s.op[j] = q.opac;
-    s.ex[j] = q.ex;
-    s.ey[j] = q.ey;
-    s.r[j] = q.r;
-    s.g[j] = q.g;
-    s.b[j] = q.b;
+    s.box[j] = make_float4(q.mx - q.ex, q.mx + q.ex, q.my - q.ey, q.my + q.ey);
+    s.q0[j] = make_float4(q.mx, q.my, q.ca * (-0.5f * kLog2e), q.cb * (-kLog2e));
+    s.q1[j] = make_float4(q.cc * (-0.5f * kLog2e), q.opac, q.r, q.g);
+    s.qb[j] = q.b;
 }
 
 __device__ __forceinline__ BlendRec load_rec(const BlendRec* recs, uint32_t id) {
@@ -68,6 +70,7 @@ __device__ __forceinline__ BlendRec load_rec(const BlendRec* recs, uint32_t id) 
 struct Pix {
     float T, c0, c1, c2;
     bool done;
+    uint32_t stop;   // list index of the entry that stopped the pixel (T would drop below 1e-4)
 };
 
 // Pixel geometry of thread `tid` in a tile: warp w covers an 8x4 block.
@@ -95,34 +98,58 @@ __device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int W, int H) 
     return g;
 }
 
+// 2^x (hardware approximation, flushes subnormal results to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Work counters (measurement builds of the kernels only): [0] pixel-primitive
 // evaluations, [1] tiles blended, [2] list entries staged.
-template <bool COUNT>
-__device__ __forceinline__ void blend_batch(const Stage& s, int cnt, const PixGeo& g, Pix& p, unsigned int& nev) {
-    if (__all_sync(0xffffffffu, p.done)) return;
-    for (int j = 0; j < cnt; j++) {
-        // warp-uniform cull against the conservative alpha box (NaN never culls)
-        const float mx = s.mx[j], ex = s.ex[j];
-        if (mx + ex < g.wx0 || mx - ex > g.wx1) continue;
-        const float my = s.my[j], ey = s.ey[j];
-        if (my + ey < g.wy0 || my - ey > g.wy1) continue;
-        if (p.done) continue;
-        if (COUNT) nev++;
-        const float dx = mx - g.pxc, dy = my - g.pyc;
-        const float power = -0.5f * (s.ca[j] * dx * dx + s.cc[j] * dy * dy) - s.cb[j] * dx * dy;
-        if (power > 0.0f) continue;
-        float alpha = s.op[j] * __expf(power);
-        if (alpha < 1.0f / 255.0f) continue;
-        if (alpha > 0.99f) alpha = 0.99f;
-        const float Tn = p.T * (1.0f - alpha);
-        if (Tn < 1e-4f) {
-            p.done = true;
-            continue;
+//
+// Each warp tests 32 staged entries at a time against its pixel block (one box
+// load per lane, a ballot), then walks only the survivors in list order.  An
+// entry culled here cannot reach alpha >= 1/255 at any of the warp's pixels, so
+// skipping it changes no pixel; a NaN box never culls.
+template <bool COUNT, bool TRACK>
+__device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t base, const PixGeo& g, Pix& p,
+                                            unsigned int& nev) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < cnt; c += 32) {
+        if (__all_sync(0xffffffffu, p.done)) return;
+        const int j = c + lane;
+        bool pass = false;
+        if (j < cnt) {
+            const float4 bx = s.box[j];
+            pass = !(bx.y < g.wx0 || bx.x > g.wx1 || bx.w < g.wy0 || bx.z > g.wy1);
         }
-        p.c0 = p.c0 + s.r[j] * alpha * p.T;
-        p.c1 = p.c1 + s.g[j] * alpha * p.T;
-        p.c2 = p.c2 + s.b[j] * alpha * p.T;
-        p.T = Tn;
+        unsigned m = __ballot_sync(0xffffffffu, pass);
+        while (m) {
+            const int e = c + __ffs(m) - 1;
+            m &= m - 1;
+            if (p.done) continue;
+            if (COUNT) nev++;
+            const float4 q0 = s.q0[e];
+            const float4 q1 = s.q1[e];
+            const float dx = q0.x - g.pxc, dy = q0.y - g.pyc;
+            const float e2 = dx * (q0.z * dx + q0.w * dy) + q1.x * dy * dy;   // power * log2(e)
+            if (e2 > 0.0f) continue;
+            float alpha = q1.y * ex2_approx(e2);
+            if (alpha < 1.0f / 255.0f) continue;
+            alpha = alpha > 0.99f ? 0.99f : alpha;     // keeps NaN
+            const float Tn = p.T * (1.0f - alpha);
+            if (Tn < 1e-4f) {
+                p.done = true;
+                if (TRACK) p.stop = base + (uint32_t)e;
+                continue;
+            }
+            const float w = alpha * p.T;
+            p.c0 = p.c0 + q1.z * w;
+            p.c1 = p.c1 + q1.w * w;
+            p.c2 = p.c2 + s.qb[e] * w;
+            p.T = Tn;
+        }
     }
 }
 
@@ -179,34 +206,39 @@ __device__ __forceinline__ void add_work(unsigned long long* work, unsigned int 
     }
 }
 
-template <int MODE, bool COUNT>   // MODE 0: write the image, 1: compare with the clean image
+// MODE 0: write the image; 1: compare with the clean image; 2: write the image
+// and each pixel's stop index (0xffffffff if it never stopped), which the
+// dirty-tile kernel uses to leave pixels that stopped before a change untouched.
+template <int MODE, bool COUNT>
 __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
                                                    const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                    float* __restrict__ img, const float* __restrict__ clean,
-                                                   CmpAcc* acc, unsigned long long* work) {
+                                                   CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
     const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
-    Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside};
+    Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, 0xffffffffu};
     const uint2 rg = ranges[tile];
     unsigned int nev = 0, staged = 0;
     for (uint32_t base = rg.x; base < rg.y; base += kBT) {
         int cnt = (int)min((uint32_t)kBT, rg.y - base);
-        __syncthreads();
         if ((int)threadIdx.x < cnt) stage_put(s, threadIdx.x, load_rec(recs, ids[base + threadIdx.x]));
         __syncthreads();
         staged += cnt;
-        blend_batch<COUNT>(s, cnt, g, p, nev);
+        blend_batch<COUNT, MODE == 2>(s, cnt, base - rg.x, g, p, nev);
+        // also the barrier that lets the next batch overwrite the stage
         if (__syncthreads_count(p.done) == kBT) break;
     }
     if (COUNT) add_work(work, nev, staged);
     const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
-    if (MODE == 0) {
+    if (MODE != 1) {
         if (g.inside) {
-            float* o = img + ((size_t)g.py * W + g.px) * 3;
+            const size_t px = (size_t)g.py * W + g.px;
+            float* o = img + px * 3;
             o[0] = v0;
             o[1] = v1;
             o[2] = v2;
+            if (MODE == 2) stop[px] = p.stop;
         }
     } else {
         compare_tile(g, v0, v1, v2, clean, W, acc);
@@ -251,43 +283,76 @@ __global__ void k_zero_acc(CmpAcc* acc, int count) {
 struct ViewPtrs {
     const BlendRec* recs;
     const uint32_t* ids;
+    const uint32_t* dk;      // depth bits of ids[j] (list-aligned)
     const uint2* ranges;
     const float* clean;
+    const uint32_t* stop;    // clean stop index of every pixel
     int W, H, tiles_x, pad;
 };
 
-// lexicographic (depth, id) < (d, p)
-__device__ __forceinline__ bool key_less(float dj, uint32_t ij, float d, uint32_t p) {
-    return dj < d || (dj == d && ij < p);
+// First index in [lo, hi) whose (depth bits, id) is not below (dkey, p); the
+// lists are sorted by (depth, id).  Called by a whole warp: each round probes 31
+// splitters and keeps the 1/32 of the interval that holds the answer.
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict__ dk, const uint32_t* __restrict__ ids,
+                                                     uint32_t lo, uint32_t hi, uint32_t dkey, uint32_t p) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const uint32_t len = hi - lo;
+        bool less = false;
+        if (lane < 31) {
+            const uint32_t pos = lo + (uint32_t)(((uint64_t)len * (uint32_t)(lane + 1)) >> 5);
+            const uint32_t k = dk[pos], id = ids[pos];
+            less = k < dkey || (k == dkey && id < p);
+        }
+        const int c = __popc(__ballot_sync(0xffffffffu, less));
+        const uint32_t nlo = c == 0 ? lo : lo + (uint32_t)(((uint64_t)len * (uint32_t)c) >> 5) + 1;
+        const uint32_t nhi = c == 31 ? hi : lo + (uint32_t)(((uint64_t)len * (uint32_t)(c + 1)) >> 5);
+        lo = nlo;
+        hi = nhi;
+    }
+    bool less = false;
+    const uint32_t pos = lo + lane;
+    if (pos < hi) {
+        const uint32_t k = dk[pos], id = ids[pos];
+        less = k < dkey || (k == dkey && id < p);
+    }
+    return lo + __popc(__ballot_sync(0xffffffffu, less));
 }
 
+constexpr int kMaxItems = 1025;   // B * K <= 1024 (variant, view) pairs + 1
+
 template <bool COUNT>
-__global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
+__global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
                                               const uint32_t* __restrict__ item_off, int BK, int K,
                                               CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
                                               unsigned long long* work) {
     __shared__ Stage s;
     __shared__ BlendRec nrec;
+    __shared__ uint32_t s_off[kMaxItems];
     __shared__ int sh_item_ok, sh_bk, sh_tx, sh_ty, sh_has_old, sh_has_new;
-    __shared__ uint32_t sh_s, sh_e, sh_pp, sh_ins;
-    const uint32_t total = item_off[BK];
+    __shared__ uint32_t sh_s, sh_e, sh_pp, sh_ins, sh_cut;
+    for (int i = threadIdx.x; i <= BK; i += kBT) s_off[i] = item_off[i];
+    __syncthreads();
+    const uint32_t total = s_off[BK];
+    const int lane = threadIdx.x & 31;
     while (true) {
-        if (threadIdx.x == 0) {
-            uint32_t item = atomicAdd(&queue[0], 1u);
-            sh_item_ok = item < total;
+        if (threadIdx.x < 32) {
+            uint32_t item = 0;
+            if (lane == 0) item = atomicAdd(&queue[0], 1u);
+            item = __shfl_sync(0xffffffffu, item, 0);
             if (item < total) {
-                // (variant, view) of this item: last bk with item_off[bk] <= item
+                // (variant, view) of this item: last bk with s_off[bk] <= item
                 int lo = 0, hi = BK - 1;
                 while (lo < hi) {
                     int mid = (lo + hi + 1) >> 1;
-                    if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+                    if (s_off[mid] <= item) lo = mid; else hi = mid - 1;
                 }
                 const int bk = lo;
                 const DirtyDesc& d = desc[bk];
-                uint32_t j = item - item_off[bk];
+                const uint32_t j = item - s_off[bk];
                 int tx = 0, ty = 0;
-                uint32_t wn = (uint32_t)d.nx1 - d.nx0;
-                uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
+                const uint32_t wn = (uint32_t)d.nx1 - d.nx0;
+                const uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
                 if (j < an) {
                     tx = d.nx0 + (int)(j % wn);
                     ty = d.ny0 + (int)(j / wn);
@@ -301,8 +366,8 @@ __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ view
                             ex1 = min((int)d.ox1, (int)d.nx1);
                             if (ex1 < ex0) ex1 = ex0;
                         }
-                        uint32_t left = (uint32_t)(ex0 - d.ox0);
-                        uint32_t row = (uint32_t)(d.ox1 - d.ox0) - (uint32_t)(ex1 - ex0);
+                        const uint32_t left = (uint32_t)(ex0 - d.ox0);
+                        const uint32_t row = (uint32_t)(d.ox1 - d.ox0) - (uint32_t)(ex1 - ex0);
                         if (r < row) {
                             ty = y;
                             tx = r < left ? d.ox0 + (int)r : ex1 + (int)(r - left);
@@ -311,44 +376,37 @@ __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ view
                         r -= row;
                     }
                 }
-                const int k = bk % K;
-                const ViewPtrs v = views[k];
+                const ViewPtrs v = views[bk % K];
                 const int tile = ty * v.tiles_x + tx;
                 const uint2 rg = v.ranges[tile];
                 const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
                 const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
-                uint32_t pp = 0, ins = 0;
+                uint32_t pp = 0, ins = 0, cut = 0xffffffffu;
                 if (has_old) {
-                    const float dold = v.recs[d.prim].depth;
-                    uint32_t a = rg.x, b = rg.y;
-                    while (a < b) {
-                        uint32_t m = (a + b) >> 1;
-                        uint32_t id = v.ids[m];
-                        if (key_less(v.recs[id].depth, id, dold, d.prim)) a = m + 1; else b = m;
-                    }
-                    pp = a - rg.x;
+                    pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(v.recs[d.prim].depth), d.prim) -
+                         rg.x;
+                    cut = pp;
                 }
                 if (has_new) {
-                    uint32_t a = rg.x, b = rg.y;
-                    while (a < b) {
-                        uint32_t m = (a + b) >> 1;
-                        uint32_t id = v.ids[m];
-                        if (key_less(v.recs[id].depth, id, d.rec.depth, d.prim)) a = m + 1; else b = m;
-                    }
-                    ins = a - rg.x;
+                    ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(d.rec.depth), d.prim) - rg.x;
+                    cut = min(cut, ins);   // clean-list position of the insertion
                     if (has_old && pp < ins) ins -= 1;
-                    nrec = d.rec;
                 }
-                sh_bk = bk;
-                sh_tx = tx;
-                sh_ty = ty;
-                sh_s = rg.x;
-                sh_e = rg.y;
-                sh_pp = pp;
-                sh_ins = ins;
-                sh_has_old = has_old;
-                sh_has_new = has_new;
+                if (lane == 0) {
+                    if (has_new) nrec = d.rec;
+                    sh_bk = bk;
+                    sh_tx = tx;
+                    sh_ty = ty;
+                    sh_s = rg.x;
+                    sh_e = rg.y;
+                    sh_pp = pp;
+                    sh_ins = ins;
+                    sh_cut = cut;
+                    sh_has_old = has_old;
+                    sh_has_new = has_new;
+                }
             }
+            if (lane == 0) sh_item_ok = item < total;
         }
         __syncthreads();
         if (!sh_item_ok) break;
@@ -358,11 +416,25 @@ __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ view
         const uint32_t s0 = sh_s, pp = sh_pp, ins = sh_ins;
         const bool has_old = sh_has_old, has_new = sh_has_new;
         const uint32_t L = (sh_e - sh_s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
-        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside};
+        // A pixel whose clean blend stopped before the first changed list position
+        // processes the same entries in the same order and stops at the same one:
+        // its value is the clean value, bit for bit.
+        bool same = false;
+        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+        if (g.inside) {
+            const size_t px = (size_t)g.py * v.W + g.px;
+            if (v.stop[px] < sh_cut) {
+                same = true;
+                c0 = v.clean[px * 3 + 0];
+                c1 = v.clean[px * 3 + 1];
+                c2 = v.clean[px * 3 + 2];
+            }
+        }
+        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside || same, 0u};
         unsigned int nev = 0, staged = 0;
-        for (uint32_t base = 0; base < L; base += kBT) {
+        const bool all_same = __syncthreads_count(p.done) == kBT;
+        for (uint32_t base = 0; base < L && !all_same; base += kBT) {
             int cnt = (int)min((uint32_t)kBT, L - base);
-            __syncthreads();
             if ((int)threadIdx.x < cnt) {
                 uint32_t m = base + threadIdx.x;
                 if (has_new && m == ins) {
@@ -375,11 +447,16 @@ __global__ __launch_bounds__(kBT) void k_dirty(const ViewPtrs* __restrict__ view
             }
             __syncthreads();
             staged += cnt;
-            blend_batch<COUNT>(s, cnt, g, p, nev);
+            blend_batch<COUNT, false>(s, cnt, base, g, p, nev);
             if (__syncthreads_count(p.done) == kBT) break;
         }
         if (COUNT) add_work(work, nev, staged);
-        const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
+        float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
+        if (same) {
+            v0 = c0;
+            v1 = c1;
+            v2 = c2;
+        }
         compare_tile(g, v0, v1, v2, v.clean, v.W, &acc[bk]);
         __syncthreads();
     }
@@ -406,6 +483,11 @@ __global__ void k_records_to_blend(const gs_record* in, uint64_t n, BlendRec* ou
     out[i] = q;
 }
 
+__global__ void k_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_t n, uint32_t* dk) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dk[i] = __float_as_uint(recs[ids[i]].depth);
+}
+
 __global__ void k_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < ntiles) ranges[t] = make_uint2(offsets[t], offsets[t + 1]);
@@ -417,7 +499,8 @@ gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const ui
                              cudaStream_t st) {
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
-    k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr);
+    k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr,
+                                                     nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -427,9 +510,19 @@ gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const 
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     if (work)
-        k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work);
+        k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work, nullptr);
     else
-        k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr);
+        k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr,
+                                                        nullptr);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+                                  float* img, uint32_t* stop, cudaStream_t st) {
+    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    if (tx * ty == 0) return GS_OK;
+    k_blend_full<2, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr, stop);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -480,13 +573,22 @@ gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const
 
 size_t view_ptrs_size() { return sizeof(ViewPtrs); }
 
-void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const float* clean,
-                    int W, int H) {
+gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_t n, uint32_t* dk, cudaStream_t st) {
+    if (n == 0) return GS_OK;
+    k_gather_depth<<<(unsigned)div_up(n, 256), 256, 0, st>>>(recs, ids, n, dk);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
+                    const float* clean, const uint32_t* stop, int W, int H) {
     ViewPtrs v;
     v.recs = recs;
     v.ids = ids;
+    v.dk = dk;
     v.ranges = ranges;
     v.clean = clean;
+    v.stop = stop;
     v.W = W;
     v.H = H;
     v.tiles_x = (W + kTile - 1) / kTile;
