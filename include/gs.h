@@ -155,6 +155,23 @@ GS_API gs_status gs_render(gs_scene* scene, const gs_camera* host_cams, int K, f
  * (clamps = 0).  dev_out: K records. */
 GS_API gs_status gs_compare(const float* dev_a, const float* dev_b, int H, int W, int K, gs_result* dev_out, void* stream);
 
+/* Allocation-free variant of gs_compare (the paper has no counterpart; it is a
+ * library convenience).  For callers that must not allocate device memory once
+ * they are running: flight and embedded renderers that forbid dynamic
+ * allocation after start-up, and processes whose allocator already owns all of
+ * HBM under a fixed budget.  gs_compare takes its accumulators from the stream-
+ * ordered allocator; this call instead uses one fixed device array of 64
+ * accumulators compiled into the library, so it allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  Inputs and outputs are
+ * as for gs_compare; K must be at most 64, otherwise GS_ERR_ARG.  The first call
+ * on a device looks up the array's device address for that device (make that
+ * first call before any stream capture).  Every call shares the one array, which
+ * keeps the last call's contents; each call clears what it uses first, but calls
+ * that overlap on the GPU (e.g. on two streams) race and must be serialised.
+ * Every GPU that loads the library holds the array (1.5 KB) until exit. */
+GS_API gs_status gs_compare_noalloc(const float* dev_a, const float* dev_b, int H, int W, int K, gs_result* dev_out,
+                                    void* stream);
+
 /* ---------------------------------------------------------------------------
  * Injection campaign (Sec. 3 "Parallel injection engine").
  * gs_set_views renders the clean frame of each view and keeps its state

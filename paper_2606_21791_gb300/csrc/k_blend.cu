@@ -20,6 +20,8 @@
 // items from an atomic queue.  A dirty tile is re-blended from the clean sorted
 // list with the flipped primitive's clean entry removed and its corrupted record
 // merged in at its (depth, index) position, and compared on the fly.
+#include <mutex>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -610,4 +612,54 @@ gs_status launch_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* r
     return GS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free comparison.  The per-image accumulators live in one fixed
+// device array instead of memory obtained at call time, for callers that may
+// not allocate (see gs_compare_noalloc in gs.h).  Every GPU that loads this
+// library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxImages = 64;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) CmpAcc g_noalloc_acc[kNoAllocMaxImages];
+
+namespace {
+std::mutex g_noalloc_mu;
+CmpAcc* g_noalloc_ptr[kNoAllocMaxDevices] = {};   // device address of the array, per device
+}  // namespace
+
+// Once per device, with that device current: the array's device address.  In
+// host code the array's name is only a host-side stand-in, so kernels are given
+// this address, never the name.
+static gs_status noalloc_scratch(CmpAcc** out) {
+    int dev = 0;
+    GS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(GS_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_acc);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-alloc comparison scratch)");
+        g_noalloc_ptr[dev] = (CmpAcc*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GS_OK;
+}
+
 }  // namespace gs
+
+extern "C" gs_status gs_compare_noalloc(const float* dev_a, const float* dev_b, int H, int W, int K,
+                                        gs_result* dev_out, void* stream) {
+    using namespace gs;
+    if (!dev_a || !dev_b || !dev_out || H < 1 || W < 1 || K < 1)
+        return set_error(GS_ERR_ARG, "bad gs_compare_noalloc arguments");
+    if (K > kNoAllocMaxImages)
+        return set_error(GS_ERR_ARG, "gs_compare_noalloc: at most 64 image pairs per call (fixed scratch size)");
+    CmpAcc* acc = nullptr;
+    GS_TRY(noalloc_scratch(&acc));
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's sums: clear the K accumulators first
+    GS_TRY(launch_zero_acc(acc, K, st));
+    const size_t img = (size_t)H * W * 3;
+    for (int k = 0; k < K; k++) GS_TRY(launch_compare(dev_a + k * img, dev_b + k * img, H, W, acc + k, st));
+    return launch_finalize(acc, K, dev_out, st);
+}

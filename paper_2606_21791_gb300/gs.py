@@ -53,6 +53,7 @@ SIGNATURES = {
     "gs_guard": (_i32, [_vp, _i32, _u64, _vp, _vp]),
     "gs_render": (_i32, [_vp, _vp, _i32, _vp, _vp]),
     "gs_compare": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "gs_compare_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "gs_set_views": (_i32, [_vp, _vp, _i32, _vp]),
     "gs_clean_image": (_i32, [_vp, _i32, _vp, _vp]),
     "gs_inject_and_render": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
@@ -218,6 +219,12 @@ def gs_render(scene, cams, dev_rgb, stream=None):
 
 def gs_compare(dev_a, dev_b, H: int, W: int, K: int, dev_out, stream=None):
     _check(load_library().gs_compare(_ptr(dev_a), _ptr(dev_b), H, W, K, _ptr(dev_out), _stream(stream)), "gs_compare")
+
+
+def gs_compare_noalloc(dev_a, dev_b, H: int, W: int, K: int, dev_out, stream=None):
+    """gs_compare without any device allocation (fixed 64-pair scratch in the library)."""
+    _check(load_library().gs_compare_noalloc(_ptr(dev_a), _ptr(dev_b), H, W, K, _ptr(dev_out), _stream(stream)),
+           "gs_compare_noalloc")
 
 
 def gs_set_views(scene, cams, stream=None):
