@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--guard-n", type=int, default=66_000_000)
     ap.add_argument("--only-guard", action="store_true", help="run only the guard measurement (profiling)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency measurement")
     ap.add_argument("--gaussians", type=int, default=2_000_000,
                     help="scene size (the 2M default is the benchmark; smaller only for profiling captures)")
     return ap.parse_args()
@@ -379,12 +380,176 @@ def main():
 
     if not args.no_guard_stress:
         line["guard"] = guard_stress(args, G, S, dev, pk, pk_kind)
+    if not args.no_serving:
+        line["serving"] = serving(args, G, S, dev)
+        st = line["serving"]["storm"]
+        line["p99_frame_latency_ms"] = {"storm_guard_on": st["guard_on"]["p99_ms"],
+                                        "storm_guard_off": st["guard_off"]["p99_ms"],
+                                        "poisson_80pct": line["serving"]["poisson"][1]["p99_ms"]}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(scene, cams, flips)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def serving(args, G, S, dev):
+    """Serving loop: 4 resident scenes (6,741 / 134,826 / 300,000 / 2,000,000
+    Gaussians, SH 3, fp16 storage), mixed 800x800 and 1600x1040 render requests
+    with Poisson arrivals at 50/80/95% of the measured capacity plus interleaved
+    1,000-upset campaigns, and an upset storm (1,000 upsets per frame, 300 frames)
+    on the largest scene with the guard on and off."""
+    import torch
+    rng = np.random.default_rng(S.SEED_BASE + 40)
+    sizes = (6_741, 134_826, 300_000, 2_000_000)
+    t0 = time.perf_counter()
+    scenes = [S.make_scene(n, 3, S.FP16, S.SEED_BASE + 41 + i, layout="clusters") for i, n in enumerate(sizes)]
+    handles = [G.gs_load_scene(sc.planes, sc.n, 3, S.FP16) for sc in scenes]
+    G.gs_set_views(handles[1], S.ring_cameras(1, 800, 800))          # campaign target
+    camp_flips = S.flips_stratified(1000, sizes[1], 59, S.FP16, S.SEED_BASE + 42)
+    d_camp = G.to_device(camp_flips, dev)
+    camp_out = G.device_bytes(1000 * 24, dev)
+    slots = 4
+    srv = G.gs_server_create(200 << 30, slots)
+    ids = [G.gs_server_add_scene(srv, h) for h in handles]
+    res = [(800, 800), (1600, 1040)]
+    pool = [torch.empty(1600 * 1040 * 3, dtype=torch.float32, device=dev) for _ in range(48)]
+
+    def make(i):
+        if i % 10 == 9:
+            return G.make_request(G.GS_REQ_CAMPAIGN, ids[1], dev_flips=d_camp, nflips=1000, dev_results=camp_out)
+        W, H = res[int(rng.integers(0, 2))]
+        cam = S.ring_cameras(1, W, H, elevation_deg=float(rng.uniform(-30, 30)))[0]
+        return G.make_request(G.GS_REQ_RENDER, ids[int(rng.integers(0, 4))], cam, dev_rgb=pool[i % len(pool)])
+
+    # warm every path (scratch growth, graph capture)
+    for i in range(12):
+        G.gs_server_wait(srv, G.gs_server_submit(srv, make(i)))
+    # capacity: closed loop, `slots` requests in flight
+    n_cap = 120
+    reqs = [make(i) for i in range(n_cap)]
+    c0 = time.perf_counter()
+    inflight = []
+    for i, r in enumerate(reqs):
+        inflight.append(G.gs_server_submit(srv, r))
+        if len(inflight) >= 2 * slots:
+            G.gs_server_wait(srv, inflight.pop(0))
+    for t in inflight:
+        G.gs_server_wait(srv, t)
+    cap_rps = n_cap / (time.perf_counter() - c0)
+    # open loop: Poisson arrivals at fractions of capacity; latency = arrival -> done
+    poisson = []
+    for load in (0.5, 0.8, 0.95):
+        rate = load * cap_rps
+        n = 150
+        gaps = rng.exponential(1.0 / rate, size=n)
+        reqs = [make(1000 + i) for i in range(n)]
+        tickets = []
+        start = time.perf_counter()
+        arrival = 0.0
+        base_ms = None
+        for i in range(n):
+            arrival += gaps[i]
+            while time.perf_counter() - start < arrival:
+                time.sleep(0.0002)
+            tickets.append(G.gs_server_submit(srv, reqs[i]))
+        lat = []
+        for t in tickets:
+            r = G.gs_server_wait(srv, t)
+            lat.append(r["t_done_ms"] - r["t_submit_ms"])
+        span = time.perf_counter() - start
+        poisson.append({"load": load, "offered_rps": rate, "throughput_rps": n / span,
+                        "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99), "mean_ms": sum(lat) / n})
+    G.gs_server_destroy(srv)
+    # upset storm on the largest scene: 1,000 upsets accumulate per frame
+    storm = {}
+    for guard in (1, 0):
+        h = G.gs_load_scene(scenes[3].planes, scenes[3].n, 3, S.FP16)
+        srv = G.gs_server_create(200 << 30, 1)
+        sid = G.gs_server_add_scene(srv, h)
+        cam = S.ring_cameras(1, 1600, 1040)[0]
+        img = torch.empty(1600 * 1040 * 3, dtype=torch.float32, device=dev)
+        frames = 300
+        fl = S.flips_multi(1000 * frames, scenes[3].n, 59, S.FP16, S.SEED_BASE + 43)
+        d_fl = G.to_device(fl, dev)
+        lat = []
+        for f in range(frames + 5):
+            fi = f % frames
+            r = G.make_request(G.GS_REQ_STORM, sid, cam, guard_mode=0 if guard else -1,
+                               word_mask=S.GUARD_WORDS_DEFAULT, dev_flips=d_fl[fi * 8000:(fi + 1) * 8000], nflips=1000,
+                               dev_rgb=img)
+            resp = G.gs_server_wait(srv, G.gs_server_submit(srv, r))
+            if f >= 5:
+                lat.append(resp["t_done_ms"] - resp["t_submit_ms"])
+        finite = bool(torch.isfinite(img).all().item())
+        G.gs_server_destroy(srv)
+        G.gs_free_scene(h)
+        storm["guard_on" if guard else "guard_off"] = {
+            "frames": frames, "upsets_per_frame": 1000, "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99),
+            "mean_ms": sum(lat) / len(lat), "last_frame_finite": finite}
+    for h in handles:
+        G.gs_free_scene(h)
+    torch.cuda.empty_cache()
+    log(f"[bench] serving measured in {time.perf_counter() - t0:.1f}s")
+    return {"scenes": list(sizes), "storage": "fp16", "slots": slots, "capacity_rps": cap_rps,
+            "mix": "90% renders (random scene, 800x800 or 1600x1040, random view), 10% 1,000-upset campaigns on the "
+                   "134,826-Gaussian scene (800x800)",
+            "poisson": poisson, "storm": storm,
+            "latency": "host ms from arrival (open loop) or submission (storm) to completion of the request's stream"}
+
+
+def guard_frame(G, S, h, n, dev, guard_ms):
+    """One 2592x1944 frame of the guard-stress scene, the guard's share of a
+    guarded frame, and k simultaneous upsets (k = 1, 1,000, 20,000) rendered
+    without and with the FIELD guard: PSNR against the clean frame."""
+    import torch
+    W, H = 2592, 1944
+    cam = S.look_at_camera((0.0, 0.0, 15.0), width=W, height=H)
+    stream = torch.cuda.current_stream()
+    clean = torch.empty(W * H * 3, dtype=torch.float32, device=dev)
+    img = torch.empty_like(clean)
+    G.gs_render(h, cam, clean)                       # sizes the scratch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    G.gs_render(h, cam, clean)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    frame_ms = ev[0].elapsed_time(ev[1])
+    saved = torch.empty(n * 59, dtype=torch.int32, device=dev)
+    G.gs_read_planes(h, saved)
+    out = G.device_bytes(24, dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    dose = []
+    for k in (1, 1000, 20000):
+        fl = S.flips_multi(k, n, 59, S.FP32, S.SEED_BASE + 50 + k)
+        d = G.to_device(fl, dev)
+        row = {"k": k}
+        for guard in (False, True):
+            G.gs_write_planes(h, saved)
+            G.gs_apply_flips(h, d, k)
+            if guard:
+                cnt.zero_()
+                G.gs_guard(h, 0, S.GUARD_WORDS_DEFAULT, cnt)
+            G.gs_render(h, cam, img)
+            G.gs_compare(img, clean, H, W, 1, out)
+            r = G.from_device(out, G.RESULT_DTYPE)[0]
+            mse = max(float(r["sse"]) / (W * H * 3), 1e-10)
+            key = "guard" if guard else "no_guard"
+            row[key] = {"psnr_db": 10 * math.log10(1 / mse), "footprint": float(r["footprint"]) / (W * H),
+                        "nonfinite_px": int(r["nonfinite"])}
+            if guard:
+                row[key]["clamps"] = int(cnt.item())
+        dose.append(row)
+    G.gs_write_planes(h, saved)
+    del saved
+    return {"resolution": f"{W}x{H}", "render_ms": frame_ms, "guard_ms": guard_ms,
+            "guard_share_of_guarded_frame": guard_ms / (guard_ms + frame_ms), "dose": dose}
 
 
 def guard_stress(args, G, S, dev, pk, pk_kind):
@@ -422,6 +587,8 @@ def guard_stress(args, G, S, dev, pk, pk_kind):
         gbs = n * bytes_per / t / 1e9
         res[name] = {"ms": t * 1000, "gb_s": gbs, "frac": gbs / pk["hbm_gbs"], "bytes_per_launch": n * bytes_per,
                      "clamps": int(cnt.item())}
+    if not args.only_guard:
+        res["frame"] = guard_frame(G, S, h, n, dev, res["field"]["ms"])
     G.gs_free_scene(h)
     torch.cuda.empty_cache()
     return res

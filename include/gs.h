@@ -115,6 +115,10 @@ GS_API gs_status gs_scene_info(const gs_scene* scene, uint64_t* n, int* sh_degre
 GS_API gs_status gs_scene_planes(gs_scene* scene, void** dev_planes);
 /* Copy the planes back into `dst` (host or device per `dst_on_device`). */
 GS_API gs_status gs_read_planes(gs_scene* scene, void* dst, int dst_on_device, void* stream);
+/* Overwrite the resident planes from `src` (same layout; host or device), e.g.
+ * to restore a saved clean state.  The FIELD box and any views are not
+ * recomputed. */
+GS_API gs_status gs_write_planes(gs_scene* scene, const void* src, int src_on_device, void* stream);
 
 /* Read and clear the scene's sticky device error flags (bit 0: a flip site was
  * out of range and skipped).  Synchronises the device. */
@@ -196,9 +200,10 @@ GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_f
 /* Enable (default) or disable CUDA-graph replay of the batched dirty-tile step. */
 GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
 /* Work counters for measurement: while enabled, the blend kernels count
- * pixel-primitive evaluations, tiles blended and list entries staged (graphs
- * are bypassed).  gs_read_work copies [evaluations, tiles, entries] and
- * resets them (synchronises). */
+ * pixel-primitive evaluations, tiles blended, list entries staged and dirty
+ * tiles left untouched because every pixel stopped before the change (graphs
+ * are bypassed).  gs_read_work copies those 4 counts and resets them
+ * (synchronises). */
 GS_API gs_status gs_count_work(gs_scene* scene, int enable);
 GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
 /* Kernel timing for measurement: while enabled, CUDA events bracket the

@@ -25,12 +25,13 @@ gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* of
                                    cudaStream_t st);
 gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st);
+                             void* plan, CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st);
+size_t plan_item_size();
 size_t view_ptrs_size();
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, int W, int H);
+                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, int W, int H);
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
-                                  float* img, uint32_t* stop, cudaStream_t st);
+                                  float* img, uint32_t* stop, uint32_t* tile_stop, cudaStream_t st);
 gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_t n, uint32_t* dk, cudaStream_t st);
 gs_status launch_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges, cudaStream_t st);
 uint32_t key_to_bits(uint32_t key, int fmt);
@@ -119,6 +120,7 @@ void free_views(gs_scene* s) {
         cudaFree(v.ranges);
         cudaFree(v.clean);
         cudaFree(v.stop);
+        cudaFree(v.tile_stop);
     }
     s->views.clear();
     s->K = 0;
@@ -141,6 +143,8 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     cudaFree(s->res_stage);
     cudaFree(s->queue);
     cudaFree(s->saved);
+    cudaFree(s->plan);
+    s->plan = nullptr;
     int cb = std::max(B, s->cap_B);
     int cf = std::max(fpv * B, s->cap_flips);
     GS_TRY(dmalloc((void**)&s->flip_stage, sizeof(gs_flip) * cf));
@@ -150,6 +154,9 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     GS_TRY(dmalloc((void**)&s->res_stage, sizeof(gs_result) * cb * K));
     GS_TRY(dmalloc((void**)&s->queue, sizeof(unsigned int) * 4));
     GS_TRY(dmalloc((void**)&s->saved, sizeof(uint32_t) * cf));
+    // every (variant, view) can dirty at most every tile of its view
+    s->plan_cap = (uint64_t)cb * K * (uint64_t)std::max(s->max_tiles, 1);
+    GS_TRY(dmalloc(&s->plan, plan_item_size() * s->plan_cap));
     s->cap_B = cb;
     s->cap_flips = cf;
     return GS_OK;
@@ -174,7 +181,8 @@ gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaS
                               (const uint2* const*)s->dev_clean_rects, s->desc, s->item_off, s->acc, s->queue, st));
     // external records: inside a stream capture they become event-record nodes of the graph
     if (s->ev_k0) GS_CUDA(cudaEventRecordWithFlags(s->ev_k0, st, cudaEventRecordExternal));
-    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->acc, s->queue, s->work_ctr, st));
+    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->acc, s->queue, s->work_ctr,
+                              st));
     if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
     GS_TRY(launch_finalize(s->acc, B * K, s->res_stage, st));
     return GS_OK;
@@ -313,6 +321,7 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->res_stage);
     cudaFree(s->queue);
     cudaFree(s->saved);
+    cudaFree(s->plan);
     cudaFree(s->work_ctr);
     if (s->ev_k0) cudaEventDestroy(s->ev_k0);
     if (s->ev_k1) cudaEventDestroy(s->ev_k1);
@@ -341,6 +350,15 @@ gs_status gs_read_planes(gs_scene* s, void* dst, int dst_on_device, void* stream
     GS_CUDA(cudaMemcpyAsync(dst, s->planes, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             (cudaStream_t)stream));
     if (!dst_on_device) GS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return GS_OK;
+}
+
+gs_status gs_write_planes(gs_scene* s, const void* src, int src_on_device, void* stream) {
+    if (!s || !src) return set_error(GS_ERR_ARG, "NULL argument");
+    size_t bytes = (size_t)s->n * s->nwords * word_bytes(s->fmt);
+    GS_CUDA(cudaMemcpyAsync(s->planes, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream));
+    if (!src_on_device) GS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return GS_OK;
 }
 
@@ -443,15 +461,16 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
         GS_TRY(dmalloc((void**)&v.ranges, sizeof(uint2) * ntiles));
         GS_TRY(dmalloc((void**)&v.clean, sizeof(float) * (size_t)v.cam.W * v.cam.H * 3));
         GS_TRY(dmalloc((void**)&v.stop, sizeof(uint32_t) * (size_t)v.cam.W * v.cam.H));
+        GS_TRY(dmalloc((void**)&v.tile_stop, sizeof(uint32_t) * ntiles));
         GS_CUDA(cudaMemcpyAsync(v.recs, s->work.recs, sizeof(BlendRec) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.rects, s->work.rects, sizeof(uint2) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ranges, s->work.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
-        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, st));
+        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop, st));
         GS_TRY(launch_gather_depth(v.recs, v.ids, np, v.dk, st));
         v.npairs = np;
-        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.dk, v.ranges, v.clean, v.stop, v.cam.W,
-                       v.cam.H);
+        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.dk, v.ranges, v.clean, v.stop,
+                       v.tile_stop, v.cam.W, v.cam.H);
         crects[k] = v.rects;
         max_pairs = std::max(max_pairs, np);
         max_tiles = std::max(max_tiles, ntiles);
@@ -653,8 +672,8 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
 gs_status gs_count_work(gs_scene* s, int enable) {
     if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
     if (enable && !s->work_ctr) {
-        GS_TRY(dmalloc((void**)&s->work_ctr, sizeof(unsigned long long) * 4));
-        GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 4));
+        GS_TRY(dmalloc((void**)&s->work_ctr, sizeof(unsigned long long) * 8));
+        GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 8));
     }
     if (!enable && s->work_ctr) {
         cudaFree(s->work_ctr);
@@ -666,8 +685,8 @@ gs_status gs_count_work(gs_scene* s, int enable) {
 gs_status gs_read_work(gs_scene* s, uint64_t* host_counts) {
     if (!s || !host_counts) return set_error(GS_ERR_ARG, "NULL argument");
     if (!s->work_ctr) return set_error(GS_ERR_STATE, "work counting is off");
-    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost));
-    GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 4));
+    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 8));
     return GS_OK;
 }
 

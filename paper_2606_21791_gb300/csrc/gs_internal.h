@@ -94,6 +94,7 @@ struct ViewState {
     uint2* ranges = nullptr;         // [ntiles] (start, end)
     float* clean = nullptr;          // [H*W*3]
     uint32_t* stop = nullptr;        // [H*W] list index that stopped each clean pixel
+    uint32_t* tile_stop = nullptr;   // [ntiles] largest stop index in each tile
     uint64_t npairs = 0;
     uint64_t cap_pairs = 0;
 };
@@ -162,6 +163,8 @@ struct gs_scene {
     gs::CmpAcc* acc = nullptr;
     gs_result* res_stage = nullptr;
     unsigned int* queue = nullptr;
+    void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
+    uint64_t plan_cap = 0;
     uint32_t* saved = nullptr;
     bool use_graphs = true;
     int batch = 0;                          // variants per dirty-tile launch (0: default)

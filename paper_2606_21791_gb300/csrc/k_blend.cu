@@ -215,7 +215,8 @@ template <int MODE, bool COUNT>
 __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
                                                    const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                    float* __restrict__ img, const float* __restrict__ clean,
-                                                   CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop) {
+                                                   CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop,
+                                                   uint32_t* __restrict__ tile_stop) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
     const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
@@ -241,6 +242,18 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
             o[1] = v1;
             o[2] = v2;
             if (MODE == 2) stop[px] = p.stop;
+        }
+        if (MODE == 2) {
+            // the tile's largest stop index: a change at or after it leaves every pixel as it is
+            __shared__ uint32_t wmax[kBT / 32];
+            const uint32_t m = __reduce_max_sync(0xffffffffu, g.inside ? p.stop : 0u);
+            if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t t = 0;
+                for (int w = 0; w < kBT / 32; w++) t = max(t, wmax[w]);
+                tile_stop[tile] = t;
+            }
         }
     } else {
         compare_tile(g, v0, v1, v2, clean, W, acc);
@@ -289,6 +302,7 @@ struct ViewPtrs {
     const uint2* ranges;
     const float* clean;
     const uint32_t* stop;    // clean stop index of every pixel
+    const uint32_t* tile_stop;   // largest stop index of each tile
     int W, H, tiles_x, pad;
 };
 
@@ -321,103 +335,161 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
     return lo + __popc(__ballot_sync(0xffffffffu, less));
 }
 
-constexpr int kMaxItems = 1025;   // B * K <= 1024 (variant, view) pairs + 1
+// One dirty tile that needs re-blending (80 B).  ins is the insertion position
+// in the clean list without the primitive's old entry; cut is the first changed
+// position of the clean list; rec is the corrupted record (when flags bit 1).
+struct __align__(16) PlanItem {
+    BlendRec rec;
+    uint32_t bk;      // (variant, view) = variant * K + view
+    uint32_t tile;
+    uint32_t s, e;    // clean list range
+    uint32_t pp, ins, cut;
+    uint32_t flags;   // bit 0: old entry in this tile, bit 1: corrupted entry in this tile
+};
 
+// Plan: one warp per (variant, view, dirty tile) work item, grid-strided.
+// Decodes the tile, finds the removal and insertion positions with warp
+// searches, and drops the tile when every pixel stopped before the first
+// changed position (its pixels are then the clean ones, Delta = 0); the rest
+// are appended to the plan.
 template <bool COUNT>
-__global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
-                                              const uint32_t* __restrict__ item_off, int BK, int K,
-                                              CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
-                                              unsigned long long* work) {
-    __shared__ Stage s;
-    __shared__ BlendRec nrec;
-    __shared__ uint32_t s_off[kMaxItems];
-    __shared__ int sh_item_ok, sh_bk, sh_tx, sh_ty, sh_has_old, sh_has_new;
-    __shared__ uint32_t sh_s, sh_e, sh_pp, sh_ins, sh_cut;
-    for (int i = threadIdx.x; i <= BK; i += kBT) s_off[i] = item_off[i];
-    __syncthreads();
-    const uint32_t total = s_off[BK];
+__global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
+                                             const uint32_t* __restrict__ item_off, int BK, int K,
+                                             PlanItem* __restrict__ plan, unsigned int* __restrict__ plan_count,
+                                             unsigned long long* work) {
     const int lane = threadIdx.x & 31;
-    while (true) {
-        if (threadIdx.x < 32) {
-            uint32_t item = 0;
-            if (lane == 0) item = atomicAdd(&queue[0], 1u);
-            item = __shfl_sync(0xffffffffu, item, 0);
-            if (item < total) {
-                // (variant, view) of this item: last bk with s_off[bk] <= item
-                int lo = 0, hi = BK - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= item) lo = mid; else hi = mid - 1;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t total = item_off[BK];
+    unsigned int skipped = 0;
+    for (uint32_t item = warp; item < total; item += nwarps) {
+        // (variant, view) of this item: last bk with item_off[bk] <= item
+        int lo = 0, hi = BK - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const int bk = lo;
+        const DirtyDesc& d = desc[bk];
+        const uint32_t j = item - item_off[bk];
+        int tx = 0, ty = 0;
+        const uint32_t wn = (uint32_t)d.nx1 - d.nx0;
+        const uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
+        if (j < an) {
+            tx = d.nx0 + (int)(j % wn);
+            ty = d.ny0 + (int)(j / wn);
+        } else {
+            // tiles of the clean rect that are not in the corrupted rect, row-major
+            uint32_t r = j - an;
+            for (int y = d.oy0; y < d.oy1; y++) {
+                int ex0 = d.ox0, ex1 = d.ox0;   // excluded x range of this row
+                if (d.new_vis && y >= d.ny0 && y < d.ny1) {
+                    ex0 = max((int)d.ox0, (int)d.nx0);
+                    ex1 = min((int)d.ox1, (int)d.nx1);
+                    if (ex1 < ex0) ex1 = ex0;
                 }
-                const int bk = lo;
-                const DirtyDesc& d = desc[bk];
-                const uint32_t j = item - s_off[bk];
-                int tx = 0, ty = 0;
-                const uint32_t wn = (uint32_t)d.nx1 - d.nx0;
-                const uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
-                if (j < an) {
-                    tx = d.nx0 + (int)(j % wn);
-                    ty = d.ny0 + (int)(j / wn);
-                } else {
-                    // tiles of the clean rect that are not in the corrupted rect, row-major
-                    uint32_t r = j - an;
-                    for (int y = d.oy0; y < d.oy1; y++) {
-                        int ex0 = d.ox0, ex1 = d.ox0;   // excluded x range of this row
-                        if (d.new_vis && y >= d.ny0 && y < d.ny1) {
-                            ex0 = max((int)d.ox0, (int)d.nx0);
-                            ex1 = min((int)d.ox1, (int)d.nx1);
-                            if (ex1 < ex0) ex1 = ex0;
-                        }
-                        const uint32_t left = (uint32_t)(ex0 - d.ox0);
-                        const uint32_t row = (uint32_t)(d.ox1 - d.ox0) - (uint32_t)(ex1 - ex0);
-                        if (r < row) {
-                            ty = y;
-                            tx = r < left ? d.ox0 + (int)r : ex1 + (int)(r - left);
-                            break;
-                        }
-                        r -= row;
-                    }
+                const uint32_t left = (uint32_t)(ex0 - d.ox0);
+                const uint32_t row = (uint32_t)(d.ox1 - d.ox0) - (uint32_t)(ex1 - ex0);
+                if (r < row) {
+                    ty = y;
+                    tx = r < left ? d.ox0 + (int)r : ex1 + (int)(r - left);
+                    break;
                 }
-                const ViewPtrs v = views[bk % K];
-                const int tile = ty * v.tiles_x + tx;
-                const uint2 rg = v.ranges[tile];
-                const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
-                const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
-                uint32_t pp = 0, ins = 0, cut = 0xffffffffu;
-                if (has_old) {
-                    pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(v.recs[d.prim].depth), d.prim) -
-                         rg.x;
-                    cut = pp;
-                }
-                if (has_new) {
-                    ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(d.rec.depth), d.prim) - rg.x;
-                    cut = min(cut, ins);   // clean-list position of the insertion
-                    if (has_old && pp < ins) ins -= 1;
-                }
-                if (lane == 0) {
-                    if (has_new) nrec = d.rec;
-                    sh_bk = bk;
-                    sh_tx = tx;
-                    sh_ty = ty;
-                    sh_s = rg.x;
-                    sh_e = rg.y;
-                    sh_pp = pp;
-                    sh_ins = ins;
-                    sh_cut = cut;
-                    sh_has_old = has_old;
-                    sh_has_new = has_new;
-                }
+                r -= row;
             }
-            if (lane == 0) sh_item_ok = item < total;
+        }
+        const ViewPtrs v = views[bk % K];
+        const int tile = ty * v.tiles_x + tx;
+        const uint2 rg = v.ranges[tile];
+        const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
+        const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
+        uint32_t pp = 0, ins = 0, cut = 0xffffffffu;
+        if (has_old) {
+            pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(v.recs[d.prim].depth), d.prim) - rg.x;
+            cut = pp;
+        }
+        if (has_new) {
+            ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(d.rec.depth), d.prim) - rg.x;
+            cut = min(cut, ins);   // clean-list position of the insertion
+            if (has_old && pp < ins) ins -= 1;
+        }
+        if (v.tile_stop[tile] < cut) {   // every pixel stopped before the change
+            skipped++;
+            continue;
+        }
+        if (lane == 0) {
+            PlanItem it;
+            it.rec = d.rec;
+            it.bk = (uint32_t)bk;
+            it.tile = (uint32_t)tile;
+            it.s = rg.x;
+            it.e = rg.y;
+            it.pp = pp;
+            it.ins = ins;
+            it.cut = cut;
+            it.flags = (has_old ? 1u : 0u) | (has_new ? 2u : 0u);
+            plan[atomicAdd(plan_count, 1u)] = it;
+        }
+    }
+    if (COUNT && lane == 0 && skipped) atomicAdd(&work[3], (unsigned long long)skipped);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void fetch_plan_async(PlanItem* dst, const PlanItem* src) {
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(PlanItem) / 16); i++)
+        cp_async16(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i);
+    cp_async_commit();
+}
+
+// Dirty-tile blend: persistent; each block takes plan items from a queue.  The
+// next item is copied into the other half of a shared double buffer
+// (cp.async) while the current one is blended.  A tile is re-blended from the
+// clean list with the old entry removed and the corrupted record merged in,
+// and compared on the fly with the clean tile.
+template <bool COUNT>
+__global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ views, int K,
+                                                 const PlanItem* __restrict__ plan,
+                                                 const unsigned int* __restrict__ plan_count,
+                                                 CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
+                                                 unsigned long long* work) {
+    __shared__ Stage s;
+    __shared__ PlanItem pbuf[2];
+    __shared__ int sh_ok;
+    const uint32_t total = *plan_count;
+    bool have = false;   // thread 0: pbuf[cur] holds (or is receiving) an item
+    int cur = 0;
+    if (threadIdx.x == 0) {
+        const uint32_t i0 = atomicAdd(&queue[0], 1u);
+        have = i0 < total;
+        if (have) fetch_plan_async(&pbuf[0], &plan[i0]);
+    }
+    while (true) {
+        if (threadIdx.x == 0) {
+            cp_async_wait_all();
+            sh_ok = have;
+            if (have) {
+                const uint32_t i1 = atomicAdd(&queue[0], 1u);
+                have = i1 < total;
+                if (have) fetch_plan_async(&pbuf[cur ^ 1], &plan[i1]);
+            }
         }
         __syncthreads();
-        if (!sh_item_ok) break;
-        const int bk = sh_bk, k = bk % K;
-        const ViewPtrs v = views[k];
-        const PixGeo g = pix_geo(sh_tx, sh_ty, v.W, v.H);
-        const uint32_t s0 = sh_s, pp = sh_pp, ins = sh_ins;
-        const bool has_old = sh_has_old, has_new = sh_has_new;
-        const uint32_t L = (sh_e - sh_s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
+        if (!sh_ok) break;
+        const PlanItem& it = pbuf[cur];
+        const int bk = (int)it.bk;
+        const ViewPtrs v = views[bk % K];
+        const PixGeo g = pix_geo((int)(it.tile % (uint32_t)v.tiles_x), (int)(it.tile / (uint32_t)v.tiles_x), v.W,
+                                 v.H);
+        const uint32_t s0 = it.s, pp = it.pp, ins = it.ins, cut = it.cut;
+        const bool has_old = it.flags & 1u, has_new = it.flags & 2u;
+        const uint32_t L = (it.e - it.s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         // A pixel whose clean blend stopped before the first changed list position
         // processes the same entries in the same order and stops at the same one:
         // its value is the clean value, bit for bit.
@@ -425,7 +497,7 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
         if (g.inside) {
             const size_t px = (size_t)g.py * v.W + g.px;
-            if (v.stop[px] < sh_cut) {
+            if (v.stop[px] < cut) {
                 same = true;
                 c0 = v.clean[px * 3 + 0];
                 c1 = v.clean[px * 3 + 1];
@@ -434,13 +506,12 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         }
         Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside || same, 0u};
         unsigned int nev = 0, staged = 0;
-        const bool all_same = __syncthreads_count(p.done) == kBT;
-        for (uint32_t base = 0; base < L && !all_same; base += kBT) {
+        for (uint32_t base = 0; base < L; base += kBT) {
             int cnt = (int)min((uint32_t)kBT, L - base);
             if ((int)threadIdx.x < cnt) {
                 uint32_t m = base + threadIdx.x;
                 if (has_new && m == ins) {
-                    stage_put(s, threadIdx.x, nrec);
+                    stage_put(s, threadIdx.x, it.rec);
                 } else {
                     uint32_t j = (has_new && m > ins) ? m - 1 : m;
                     uint32_t ci = (has_old && j >= pp) ? j + 1 : j;
@@ -461,6 +532,7 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         }
         compare_tile(g, v0, v1, v2, v.clean, v.W, &acc[bk]);
         __syncthreads();
+        cur ^= 1;
     }
 }
 
@@ -502,7 +574,7 @@ gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const ui
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr,
-                                                     nullptr);
+                                                     nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -512,19 +584,21 @@ gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const 
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     if (work)
-        k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work, nullptr);
+        k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work, nullptr,
+                                                       nullptr);
     else
         k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr,
-                                                        nullptr);
+                                                        nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
-                                  float* img, uint32_t* stop, cudaStream_t st) {
+                                  float* img, uint32_t* stop, uint32_t* tile_stop, cudaStream_t st) {
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
-    k_blend_full<2, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr, stop);
+    k_blend_full<2, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr, stop,
+                                                     tile_stop);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -562,13 +636,21 @@ int dirty_grid() {
     return blocks;
 }
 
+size_t plan_item_size() { return sizeof(PlanItem); }
+
+// queue[0]: blend work queue, queue[1]: plan item count (both zeroed by the injector)
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st) {
-    if (work)
-        k_dirty<true><<<dirty_grid(), kBT, 0, st>>>((const ViewPtrs*)dev_views, desc, item_off, BK, K, acc, queue, work);
-    else
-        k_dirty<false><<<dirty_grid(), kBT, 0, st>>>((const ViewPtrs*)dev_views, desc, item_off, BK, K, acc, queue,
-                                                     nullptr);
+                             void* plan, CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st) {
+    const ViewPtrs* views = (const ViewPtrs*)dev_views;
+    PlanItem* pl = (PlanItem*)plan;
+    const int plan_blocks = num_sms() * 8;
+    if (work) {
+        k_plan<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue + 1, work);
+        k_dirty<true><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue + 1, acc, queue, work);
+    } else {
+        k_plan<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue + 1, nullptr);
+        k_dirty<false><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue + 1, acc, queue, nullptr);
+    }
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -583,7 +665,7 @@ gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_
 }
 
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, int W, int H) {
+                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, int W, int H) {
     ViewPtrs v;
     v.recs = recs;
     v.ids = ids;
@@ -591,6 +673,7 @@ void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, c
     v.ranges = ranges;
     v.clean = clean;
     v.stop = stop;
+    v.tile_stop = tile_stop;
     v.W = W;
     v.H = H;
     v.tiles_x = (W + kTile - 1) / kTile;

@@ -46,6 +46,7 @@ SIGNATURES = {
     "gs_scene_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "gs_scene_planes": (_i32, [_vp, C.POINTER(_vp)]),
     "gs_read_planes": (_i32, [_vp, _vp, _i32, _vp]),
+    "gs_write_planes": (_i32, [_vp, _vp, _i32, _vp]),
     "gs_scene_errors": (_i32, [_vp, _vp]),
     "gs_apply_flips": (_i32, [_vp, _vp, _i64, _vp]),
     "gs_field_box": (_i32, [_vp, _vp, _vp]),
@@ -184,6 +185,13 @@ def gs_read_planes(scene, dst, stream=None):
     return dst
 
 
+def gs_write_planes(scene, src, stream=None):
+    on_dev = not isinstance(src, np.ndarray)
+    if not on_dev:
+        src = np.ascontiguousarray(src)
+    _check(load_library().gs_write_planes(scene, _ptr(src), int(on_dev), _stream(stream)), "gs_write_planes")
+
+
 def gs_scene_errors(scene) -> int:
     f = np.zeros(1, dtype=np.uint32)
     _check(load_library().gs_scene_errors(scene, _ptr(f)), "gs_scene_errors")
@@ -258,9 +266,9 @@ def gs_count_work(scene, enable: bool):
 
 
 def gs_read_work(scene):
-    c = np.zeros(3, dtype=np.uint64)
+    c = np.zeros(4, dtype=np.uint64)
     _check(load_library().gs_read_work(scene, _ptr(c)), "gs_read_work")
-    return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2])}
+    return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2]), "tiles_unchanged": int(c[3])}
 
 
 def gs_time_kernels(scene, enable: bool):
