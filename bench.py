@@ -328,11 +328,13 @@ def main():
     torch.cuda.synchronize()
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     plain_out = G.device_bytes(nplain * K_views * 24, dev)
+    torch.cuda.nvtx.range_push("plain_loop")
     pe0.record(stream)
     G.gs_inject_and_render_full(h, flips_at(args.warmup)[: 8 * nplain] if B >= nplain else d_flips[:8 * nplain],
                                 nplain, 1, G.GS_GUARD_OFF, mask, plain_out)
     pe1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     plain_s = pe0.elapsed_time(pe1) / 1000.0
     plain = {"value": nplain / plain_s, "unit": UNIT, "sample": f"{nplain} upsets, {K_views} views each",
              "mpix_s": nplain * K_views * Wd * Hd / plain_s / 1e6}
@@ -516,10 +518,12 @@ def guard_frame(G, S, h, n, dev, guard_ms):
     img = torch.empty_like(clean)
     G.gs_render(h, cam, clean)                       # sizes the scratch
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.nvtx.range_push("frame_66M")
     ev[0].record(stream)
     G.gs_render(h, cam, clean)
     ev[1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     frame_ms = ev[0].elapsed_time(ev[1])
     saved = torch.empty(n * 59, dtype=torch.int32, device=dev)
     G.gs_read_planes(h, saved)

@@ -113,6 +113,7 @@ struct RenderWork {
     uint32_t* pkey[2] = {nullptr, nullptr};    // pair tile keys
     uint32_t* pval[2] = {nullptr, nullptr};    // pair primitive ids
     uint32_t* hist = nullptr;                   // radix histograms
+    unsigned long long* hpart = nullptr;        // block partials of the histogram scan
     uint32_t* scan_tmp = nullptr;               // block sums for scans
     uint2* ranges = nullptr;
     unsigned long long* total = nullptr;        // [0] pair count, [1] overflow flag

@@ -10,7 +10,7 @@
 // passes).  The result equals a stable sort of (tile << 32 | depth bits) keys
 // emitted in primitive order, with depth ties broken by primitive index.
 //
-// One radix pass = histogram kernel (per-block digit counts) + single-block
+// One radix pass = histogram kernel (per-block digit counts) + multi-block
 // exclusive scan over (digit, block) + scatter kernel (stable in-block ranking
 // with warp match/ballot, block-local reorder in shared memory, coalesced
 // write-out).  Item counts may live on the device so the whole pipeline runs
@@ -46,40 +46,6 @@ __global__ __launch_bounds__(kRT) void k_radix_hist(const uint32_t* __restrict__
     }
     __syncthreads();
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
-}
-
-// exclusive scan of `len` uint32 in place (single block)
-__global__ __launch_bounds__(kScanT) void k_scan_single(uint32_t* data, uint64_t len) {
-    __shared__ uint32_t wsum[kScanT / 32];
-    uint64_t chunk = (len + kScanT - 1) / kScanT;
-    uint64_t b = (uint64_t)threadIdx.x * chunk;
-    uint64_t e = b + chunk < len ? b + chunk : len;
-    uint32_t s = 0;
-    for (uint64_t i = b; i < e; i++) s += data[i];
-    // block exclusive scan of s
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t t = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        wsum[lane] = t;
-    }
-    __syncthreads();
-    uint32_t run = x - s + (wid > 0 ? wsum[wid - 1] : 0u);
-    for (uint64_t i = b; i < e; i++) {
-        uint32_t v = data[i];
-        data[i] = run;
-        run += v;
-    }
 }
 
 template <bool VALS>
@@ -254,9 +220,11 @@ __global__ __launch_bounds__(kScanT) void k_scan_partials_top(unsigned long long
     }
 }
 
-__global__ __launch_bounds__(kScanBlockT) void k_scan_apply(const uint32_t* __restrict__ in, uint64_t n,
+// in and out may be the same array: every element is read and then written by
+// the same thread, and by no other
+__global__ __launch_bounds__(kScanBlockT) void k_scan_apply(const uint32_t* in, uint64_t n,
                                                            const unsigned long long* __restrict__ part,
-                                                           uint32_t* __restrict__ out) {
+                                                           uint32_t* out) {
     __shared__ uint32_t wsum[kScanBlockT / 32];
     __shared__ uint32_t carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -379,14 +347,22 @@ __global__ void k_rects_to_keys(const float* depth, const int32_t* rects, uint64
 
 int radix_blocks(uint64_t cap) { return (int)std::max<uint64_t>(1, div_up(cap, kRTile)); }
 
-// one stable LSD radix sort over `bits` key bits; returns the index (0/1) of the
-// buffer holding the result
+int hist_parts(uint64_t cap) { return (int)div_up((uint64_t)256 * radix_blocks(cap), kScanTile); }
+
+// one stable LSD radix sort over `bits` key bits; `cur` returns the index
+// (0/1) of the buffer holding the result.  The (digit, block) histogram is
+// scanned by block partials -> single-block scan of the partials -> apply.
 gs_status radix_sort(uint32_t* k[2], uint32_t* v[2], const unsigned long long* dcount, uint64_t cap, int bits,
-                     uint32_t* hist, int& cur, cudaStream_t st) {
-    int nblocks = radix_blocks(cap);
+                     uint32_t* hist, unsigned long long* hpart, int& cur, cudaStream_t st) {
+    const int nblocks = radix_blocks(cap);
+    const uint64_t hlen = (uint64_t)256 * nblocks;
+    const int nparts = hist_parts(cap);
+    unsigned long long* htot = hpart + nparts + 1;   // scratch for the partial scan's totals
     for (int shift = 0; shift < bits; shift += 8) {
         k_radix_hist<<<nblocks, kRT, 0, st>>>(k[cur], dcount, cap, shift, hist, nblocks);
-        k_scan_single<<<1, kScanT, 0, st>>>(hist, (uint64_t)256 * nblocks);
+        k_scan_partials<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart);
+        k_scan_partials_top<<<1, kScanT, 0, st>>>(hpart, nparts, htot, ~0ull);
+        k_scan_apply<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart, hist);
         k_radix_scatter<true><<<nblocks, kRT, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], dcount, cap, shift,
                                                        hist, nblocks);
         cur ^= 1;
@@ -446,8 +422,11 @@ gs_status alloc_render_work(RenderWork& w, uint64_t n, uint64_t cap_pairs, int n
             w.cap_pairs = cap_pairs;
         }
         cudaFree(w.hist);
-        uint64_t hb = std::max<uint64_t>(radix_blocks(std::max<uint64_t>(w.cap_pairs, w.n)), 1);
+        cudaFree(w.hpart);
+        const uint64_t big = std::max<uint64_t>(w.cap_pairs, w.n);
+        uint64_t hb = std::max<uint64_t>(radix_blocks(big), 1);
         GS_TRY(A((void**)&w.hist, 4 * 256 * hb));
+        GS_TRY(A((void**)&w.hpart, sizeof(unsigned long long) * (hist_parts(big) + 8)));
     }
     if (grow_t) {
         cudaFree(w.ranges);
@@ -476,6 +455,7 @@ void free_render_work(RenderWork& w) {
     cudaFree(w.cnt);
     cudaFree(w.off);
     cudaFree(w.hist);
+    cudaFree(w.hpart);
     cudaFree(w.scan_tmp);
     cudaFree(w.ranges);
     cudaFree(w.total);
@@ -490,7 +470,7 @@ gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, 
     int ntiles = tiles_x * tiles_y;
     int cur = 0;
     // depth order of the primitives
-    GS_TRY(radix_sort(w.dkey, w.dval, nullptr, n, 32, w.hist, cur, st));
+    GS_TRY(radix_sort(w.dkey, w.dval, nullptr, n, 32, w.hist, w.hpart, cur, st));
     const uint32_t* sorted_ids = w.dval[cur];
     // tiles per primitive in depth order, exclusive scan, pair count
     unsigned blocks = (unsigned)div_up(std::max<uint64_t>(n, 1), 256);
@@ -511,7 +491,7 @@ gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, 
     int tbits = 1;
     while ((1 << tbits) < ntiles) tbits++;
     int pcur = 0;
-    GS_TRY(radix_sort(w.pkey, w.pval, w.total, w.cap_pairs, tbits, w.hist, pcur, st));
+    GS_TRY(radix_sort(w.pkey, w.pval, w.total, w.cap_pairs, tbits, w.hist, w.hpart, pcur, st));
     GS_CUDA(cudaMemsetAsync(w.ranges, 0, sizeof(uint2) * ntiles, st));
     k_ranges<<<num_sms() * 8, 256, 0, st>>>(w.pkey[pcur], w.total, w.cap_pairs, w.ranges);
     GS_CUDA(cudaGetLastError());
