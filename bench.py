@@ -48,7 +48,7 @@ def log(*a):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-guard-stress", action="store_true", help="skip the 66M-Gaussian guard measurement")
@@ -220,6 +220,7 @@ def main():
     import paper_2606_21791_gb300 as P
     P.build()
     from paper_2606_21791_gb300 import gs as G
+    from paper_2606_21791_gb300 import replicas as R
     from paper_2606_21791_gb300 import synth as S
 
     rank, local, world = dist_info()
@@ -251,8 +252,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def flips_at(i):
-        off = ((i * world + rank) * B) % (nflips - B)
-        return d_flips[off * 8:(off + B) * 8]
+        a, b = R.step_slice(i, rank, world, B, nflips)
+        return d_flips[a * 8:b * 8]
 
     def step(i):
         G.gs_inject_and_render(h, flips_at(i), B, 1, G.GS_GUARD_OFF, mask, out)
@@ -289,12 +290,7 @@ def main():
             torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     G.gs_time_kernels(h, False)
-    t_total = sum(step_ms) / 1000.0
-    if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
-    inj = B * args.steps * world
+    t_total, inj = R.aggregate(sum(step_ms) / 1000.0, B * args.steps, dev)
     value = inj / t_total
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]
@@ -305,20 +301,20 @@ def main():
     host_out = torch.empty(B * K_views * 24, dtype=torch.uint8).pin_memory()
     dbuf = torch.empty(B * 8, dtype=torch.uint8, device=dev)
     for i in range(2):
-        off = (i * B) % (nflips - B)
-        dbuf.copy_(host_flips[off * 8:(off + B) * 8], non_blocking=True)
+        a, b = R.step_slice(i, rank, world, B, nflips)
+        dbuf.copy_(host_flips[a * 8:b * 8], non_blocking=True)
         G.gs_inject_and_render(h, dbuf, B, 1, G.GS_GUARD_OFF, mask, out)
         host_out.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for j in range(args.steps):
-        off = (((args.warmup + j) * world + rank) * B) % (nflips - B)
-        dbuf.copy_(host_flips[off * 8:(off + B) * 8], non_blocking=True)
+        a, b = R.step_slice(args.warmup + j, rank, world, B, nflips)
+        dbuf.copy_(host_flips[a * 8:b * 8], non_blocking=True)
         G.gs_inject_and_render(h, dbuf, B, 1, G.GS_GUARD_OFF, mask, out)
         host_out.copy_(out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e_t = time.perf_counter() - e0
-    e2e = {"value": B * args.steps * world / e2e_t, "unit": UNIT, "h2d_bytes_per_step": B * 8,
+    e2e_t, e2e_units = R.aggregate(time.perf_counter() - e0, B * args.steps, dev)
+    e2e = {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": B * 8,
            "d2h_bytes_per_step": B * K_views * 24,
            "how": "per step: pinned host flips -> device, gs_inject_and_render, records -> pinned host, sync"}
 

@@ -11,7 +11,8 @@
  * Precision: the study renders in fp32 (storage may be fp16/bf16, math is fp32,
  * Sec. 3 "Single-bit upset model"), so every render decision here is taken in
  * fp32 with IEEE-754 rounding of each operation (built with -ffp-contract=off,
- * no fast-math).  Metric sums accumulate in double.
+ * no fast-math); the activations' exponential is the fp32 rounding of the
+ * double exponential.  Metric sums accumulate in double.
  *
  * Conventions that the paper leaves to its external renderer (the 3DGS forward
  * pass it cites in Sec. 2 "Gaussian splatting") are fixed here as follows:
@@ -282,6 +283,14 @@ void or_sh_basis(float x, float y, float z, int degree, float* Y) { sh_basis(x, 
 
 static int finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
 
+/* The exponential of the activations (exp of the log-scale, the logistic of the
+ * opacity) is the fp32 rounding of the double-precision exponential: correctly
+ * rounded except for inputs within ~2^-29 relative of a rounding midpoint.  A
+ * plain expf differs between math libraries by an ulp on many inputs, and for
+ * needle-like primitives the 2x2 determinant a c - b^2 cancels so strongly that
+ * one ulp in a scale decides whether the primitive is culled. */
+static float exp_f32(float x) { return (float)exp((double)x); }
+
 void or_preprocess_one(const void* planes, int fmt, uint64_t n, int sh_degree, uint64_t i, const or_camera* cam,
                        int tile_w, int tile_h, or_rec* out) {
     memset(out, 0, sizeof(*out));
@@ -298,7 +307,7 @@ void or_preprocess_one(const void* planes, int fmt, uint64_t n, int sh_degree, u
 
     /* scale s = exp(log-scale) */
     float s[3];
-    for (int k = 0; k < 3; k++) s[k] = expf(or_load(planes, fmt, n, 3 + k, i));
+    for (int k = 0; k < 3; k++) s[k] = exp_f32(or_load(planes, fmt, n, 3 + k, i));
 
     /* rotation from the normalised quaternion (w, x, y, z) */
     float qw = or_load(planes, fmt, n, 6, i), qx = or_load(planes, fmt, n, 7, i);
@@ -409,7 +418,7 @@ void or_preprocess_one(const void* planes, int fmt, uint64_t n, int sh_degree, u
 
     /* opacity = logistic(logit) */
     float o = or_load(planes, fmt, n, 10, i);
-    float opac = 1.0f / (1.0f + expf(-o));
+    float opac = 1.0f / (1.0f + exp_f32(-o));
 
     out->mx = mx;
     out->my = my;

@@ -50,6 +50,13 @@ __device__ __forceinline__ bool finite3(float a, float b, float c) {
     return isfinite(a) && isfinite(b) && isfinite(c);
 }
 
+// Exponential of the activations, rounded once to fp32 from the double-precision
+// exponential (correctly rounded except within ~2^-29 of a rounding midpoint), so
+// that it agrees with any other correctly rounded evaluation: for needle-like
+// primitives the determinant a c - b^2 cancels so strongly that one ulp in a
+// scale decides whether the primitive is culled.
+__device__ __forceinline__ float exp_f32(float x) { return (float)exp((double)x); }
+
 // Conservative half extents of the region where alpha = opac * exp(-q/2) can
 // reach 1/255, for 2D covariance diagonal (a, c); see BlendRec.  Margins (1e-3
 // relative on the quadratic form plus 0.01 px) dwarf fp32 rounding of the
@@ -81,7 +88,7 @@ __device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const De
     if (!finite3(p0, p1, z)) return false;
     if (!(z > cam.znear) || !(z < cam.zfar)) return false;
 
-    float s0 = expf(src(3)), s1 = expf(src(4)), s2 = expf(src(5));
+    float s0 = exp_f32(src(3)), s1 = exp_f32(src(4)), s2 = exp_f32(src(5));
 
     float qw = src(6), qx = src(7), qy = src(8), qz = src(9);
     float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
@@ -220,7 +227,7 @@ __device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const De
         rgb[ch] = (acc < 0.0f) ? 0.0f : acc;
     }
     float o = src(10);
-    float opac = 1.0f / (1.0f + expf(-o));
+    float opac = 1.0f / (1.0f + exp_f32(-o));
 
     rec.mx = mx;
     rec.my = my;
