@@ -31,9 +31,7 @@ namespace {
 constexpr int kBT = 256;
 
 // Shared staging of one batch of list entries.  box = conservative alpha box
-// (x0, x1, y0, y1); q0 = (mean x, mean y, A, B), q1 = (C, opacity, r, g), qb = b,
-// with the conic pre-scaled so that A dx^2 + C dy^2 + B dx dy is the exponent
-// in base 2: A = -ca log2(e) / 2, B = -cb log2(e), C = -cc log2(e) / 2.
+// (x0, x1, y0, y1); q0 = (mean x, mean y, ca, cb), q1 = (cc, opacity, r, g), qb = b.
 struct Stage {
     float4 box[kBT];
     float4 q0[kBT];
@@ -45,8 +43,8 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ void stage_put(Stage& s, int j, const BlendRec& q) {
     s.box[j] = make_float4(q.mx - q.ex, q.mx + q.ex, q.my - q.ey, q.my + q.ey);
-    s.q0[j] = make_float4(q.mx, q.my, q.ca * (-0.5f * kLog2e), q.cb * (-kLog2e));
-    s.q1[j] = make_float4(q.cc * (-0.5f * kLog2e), q.opac, q.r, q.g);
+    s.q0[j] = make_float4(q.mx, q.my, q.ca, q.cb);
+    s.q1[j] = make_float4(q.cc, q.opac, q.r, q.g);
     s.qb[j] = q.b;
 }
 
@@ -100,11 +98,41 @@ __device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int W, int H) 
     return g;
 }
 
+// Natural pixel of thread index u in a tile (the pix_geo mapping).
+__device__ __forceinline__ void pix_of(int tile_x, int tile_y, int u, int& px, int& py) {
+    const int w = u >> 5, l = u & 31;
+    px = tile_x * kTile + (w & 1) * 8 + (l & 7);
+    py = tile_y * kTile + (w >> 1) * 4 + (l >> 3);
+}
+
 // 2^x (hardware approximation, flushes subnormal results to zero)
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Exponent of the Gaussian at offset (dx, dy): -(ca dx^2 + cc dy^2)/2 - cb dx dy,
+// every operation rounded on its own in this order (no contraction), so it is
+// reproducible bit for bit by any fp32 evaluation in the same order -- which
+// matters for near-degenerate conics, where cancellation makes the rounding
+// error large compared with the value.
+__device__ __forceinline__ float gauss_power(float ca, float cb, float cc, float dx, float dy) {
+    const float t1 = __fmul_rn(__fmul_rn(ca, dx), dx);
+    const float t2 = __fmul_rn(__fmul_rn(cc, dy), dy);
+    const float h = __fmul_rn(-0.5f, __fadd_rn(t1, t2));
+    const float t3 = __fmul_rn(__fmul_rn(cb, dx), dy);
+    return __fsub_rn(h, t3);
+}
+
+// alpha of a record at a pixel centre as the blend computes it, before the cap;
+// returns false where the blend skips the record (power > 0 or alpha < 1/255).
+__device__ __forceinline__ bool blend_alpha(float mx, float my, float ca, float cb, float cc, float opac, float pxc,
+                                            float pyc, float& alpha) {
+    const float power = gauss_power(ca, cb, cc, __fsub_rn(mx, pxc), __fsub_rn(my, pyc));
+    if (power > 0.0f) return false;
+    alpha = opac * ex2_approx(__fmul_rn(power, kLog2e));
+    return !(alpha < 1.0f / 255.0f);
 }
 
 // Work counters (measurement builds of the kernels only): [0] pixel-primitive
@@ -134,11 +162,8 @@ __device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t ba
             if (COUNT) nev++;
             const float4 q0 = s.q0[e];
             const float4 q1 = s.q1[e];
-            const float dx = q0.x - g.pxc, dy = q0.y - g.pyc;
-            const float e2 = dx * (q0.z * dx + q0.w * dy) + q1.x * dy * dy;   // power * log2(e)
-            if (e2 > 0.0f) continue;
-            float alpha = q1.y * ex2_approx(e2);
-            if (alpha < 1.0f / 255.0f) continue;
+            float alpha;
+            if (!blend_alpha(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, g.pxc, g.pyc, alpha)) continue;
             alpha = alpha > 0.99f ? 0.99f : alpha;     // keeps NaN
             const float Tn = p.T * (1.0f - alpha);
             if (Tn < 1e-4f) {
@@ -335,11 +360,12 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
     return lo + __popc(__ballot_sync(0xffffffffu, less));
 }
 
-// One dirty tile that needs re-blending (80 B).  ins is the insertion position
+// One dirty tile that needs re-blending (128 B).  ins is the insertion position
 // in the clean list without the primitive's old entry; cut is the first changed
 // position of the clean list; rec is the corrupted record (when flags bit 1).
 struct __align__(16) PlanItem {
     BlendRec rec;
+    BlendRec orec;    // clean (old) record
     uint32_t bk;      // (variant, view) = variant * K + view
     uint32_t tile;
     uint32_t s, e;    // clean list range
@@ -347,11 +373,28 @@ struct __align__(16) PlanItem {
     uint32_t flags;   // bit 0: old entry in this tile, bit 1: corrupted entry in this tile
 };
 
+// A pixel of a dirty tile keeps its clean value, bit for bit, when its clean
+// blend stopped before the first changed list position, or when its blend skips
+// both the removed (clean) and the inserted (corrupted) record (power > 0 or
+// alpha < 1/255, decided by the blend's own arithmetic): the state changes of
+// its blend are then those of the clean blend.  Every other pixel is "active"
+// and must be re-blended.
+__device__ __forceinline__ bool affects(const BlendRec& q, float x, float y) {
+    float alpha;
+    return blend_alpha(q.mx, q.my, q.ca, q.cb, q.cc, q.opac, x, y, alpha);
+}
+
+__device__ __forceinline__ bool pixel_active(int px, int py, int W, int H, uint32_t stop, uint32_t cut, bool has_old,
+                                             const BlendRec& orec, bool has_new, const BlendRec& nrec) {
+    if (px >= W || py >= H || stop < cut) return false;
+    const float x = (float)px + 0.5f, y = (float)py + 0.5f;
+    return (has_old && affects(orec, x, y)) || (has_new && affects(nrec, x, y));
+}
+
 // Plan: one warp per (variant, view, dirty tile) work item, grid-strided.
 // Decodes the tile, finds the removal and insertion positions with warp
-// searches, and drops the tile when every pixel stopped before the first
-// changed position (its pixels are then the clean ones, Delta = 0); the rest
-// are appended to the plan.
+// searches, and drops the tile when none of its pixels is active (Delta = 0
+// there); the rest are appended to the plan.
 template <bool COUNT>
 __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
                                              const uint32_t* __restrict__ item_off, int BK, int K,
@@ -413,13 +456,26 @@ __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views
             cut = min(cut, ins);   // clean-list position of the insertion
             if (has_old && pp < ins) ins -= 1;
         }
-        if (v.tile_stop[tile] < cut) {   // every pixel stopped before the change
+        bool any = false;
+        BlendRec orec = d.rec;
+        if (v.tile_stop[tile] >= cut) {
+            if (has_old) orec = v.recs[d.prim];
+            for (int u = lane; u < kBT && !any; u += 32) {
+                int px, py;
+                pix_of(tx, ty, u, px, py);
+                const bool in = px < v.W && py < v.H;
+                const uint32_t st = in ? v.stop[(size_t)py * v.W + px] : 0u;
+                any = __any_sync(0xffffffffu, pixel_active(px, py, v.W, v.H, st, cut, has_old, orec, has_new, d.rec));
+            }
+        }
+        if (!any) {   // every pixel keeps its clean value
             skipped++;
             continue;
         }
         if (lane == 0) {
             PlanItem it;
             it.rec = d.rec;
+            it.orec = orec;
             it.bk = (uint32_t)bk;
             it.tile = (uint32_t)tile;
             it.s = rg.x;
@@ -462,6 +518,9 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
     __shared__ Stage s;
     __shared__ PlanItem pbuf[2];
     __shared__ int sh_ok;
+    __shared__ uint32_t s_wcnt[kBT / 32];
+    __shared__ uint16_t s_pix[kBT];
+    __shared__ float3 s_out[kBT];
     const uint32_t total = *plan_count;
     bool have = false;   // thread 0: pbuf[cur] holds (or is receiving) an item
     int cur = 0;
@@ -485,28 +544,49 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         const PlanItem& it = pbuf[cur];
         const int bk = (int)it.bk;
         const ViewPtrs v = views[bk % K];
-        const PixGeo g = pix_geo((int)(it.tile % (uint32_t)v.tiles_x), (int)(it.tile / (uint32_t)v.tiles_x), v.W,
-                                 v.H);
+        const int tx = (int)(it.tile % (uint32_t)v.tiles_x), ty = (int)(it.tile / (uint32_t)v.tiles_x);
+        const PixGeo g = pix_geo(tx, ty, v.W, v.H);   // this thread's natural pixel
         const uint32_t s0 = it.s, pp = it.pp, ins = it.ins, cut = it.cut;
         const bool has_old = it.flags & 1u, has_new = it.flags & 2u;
         const uint32_t L = (it.e - it.s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
-        // A pixel whose clean blend stopped before the first changed list position
-        // processes the same entries in the same order and stops at the same one:
-        // its value is the clean value, bit for bit.
-        bool same = false;
-        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-        if (g.inside) {
-            const size_t px = (size_t)g.py * v.W + g.px;
-            if (v.stop[px] < cut) {
-                same = true;
-                c0 = v.clean[px * 3 + 0];
-                c1 = v.clean[px * 3 + 1];
-                c2 = v.clean[px * 3 + 2];
-            }
+        const size_t npx = g.inside ? (size_t)g.py * v.W + g.px : 0;
+        const bool active = g.inside && pixel_active(g.px, g.py, v.W, v.H, v.stop[npx], cut, has_old, it.orec,
+                                                     has_new, it.rec);
+        // compact the active pixels into the first threads (in natural order)
+        const unsigned am = __ballot_sync(0xffffffffu, active);
+        if ((threadIdx.x & 31) == 0) s_wcnt[threadIdx.x >> 5] = __popc(am);
+        __syncthreads();
+        uint32_t before = 0, n_active = 0;
+#pragma unroll
+        for (int w = 0; w < kBT / 32; w++) {
+            const uint32_t c = s_wcnt[w];
+            if (w < (int)(threadIdx.x >> 5)) before += c;
+            n_active += c;
         }
-        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside || same, 0u};
+        if (active) s_pix[before + __popc(am & ((1u << (threadIdx.x & 31)) - 1u))] = (uint16_t)threadIdx.x;
+        __syncthreads();
+        // thread t blends the t-th active pixel; its warp culls against the bounding
+        // box of the warp's active pixels
+        PixGeo ga;
+        const bool mine = threadIdx.x < n_active;
+        int ax = 0x7fffffff, ay = 0x7fffffff, bx = -1, by = -1;
+        uint32_t u = 0;
+        if (mine) {
+            u = s_pix[threadIdx.x];
+            pix_of(tx, ty, (int)u, ga.px, ga.py);
+            ax = bx = ga.px;
+            ay = by = ga.py;
+        }
+        ga.pxc = (float)ga.px + 0.5f;
+        ga.pyc = (float)ga.py + 0.5f;
+        ga.wx0 = (float)__reduce_min_sync(0xffffffffu, ax) + 0.5f;
+        ga.wx1 = (float)__reduce_max_sync(0xffffffffu, bx) + 0.5f;
+        ga.wy0 = (float)__reduce_min_sync(0xffffffffu, ay) + 0.5f;
+        ga.wy1 = (float)__reduce_max_sync(0xffffffffu, by) + 0.5f;
+        ga.inside = mine;
+        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !mine, 0u};
         unsigned int nev = 0, staged = 0;
-        for (uint32_t base = 0; base < L; base += kBT) {
+        for (uint32_t base = 0; base < L && n_active > 0; base += kBT) {
             int cnt = (int)min((uint32_t)kBT, L - base);
             if ((int)threadIdx.x < cnt) {
                 uint32_t m = base + threadIdx.x;
@@ -520,15 +600,24 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
             }
             __syncthreads();
             staged += cnt;
-            blend_batch<COUNT, false>(s, cnt, base, g, p, nev);
+            blend_batch<COUNT, false>(s, cnt, base, ga, p, nev);
             if (__syncthreads_count(p.done) == kBT) break;
         }
         if (COUNT) add_work(work, nev, staged);
-        float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
-        if (same) {
-            v0 = c0;
-            v1 = c1;
-            v2 = c2;
+        if (mine) s_out[u] = make_float3(p.c0 + p.T * 1.0f, p.c1 + p.T * 1.0f, p.c2 + p.T * 1.0f);
+        __syncthreads();
+        // back in natural order: active pixels take their new value, the others
+        // their clean one (Delta = 0)
+        float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+        if (active) {
+            const float3 o = s_out[threadIdx.x];
+            v0 = o.x;
+            v1 = o.y;
+            v2 = o.z;
+        } else if (g.inside) {
+            v0 = v.clean[npx * 3 + 0];
+            v1 = v.clean[npx * 3 + 1];
+            v2 = v.clean[npx * 3 + 2];
         }
         compare_tile(g, v0, v1, v2, v.clean, v.W, &acc[bk]);
         __syncthreads();

@@ -57,21 +57,43 @@ __device__ __forceinline__ bool finite3(float a, float b, float c) {
 // scale decides whether the primitive is culled.
 __device__ __forceinline__ float exp_f32(float x) { return (float)exp((double)x); }
 
-// Conservative half extents of the region where alpha = opac * exp(-q/2) can
-// reach 1/255, for 2D covariance diagonal (a, c); see BlendRec.  Margins (1e-3
-// relative on the quadratic form plus 0.01 px) dwarf fp32 rounding of the
-// blend's own alpha, so culling against the box never changes a pixel.
-__device__ __forceinline__ void cull_extent(float a, float c, float opac, float* ex, float* ey) {
-    float lim = logf(255.0f * opac);   // alpha >= 1/255 needs q <= 2 lim
-    if (lim < -1e-3f) {
+// Conservative half extents of a box that contains every pixel centre where the
+// blend can compute alpha >= 1/255 for this primitive.  The blend evaluates
+// power = -(ca dx^2 + cc dy^2)/2 - cb dx dy in fp32 with every operation
+// rounded, so its result is within g * M of the exact quadratic form of the
+// fp32 conic, M = (|ca| dx^2 + |cc| dy^2)/2 + |cb| |dx dy|, g = 1e-6 (several
+// ulps).  alpha >= 1/255 needs power >= -L, L = ln(255 opac) (+ a margin for
+// the exponential), so candidate pixels satisfy d^T Q'' d <= 2 L with
+// Q'' = [[ca - g (|ca| + |cb|), cb], [cb, cc - g (|cc| + |cb|)]].  If Q'' is
+// positive definite its ellipse's bounding box is returned; otherwise the
+// candidates are unbounded (near-degenerate conics) and the box is infinite.
+// NaN opacity gives NaN extents, which never cull.
+__device__ __forceinline__ void cull_extent(float ca, float cb, float cc, float opac, float* ex, float* ey) {
+    float lim = logf(255.0f * opac);
+    if (lim < -1e-3f) {   // alpha <= opac < 1/255 everywhere
         *ex = -INFINITY;
         *ey = -INFINITY;
         return;
     }
-    if (lim < 0.0f) lim = 0.0f;       // NaN passes through and disables culling
-    float q = 2.0f * lim * 1.001f + 1e-3f;
-    *ex = sqrtf(q * a) + 0.01f;
-    *ey = sqrtf(q * c) + 0.01f;
+    if (isnan(lim)) {
+        *ex = NAN;
+        *ey = NAN;
+        return;
+    }
+    const double g = 1e-6;
+    const double acb = fabs((double)cb);
+    const double qxx = (double)ca - g * (fabs((double)ca) + acb);
+    const double qyy = (double)cc - g * (fabs((double)cc) + acb);
+    const double qxy = (double)cb;
+    const double det = qxx * qyy - qxy * qxy;
+    if (!(qxx > 0.0) || !(det > 0.0)) {
+        *ex = INFINITY;
+        *ey = INFINITY;
+        return;
+    }
+    const double q = 2.0 * ((double)fmaxf(lim, 0.0f) + 1e-3);
+    *ex = (float)(sqrt(q * qyy / det) * (1.0 + 1e-6)) + 0.01f;
+    *ey = (float)(sqrt(q * qxx / det) * (1.0 + 1e-6)) + 0.01f;
 }
 
 // Preprocess one primitive.  `src(w)` returns the float value of word w.
@@ -235,7 +257,7 @@ __device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const De
     rec.cb = cb;
     rec.cc = cc;
     rec.opac = opac;
-    cull_extent(a, c, opac, &rec.ex, &rec.ey);
+    cull_extent(ca, cb, cc, opac, &rec.ex, &rec.ey);
     rec.r = rgb[0];
     rec.g = rgb[1];
     rec.b = rgb[2];
