@@ -29,9 +29,13 @@ gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const
 size_t plan_item_size();
 size_t view_ptrs_size();
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, int W, int H);
+                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, const float4* ck,
+                    const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H);
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
-                                  float* img, uint32_t* stop, uint32_t* tile_stop, cudaStream_t st);
+                                  float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
+                                  const uint32_t* ck_cnt, cudaStream_t st);
+int ck_stride_value();
+int ck_max_per_tile();
 gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_t n, uint32_t* dk, cudaStream_t st);
 gs_status launch_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* ranges, cudaStream_t st);
 uint32_t key_to_bits(uint32_t key, int fmt);
@@ -121,6 +125,9 @@ void free_views(gs_scene* s) {
         cudaFree(v.clean);
         cudaFree(v.stop);
         cudaFree(v.tile_stop);
+        cudaFree(v.ck);
+        cudaFree(v.ck_off);
+        cudaFree(v.ck_cnt);
     }
     s->views.clear();
     s->K = 0;
@@ -149,7 +156,7 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     int cf = std::max(fpv * B, s->cap_flips);
     GS_TRY(dmalloc((void**)&s->flip_stage, sizeof(gs_flip) * cf));
     GS_TRY(dmalloc((void**)&s->desc, sizeof(DirtyDesc) * cb * K));
-    GS_TRY(dmalloc((void**)&s->item_off, sizeof(uint32_t) * (cb * K + 1)));
+    GS_TRY(dmalloc((void**)&s->item_off, sizeof(uint32_t) * (2 * cb * K + 1)));   // offsets + per-pair counts
     GS_TRY(dmalloc((void**)&s->acc, sizeof(CmpAcc) * cb * K));
     GS_TRY(dmalloc((void**)&s->res_stage, sizeof(gs_result) * cb * K));
     GS_TRY(dmalloc((void**)&s->queue, sizeof(unsigned int) * 4));
@@ -466,11 +473,40 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
         GS_CUDA(cudaMemcpyAsync(v.rects, s->work.rects, sizeof(uint2) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ranges, s->work.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
-        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop, st));
+        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop,
+                                       nullptr, nullptr, nullptr, st));
         GS_TRY(launch_gather_depth(v.recs, v.ids, np, v.dk, st));
+        // checkpoints of the clean blend: per tile, every ck_stride list entries up to
+        // (before) the tile's last stop index, at most ck_max_per_tile
+        {
+            std::vector<uint32_t> tstop(ntiles), cnt(ntiles), off(ntiles);
+            std::vector<uint2> rg(ntiles);
+            GS_CUDA(cudaMemcpyAsync(tstop.data(), v.tile_stop, 4 * ntiles, cudaMemcpyDeviceToHost, st));
+            GS_CUDA(cudaMemcpyAsync(rg.data(), v.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToHost, st));
+            GS_CUDA(cudaStreamSynchronize(st));
+            uint64_t total = 0;
+            const uint32_t G = (uint32_t)ck_stride_value();
+            for (int t = 0; t < ntiles; t++) {
+                const uint32_t L = rg[t].y - rg[t].x;
+                const uint32_t last = L > 0 ? std::min(tstop[t], L - 1) : 0u;
+                cnt[t] = std::min(last / G, (uint32_t)ck_max_per_tile());
+                off[t] = (uint32_t)total;
+                total += cnt[t];
+            }
+            if (total >= 0xffffffffull) return set_error(GS_ERR_CAPACITY, "too many blend checkpoints");
+            v.ck_total = total;
+            GS_TRY(dmalloc((void**)&v.ck, sizeof(float4) * kTilePix * std::max<uint64_t>(total, 1)));
+            GS_TRY(dmalloc((void**)&v.ck_off, 4 * ntiles));
+            GS_TRY(dmalloc((void**)&v.ck_cnt, 4 * ntiles));
+            GS_CUDA(cudaMemcpyAsync(v.ck_off, off.data(), 4 * ntiles, cudaMemcpyHostToDevice, st));
+            GS_CUDA(cudaMemcpyAsync(v.ck_cnt, cnt.data(), 4 * ntiles, cudaMemcpyHostToDevice, st));
+            GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop,
+                                           v.ck, v.ck_off, v.ck_cnt, st));
+            GS_CUDA(cudaStreamSynchronize(st));
+        }
         v.npairs = np;
         fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.dk, v.ranges, v.clean, v.stop,
-                       v.tile_stop, v.cam.W, v.cam.H);
+                       v.tile_stop, v.ck, v.ck_off, v.ck_cnt, v.cam.W, v.cam.H);
         crects[k] = v.rects;
         max_pairs = std::max(max_pairs, np);
         max_tiles = std::max(max_tiles, ntiles);

@@ -95,6 +95,10 @@ struct ViewState {
     float* clean = nullptr;          // [H*W*3]
     uint32_t* stop = nullptr;        // [H*W] list index that stopped each clean pixel
     uint32_t* tile_stop = nullptr;   // [ntiles] largest stop index in each tile
+    float4* ck = nullptr;            // clean-blend checkpoints [total][256 pixels]
+    uint32_t* ck_off = nullptr;      // [ntiles]
+    uint32_t* ck_cnt = nullptr;      // [ntiles]
+    uint64_t ck_total = 0;
     uint64_t npairs = 0;
     uint64_t cap_pairs = 0;
 };

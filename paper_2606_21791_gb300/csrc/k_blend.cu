@@ -142,12 +142,28 @@ __device__ __forceinline__ bool blend_alpha(float mx, float my, float ca, float 
 // load per lane, a ballot), then walks only the survivors in list order.  An
 // entry culled here cannot reach alpha >= 1/255 at any of the warp's pixels, so
 // skipping it changes no pixel; a NaN box never culls.
+// Checkpoints of the clean blend: the state (T, C) of every pixel of a tile after
+// each kCkStride list entries, kept for the first `count` positions of the tile.
+constexpr int kCkStride = 64;
+constexpr int kCkMaxPerTile = 64;
+struct CkWrite {
+    float4* ck;      // NULL: no checkpoints
+    uint32_t off;    // first checkpoint of this tile
+    uint32_t count;  // checkpoints of this tile
+};
+
 template <bool COUNT, bool TRACK>
 __device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t base, const PixGeo& g, Pix& p,
-                                            unsigned int& nev) {
+                                            unsigned int& nev, const CkWrite& ckw = CkWrite{nullptr, 0u, 0u}) {
     const int lane = threadIdx.x & 31;
     for (int c = 0; c < cnt; c += 32) {
         if (__all_sync(0xffffffffu, p.done)) return;
+        if (ckw.ck && base + (uint32_t)c > 0 && ((base + (uint32_t)c) % kCkStride) == 0) {
+            // the state after entries [0, base + c) of the list
+            const uint32_t j = (base + (uint32_t)c) / kCkStride;
+            if (j <= ckw.count)
+                ckw.ck[(size_t)(ckw.off + j - 1) * kBT + threadIdx.x] = make_float4(p.T, p.c0, p.c1, p.c2);
+        }
         const int j = c + lane;
         bool pass = false;
         if (j < cnt) {
@@ -241,9 +257,12 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
                                                    const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                    float* __restrict__ img, const float* __restrict__ clean,
                                                    CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop,
-                                                   uint32_t* __restrict__ tile_stop) {
+                                                   uint32_t* __restrict__ tile_stop, float4* __restrict__ ck,
+                                                   const uint32_t* __restrict__ ck_off,
+                                                   const uint32_t* __restrict__ ck_cnt) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
+    const CkWrite ckw{ck, ck ? ck_off[tile] : 0u, ck ? ck_cnt[tile] : 0u};
     const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
     Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, 0xffffffffu};
     const uint2 rg = ranges[tile];
@@ -253,7 +272,7 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
         if ((int)threadIdx.x < cnt) stage_put(s, threadIdx.x, load_rec(recs, ids[base + threadIdx.x]));
         __syncthreads();
         staged += cnt;
-        blend_batch<COUNT, MODE == 2>(s, cnt, base - rg.x, g, p, nev);
+        blend_batch<COUNT, MODE == 2>(s, cnt, base - rg.x, g, p, nev, ckw);
         // also the barrier that lets the next batch overwrite the stage
         if (__syncthreads_count(p.done) == kBT) break;
     }
@@ -328,6 +347,9 @@ struct ViewPtrs {
     const float* clean;
     const uint32_t* stop;    // clean stop index of every pixel
     const uint32_t* tile_stop;   // largest stop index of each tile
+    const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
+    const uint32_t* ck_off;      // first checkpoint of each tile
+    const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
     int W, H, tiles_x, pad;
 };
 
@@ -443,29 +465,47 @@ __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views
         }
         const ViewPtrs v = views[bk % K];
         const int tile = ty * v.tiles_x + tx;
-        const uint2 rg = v.ranges[tile];
         const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
         const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
-        uint32_t pp = 0, ins = 0, cut = 0xffffffffu;
-        if (has_old) {
-            pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(v.recs[d.prim].depth), d.prim) - rg.x;
-            cut = pp;
-        }
-        if (has_new) {
-            ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(d.rec.depth), d.prim) - rg.x;
-            cut = min(cut, ins);   // clean-list position of the insertion
-            if (has_old && pp < ins) ins -= 1;
-        }
-        bool any = false;
         BlendRec orec = d.rec;
-        if (v.tile_stop[tile] >= cut) {
-            if (has_old) orec = v.recs[d.prim];
-            for (int u = lane; u < kBT && !any; u += 32) {
-                int px, py;
-                pix_of(tx, ty, u, px, py);
-                const bool in = px < v.W && py < v.H;
-                const uint32_t st = in ? v.stop[(size_t)py * v.W + px] : 0u;
-                any = __any_sync(0xffffffffu, pixel_active(px, py, v.W, v.H, st, cut, has_old, orec, has_new, d.rec));
+        if (has_old) orec = v.recs[d.prim];
+        // first without the list positions: is any pixel reached by the old or the new record?
+        unsigned reach[kBT / 32];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < kBT / 32; c++) {
+            int px, py;
+            pix_of(tx, ty, c * 32 + lane, px, py);
+            const float x = (float)px + 0.5f, y = (float)py + 0.5f;
+            const bool r = px < v.W && py < v.H &&
+                           ((has_old && affects(orec, x, y)) || (has_new && affects(d.rec, x, y)));
+            reach[c] = __ballot_sync(0xffffffffu, r);
+            any |= reach[c] != 0u;
+        }
+        uint32_t pp = 0, ins = 0, cut = 0xffffffffu;
+        uint2 rg = make_uint2(0u, 0u);
+        if (any) {
+            rg = v.ranges[tile];
+            if (has_old) {
+                pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(orec.depth), d.prim) - rg.x;
+                cut = pp;
+            }
+            if (has_new) {
+                ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(d.rec.depth), d.prim) - rg.x;
+                cut = min(cut, ins);   // clean-list position of the insertion
+                if (has_old && pp < ins) ins -= 1;
+            }
+            // then the reached pixels whose clean blend had not stopped before the change
+            any = false;
+            if (v.tile_stop[tile] >= cut) {
+#pragma unroll
+                for (int c = 0; c < kBT / 32; c++) {
+                    int px, py;
+                    pix_of(tx, ty, c * 32 + lane, px, py);
+                    bool a = false;
+                    if ((reach[c] >> lane) & 1u) a = v.stop[(size_t)py * v.W + px] >= cut;
+                    any |= __any_sync(0xffffffffu, a);
+                }
             }
         }
         if (!any) {   // every pixel keeps its clean value
@@ -585,8 +625,20 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         ga.wy1 = (float)__reduce_max_sync(0xffffffffu, by) + 0.5f;
         ga.inside = mine;
         Pix p{1.0f, 0.0f, 0.0f, 0.0f, !mine, 0u};
+        // The merged list equals the clean list before `cut`, so an active pixel
+        // (not stopped before `cut`) can resume from the clean blend's state at the
+        // last checkpoint at or before `cut`.
+        const uint32_t cstar = min(cut / (uint32_t)kCkStride, v.ck_cnt[it.tile]);
+        const uint32_t start = cstar * (uint32_t)kCkStride;
+        if (mine && cstar > 0) {
+            const float4 st = v.ck[(size_t)(v.ck_off[it.tile] + cstar - 1) * kBT + u];
+            p.T = st.x;
+            p.c0 = st.y;
+            p.c1 = st.z;
+            p.c2 = st.w;
+        }
         unsigned int nev = 0, staged = 0;
-        for (uint32_t base = 0; base < L && n_active > 0; base += kBT) {
+        for (uint32_t base = start; base < L && n_active > 0; base += kBT) {
             int cnt = (int)min((uint32_t)kBT, L - base);
             if ((int)threadIdx.x < cnt) {
                 uint32_t m = base + threadIdx.x;
@@ -663,7 +715,7 @@ gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const ui
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr,
-                                                     nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -674,20 +726,21 @@ gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const 
     if (tx * ty == 0) return GS_OK;
     if (work)
         k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work, nullptr,
-                                                       nullptr);
+                                                       nullptr, nullptr, nullptr, nullptr);
     else
         k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr,
-                                                        nullptr, nullptr);
+                                                        nullptr, nullptr, nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
-                                  float* img, uint32_t* stop, uint32_t* tile_stop, cudaStream_t st) {
+                                  float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
+                                  const uint32_t* ck_cnt, cudaStream_t st) {
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     k_blend_full<2, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr, stop,
-                                                     tile_stop);
+                                                     tile_stop, ck, ck_off, ck_cnt);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -753,8 +806,12 @@ gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_
     return GS_OK;
 }
 
+int ck_stride_value() { return kCkStride; }
+int ck_max_per_tile() { return kCkMaxPerTile; }
+
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, int W, int H) {
+                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, const float4* ck,
+                    const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H) {
     ViewPtrs v;
     v.recs = recs;
     v.ids = ids;
@@ -763,6 +820,9 @@ void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, c
     v.clean = clean;
     v.stop = stop;
     v.tile_stop = tile_stop;
+    v.ck = ck;
+    v.ck_off = ck_off;
+    v.ck_cnt = ck_cnt;
     v.W = W;
     v.H = H;
     v.tiles_x = (W + kTile - 1) / kTile;

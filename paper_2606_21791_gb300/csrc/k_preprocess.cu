@@ -320,102 +320,109 @@ __global__ __launch_bounds__(256) void k_preprocess(const void* planes, uint64_t
 }
 
 // ---------------------------------------------------------------------------
-// Dirty-tile injector: thread (b, k) gathers the flipped primitive's words,
-// XORs the upset in the storage format, optionally guards them (Algorithm 1
-// applied to the only primitive that can leave its box), preprocesses the
-// corrupted primitive for view k and describes the dirty tiles: the union of
-// its clean and corrupted tile rects.  One block; then a block-wide exclusive
-// scan gives each (b, k) its range of work items.  Also zeroes the comparison
-// accumulators and the work-queue counter.
+// Dirty-tile injector: one warp per variant.  The lanes gather the flipped
+// primitive's words, XOR the upset in the storage format and optionally guard
+// them (Algorithm 1 applied to the only primitive that can leave its box); then
+// lane k preprocesses the corrupted primitive for view k and describes the
+// dirty tiles: the union of its clean and corrupted tile rects.  The per-view
+// comparison accumulators are zeroed here (guard clamps reported on view 0).
 // ---------------------------------------------------------------------------
-struct WordSrc {
+struct SharedSrc {
     const float* v;
     __device__ float operator()(int w) const { return v[w]; }
 };
 
+constexpr int kPrepWarps = 8;
+
 template <int FMT>
-__global__ __launch_bounds__(1024) void k_inject_prep(const void* planes, uint64_t n, int nwords, int sh_degree,
-                                                      const DevCamera* cams, int K, const gs_flip* flips, int B,
-                                                      int guard_mode, uint64_t mask, const uint32_t* box,
-                                                      const void* pblo, const void* pbhi, int nbox,
-                                                      const uint2* const* clean_rects, DirtyDesc* desc,
-                                                      uint32_t* item_off, CmpAcc* acc, unsigned int* queue) {
-    const int tid = threadIdx.x;
-    const int total = B * K;
-    uint32_t items = 0;
-    if (tid < total) {
-        const int b = tid / K, k = tid % K;
-        gs_flip f = flips[b];
-        const int nbits = FMT == GS_FP32 ? 32 : 16;
-        bool ok = f.prim < n && f.word < nwords && f.bit < nbits;
-        uint32_t p = ok ? f.prim : 0u;
-        float v[kMaxWords];
-        unsigned int clamps = 0;
-        for (int w = 0; w < nwords; w++) {
-            uint32_t bits = load_bits<FMT>(planes, n, w, p);
-            if (ok && w == f.word) bits ^= (1u << f.bit);
-            float x = decode<FMT>(bits);
-            if (guard_mode >= 0 && ((mask >> w) & 1ull)) {
-                uint32_t lb, hb;
-                if (guard_mode == GS_GUARD_FIELD) {
-                    lb = box[w];
-                    hb = box[kMaxWords + w];
-                } else {
-                    lb = w < nbox ? load_bits<FMT>(pblo, n, w, p) : 0u;
-                    hb = w < nbox ? load_bits<FMT>(pbhi, n, w, p) : 0u;
-                }
-                float lo = decode<FMT>(lb), hi = decode<FMT>(hb);
-                if (!(x >= lo && x <= hi)) {
-                    clamps++;
-                    x = (x > hi) ? hi : lo;
-                }
+__global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
+    const void* planes, uint64_t n, int nwords, int sh_degree, const DevCamera* cams, int K, const gs_flip* flips,
+    int B, int guard_mode, uint64_t mask, const uint32_t* box, const void* pblo, const void* pbhi, int nbox,
+    const uint2* const* clean_rects, DirtyDesc* desc, uint32_t* n_items, CmpAcc* acc) {
+    __shared__ float sv[kPrepWarps][kMaxWords];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int b = blockIdx.x * kPrepWarps + wib;
+    if (b >= B) return;   // whole warps only; no block-wide barrier below
+    const gs_flip f = flips[b];
+    const int nbits = FMT == GS_FP32 ? 32 : 16;
+    const bool ok = f.prim < n && f.word < nwords && f.bit < nbits;
+    const uint32_t p = ok ? f.prim : 0u;
+    unsigned int clamps = 0;
+    for (int w = lane; w < nwords; w += 32) {
+        uint32_t bits = load_bits<FMT>(planes, n, w, p);
+        if (ok && w == f.word) bits ^= (1u << f.bit);
+        float x = decode<FMT>(bits);
+        if (guard_mode >= 0 && ((mask >> w) & 1ull)) {
+            uint32_t lb, hb;
+            if (guard_mode == GS_GUARD_FIELD) {
+                lb = box[w];
+                hb = box[kMaxWords + w];
+            } else {
+                lb = w < nbox ? load_bits<FMT>(pblo, n, w, p) : 0u;
+                hb = w < nbox ? load_bits<FMT>(pbhi, n, w, p) : 0u;
             }
-            v[w] = x;
+            const float lo = decode<FMT>(lb), hi = decode<FMT>(hb);
+            if (!(x >= lo && x <= hi)) {
+                clamps++;
+                x = (x > hi) ? hi : lo;
+            }
         }
-        DirtyDesc d;
-        d.prim = p;
-        uint2 rect = make_uint2(0, 0);
-        float rad = 0.0f;
-        bool nv = ok && preprocess_core(WordSrc{v}, sh_degree, cams[k], d.rec, rect, rad);
-        uint2 orect = ok ? clean_rects[k][p] : make_uint2(0, 0);
-        uint32_t ox0 = orect.x & 0xffff, oy0 = orect.x >> 16, ox1 = orect.y & 0xffff, oy1 = orect.y >> 16;
-        bool ov = ox1 > ox0 && oy1 > oy0;
-        uint32_t nx0 = rect.x & 0xffff, ny0 = rect.x >> 16, nx1 = rect.y & 0xffff, ny1 = rect.y >> 16;
-        if (!nv) nx0 = ny0 = nx1 = ny1 = 0;
-        uint32_t an = nv ? (nx1 - nx0) * (ny1 - ny0) : 0u;
-        uint32_t ao = ov ? (ox1 - ox0) * (oy1 - oy0) : 0u;
-        uint32_t ix = 0, iy = 0;
-        if (nv && ov) {
-            int lx = max((int)nx0, (int)ox0), hx = min((int)nx1, (int)ox1);
-            int ly = max((int)ny0, (int)oy0), hy = min((int)ny1, (int)oy1);
-            ix = hx > lx ? (uint32_t)(hx - lx) : 0u;
-            iy = hy > ly ? (uint32_t)(hy - ly) : 0u;
-        }
-        items = an + ao - ix * iy;
-        d.new_vis = nv;
-        d.old_vis = ov;
-        d.n_items = items;
-        d.nx0 = (uint16_t)nx0;
-        d.ny0 = (uint16_t)ny0;
-        d.nx1 = (uint16_t)nx1;
-        d.ny1 = (uint16_t)ny1;
-        d.ox0 = (uint16_t)ox0;
-        d.oy0 = (uint16_t)oy0;
-        d.ox1 = (uint16_t)ox1;
-        d.oy1 = (uint16_t)oy1;
-        if (!nv) d.rec = BlendRec{0, 0, 0, 0, 0, 0, -INFINITY, -INFINITY, 0, 0, 0, 0};
-        desc[tid] = d;
-        CmpAcc z;
-        z.sse_fx = 0ull;
-        z.maxabs_bits = 0u;
-        z.footprint = 0u;
-        z.nonfinite = 0u;
-        z.clamps = (k == 0) ? clamps : 0u;   // clamps reported once per variant, on view 0
-        acc[tid] = z;
+        sv[wib][w] = x;
     }
-    // block-wide exclusive scan of the item counts
+    clamps = __reduce_add_sync(0xffffffffu, clamps);
+    __syncwarp();
+    if (lane >= K) return;
+    const int k = lane, bk = b * K + k;
+    DirtyDesc d;
+    d.prim = p;
+    uint2 rect = make_uint2(0, 0);
+    float rad = 0.0f;
+    const bool nv = ok && preprocess_core(SharedSrc{sv[wib]}, sh_degree, cams[k], d.rec, rect, rad);
+    const uint2 orect = ok ? clean_rects[k][p] : make_uint2(0, 0);
+    const uint32_t ox0 = orect.x & 0xffff, oy0 = orect.x >> 16, ox1 = orect.y & 0xffff, oy1 = orect.y >> 16;
+    const bool ov = ox1 > ox0 && oy1 > oy0;
+    uint32_t nx0 = rect.x & 0xffff, ny0 = rect.x >> 16, nx1 = rect.y & 0xffff, ny1 = rect.y >> 16;
+    if (!nv) nx0 = ny0 = nx1 = ny1 = 0;
+    const uint32_t an = nv ? (nx1 - nx0) * (ny1 - ny0) : 0u;
+    const uint32_t ao = ov ? (ox1 - ox0) * (oy1 - oy0) : 0u;
+    uint32_t ix = 0, iy = 0;
+    if (nv && ov) {
+        const int lx = max((int)nx0, (int)ox0), hx = min((int)nx1, (int)ox1);
+        const int ly = max((int)ny0, (int)oy0), hy = min((int)ny1, (int)oy1);
+        ix = hx > lx ? (uint32_t)(hx - lx) : 0u;
+        iy = hy > ly ? (uint32_t)(hy - ly) : 0u;
+    }
+    const uint32_t items = an + ao - ix * iy;
+    d.new_vis = nv;
+    d.old_vis = ov;
+    d.n_items = items;
+    d.nx0 = (uint16_t)nx0;
+    d.ny0 = (uint16_t)ny0;
+    d.nx1 = (uint16_t)nx1;
+    d.ny1 = (uint16_t)ny1;
+    d.ox0 = (uint16_t)ox0;
+    d.oy0 = (uint16_t)oy0;
+    d.ox1 = (uint16_t)ox1;
+    d.oy1 = (uint16_t)oy1;
+    if (!nv) d.rec = BlendRec{0, 0, 0, 0, 0, 0, -INFINITY, -INFINITY, 0, 0, 0, 0};
+    desc[bk] = d;
+    n_items[bk] = items;
+    CmpAcc z;
+    z.sse_fx = 0ull;
+    z.maxabs_bits = 0u;
+    z.footprint = 0u;
+    z.nonfinite = 0u;
+    z.clamps = (k == 0) ? clamps : 0u;   // clamps reported once per variant, on view 0
+    acc[bk] = z;
+}
+
+// Exclusive scan of the dirty-tile counts of the B*K (variant, view) pairs
+// (single block of 1024 threads); resets the work-queue counters.
+__global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, int total, uint32_t* item_off,
+                                                     unsigned int* queue) {
     __shared__ uint32_t wsum[32];
-    const int lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t items = tid < total ? n_items[tid] : 0u;
     uint32_t x = items;
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -424,7 +431,7 @@ __global__ __launch_bounds__(1024) void k_inject_prep(const void* planes, uint64
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0u;
+        uint32_t s = wsum[lane];
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
@@ -432,7 +439,7 @@ __global__ __launch_bounds__(1024) void k_inject_prep(const void* planes, uint64
         wsum[lane] = s;
     }
     __syncthreads();
-    uint32_t incl = x + (wid > 0 ? wsum[wid - 1] : 0u);
+    const uint32_t incl = x + (wid > 0 ? wsum[wid - 1] : 0u);
     if (tid < total) item_off[tid] = incl - items;
     if (tid == total - 1) item_off[total] = incl;
     if (tid == 0) {
@@ -477,12 +484,15 @@ gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* r
 gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,
                              int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects, DirtyDesc* desc,
                              uint32_t* item_off, CmpAcc* acc, unsigned int* queue, cudaStream_t st) {
-    if (B * K > 1024) return set_error(GS_ERR_ARG, "B * K must be <= 1024");
-    int threads = ((B * K + 31) / 32) * 32;
-#define GS_PREP(F)                                                                                          \
-    k_inject_prep<F><<<1, threads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, dev_cams, K, flips, B, \
-                                            guard_mode, mask, s->dev_box, s->pbox_lo, s->pbox_hi,            \
-                                            s->nbox_words, dev_clean_rects, desc, item_off, acc, queue)
+    if (B * K > 1024 || K > 32) return set_error(GS_ERR_ARG, "B * K must be <= 1024 and K <= 32");
+    // the per-(variant, view) item counts go to the tail of item_off, past the B*K+1 offsets
+    uint32_t* n_items = item_off + (B * K + 1);
+    const int blocks = (B + kPrepWarps - 1) / kPrepWarps;
+#define GS_PREP(F)                                                                                            \
+    k_inject_prep<F><<<blocks, kPrepWarps * 32, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, dev_cams, K, \
+                                                         flips, B, guard_mode, mask, s->dev_box, s->pbox_lo,    \
+                                                         s->pbox_hi, s->nbox_words, dev_clean_rects, desc,      \
+                                                         n_items, acc)
     if (s->fmt == GS_FP32)
         GS_PREP(GS_FP32);
     else if (s->fmt == GS_FP16)
@@ -490,6 +500,7 @@ gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K
     else
         GS_PREP(GS_BF16);
 #undef GS_PREP
+    k_items_scan<<<1, 1024, 0, st>>>(n_items, B * K, item_off, queue);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

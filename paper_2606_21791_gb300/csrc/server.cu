@@ -72,7 +72,7 @@ uint64_t scene_resident_bytes(const gs_scene* s) {
     if (s->pbox_lo) b += 2ull * s->n * s->nbox_words * word_bytes(s->fmt);
     for (const auto& v : s->views)
         b += s->n * (sizeof(BlendRec) + 8) + v.npairs * 8 + (uint64_t)v.cam.tiles_x * v.cam.tiles_y * 8 +
-             (uint64_t)v.cam.W * v.cam.H * 16;
+             (uint64_t)v.cam.W * v.cam.H * 16 + v.ck_total * 4096 + (uint64_t)v.cam.tiles_x * v.cam.tiles_y * 12;
     b += render_scratch_bytes(s->work.n, s->work.cap_pairs, s->work.ntiles_cap);
     return b;
 }
