@@ -26,6 +26,8 @@ gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* of
 gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
                              void* plan, CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st);
+gs_status launch_finalize_dirty(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K,
+                                cudaStream_t st);
 size_t plan_item_size();
 size_t view_ptrs_size();
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
@@ -33,7 +35,7 @@ void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, c
                     const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H);
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
-                                  const uint32_t* ck_cnt, cudaStream_t st);
+                                  const uint32_t* ck_cnt, unsigned int* clean_nonfin, cudaStream_t st);
 int ck_stride_value();
 int ck_max_per_tile();
 gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_t n, uint32_t* dk, cudaStream_t st);
@@ -134,6 +136,8 @@ void free_views(gs_scene* s) {
     cudaFree(s->dev_cams);
     cudaFree(s->dev_views);
     cudaFree(s->dev_clean_rects);
+    cudaFree(s->clean_nonfin);
+    s->clean_nonfin = nullptr;
     s->dev_cams = nullptr;
     s->dev_views = nullptr;
     s->dev_clean_rects = nullptr;
@@ -191,7 +195,7 @@ gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaS
     GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->acc, s->queue, s->work_ctr,
                               st));
     if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
-    GS_TRY(launch_finalize(s->acc, B * K, s->res_stage, st));
+    GS_TRY(launch_finalize_dirty(s->acc, B * K, s->res_stage, s->clean_nonfin, K, st));
     return GS_OK;
 }
 
@@ -329,6 +333,7 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->queue);
     cudaFree(s->saved);
     cudaFree(s->plan);
+    cudaFree(s->clean_nonfin);
     cudaFree(s->work_ctr);
     if (s->ev_k0) cudaEventDestroy(s->ev_k0);
     if (s->ev_k1) cudaEventDestroy(s->ev_k1);
@@ -451,6 +456,8 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
     std::vector<DevCamera> dcams(K);
     std::vector<char> vptrs(view_ptrs_size() * K);
     std::vector<const uint2*> crects(K);
+    GS_TRY(dmalloc((void**)&s->clean_nonfin, sizeof(unsigned int) * K));
+    GS_CUDA(cudaMemsetAsync(s->clean_nonfin, 0, sizeof(unsigned int) * K, st));
     uint64_t max_pairs = 0;
     int max_tiles = 0;
     for (int k = 0; k < K; k++) {
@@ -474,7 +481,7 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
         GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ranges, s->work.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
         GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop,
-                                       nullptr, nullptr, nullptr, st));
+                                       nullptr, nullptr, nullptr, s->clean_nonfin + k, st));
         GS_TRY(launch_gather_depth(v.recs, v.ids, np, v.dk, st));
         // checkpoints of the clean blend: per tile, every ck_stride list entries up to
         // (before) the tile's last stop index, at most ck_max_per_tile
@@ -501,7 +508,7 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
             GS_CUDA(cudaMemcpyAsync(v.ck_off, off.data(), 4 * ntiles, cudaMemcpyHostToDevice, st));
             GS_CUDA(cudaMemcpyAsync(v.ck_cnt, cnt.data(), 4 * ntiles, cudaMemcpyHostToDevice, st));
             GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop,
-                                           v.ck, v.ck_off, v.ck_cnt, st));
+                                           v.ck, v.ck_off, v.ck_cnt, nullptr, st));
             GS_CUDA(cudaStreamSynchronize(st));
         }
         v.npairs = np;

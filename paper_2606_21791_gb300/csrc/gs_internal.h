@@ -16,7 +16,7 @@ namespace gs {
 constexpr int kTile = 16;             // render tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;
 constexpr int kMaxWords = 59;
-constexpr int kSseFracBits = 39;      // fixed-point scale of per-tile squared-error sums
+constexpr int kSseFracBits = 39;      // fixed-point scale of per-pixel squared errors (3 * 2^39 * 5.1e6 px < 2^64)
 
 // ----------------------------------------------------------------------------
 // error reporting
@@ -64,11 +64,13 @@ struct DevCamera {
 // Per (variant, view) comparison accumulator (integer/ordered atomics only, so
 // the result does not depend on the order in which tiles finish).
 struct CmpAcc {
-    unsigned long long sse_fx;  // sum of per-tile float SSE, fixed point 2^-kSseFracBits
+    unsigned long long sse_fx;  // sum of per-pixel squared errors, each rounded to fixed point 2^-kSseFracBits
     unsigned int maxabs_bits;   // float bits of the max |diff| (non-negative floats order as uints)
     unsigned int footprint;
     unsigned int nonfinite;
     unsigned int clamps;
+    unsigned int clean_nonfinite_replaced;   // dirty engine: re-blended pixels whose clean value was non-finite
+    unsigned int pad;
 };
 
 // Dirty-tile work descriptor of one (variant, view).
@@ -170,6 +172,7 @@ struct gs_scene {
     unsigned int* queue = nullptr;
     void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
     uint64_t plan_cap = 0;
+    unsigned int* clean_nonfin = nullptr;   // [K] non-finite pixels of each clean view
     uint32_t* saved = nullptr;
     bool use_graphs = true;
     int batch = 0;                          // variants per dirty-tile launch (0: default)

@@ -152,10 +152,54 @@ struct CkWrite {
     uint32_t count;  // checkpoints of this tile
 };
 
+// One list entry at one pixel: the front-to-back step.  Every operation has
+// explicit rounding, so the full-frame, clean and dirty-tile kernels compute the
+// same bits wherever this is inlined.  Returns true when the pixel stops here.
+__device__ __forceinline__ bool blend_entry(const float4 q0, const float4 q1, float qb, float pxc, float pyc, Pix& p) {
+    float alpha;
+    if (!blend_alpha(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, pxc, pyc, alpha)) return false;
+    alpha = alpha > 0.99f ? 0.99f : alpha;     // keeps NaN
+    const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
+    if (Tn < 1e-4f) {
+        p.done = true;
+        return true;
+    }
+    const float w = __fmul_rn(alpha, p.T);
+    p.c0 = __fmaf_rn(q1.z, w, p.c0);
+    p.c1 = __fmaf_rn(q1.w, w, p.c1);
+    p.c2 = __fmaf_rn(qb, w, p.c2);
+    p.T = Tn;
+    return false;
+}
+
+// Entries [c, c + 32) of a staged batch for one warp: cull 32 boxes against the
+// warp's pixel block with one ballot, then walk the survivors in list order.  An
+// entry culled here cannot reach alpha >= 1/255 at any of the warp's pixels, so
+// skipping it changes no pixel; a NaN box never culls.
+template <bool COUNT, bool TRACK>
+__device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s, const float4* q1s, const float* qbs,
+                                            int c, int cnt, uint32_t base, const PixGeo& g, Pix& p,
+                                            unsigned int& nev) {
+    const int lane = threadIdx.x & 31;
+    const int j = c + lane;
+    bool pass = false;
+    if (j < cnt) {
+        const float4 bx = box[j];
+        pass = !(bx.y < g.wx0 || bx.x > g.wx1 || bx.w < g.wy0 || bx.z > g.wy1);
+    }
+    unsigned m = __ballot_sync(0xffffffffu, pass);
+    while (m) {
+        const int e = c + __ffs(m) - 1;
+        m &= m - 1;
+        if (p.done) continue;
+        if (COUNT) nev++;
+        if (blend_entry(q0s[e], q1s[e], qbs[e], g.pxc, g.pyc, p) && TRACK) p.stop = base + (uint32_t)e;
+    }
+}
+
 template <bool COUNT, bool TRACK>
 __device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t base, const PixGeo& g, Pix& p,
                                             unsigned int& nev, const CkWrite& ckw = CkWrite{nullptr, 0u, 0u}) {
-    const int lane = threadIdx.x & 31;
     for (int c = 0; c < cnt; c += 32) {
         if (__all_sync(0xffffffffu, p.done)) return;
         if (ckw.ck && base + (uint32_t)c > 0 && ((base + (uint32_t)c) % kCkStride) == 0) {
@@ -164,76 +208,63 @@ __device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t ba
             if (j <= ckw.count)
                 ckw.ck[(size_t)(ckw.off + j - 1) * kBT + threadIdx.x] = make_float4(p.T, p.c0, p.c1, p.c2);
         }
-        const int j = c + lane;
-        bool pass = false;
-        if (j < cnt) {
-            const float4 bx = s.box[j];
-            pass = !(bx.y < g.wx0 || bx.x > g.wx1 || bx.w < g.wy0 || bx.z > g.wy1);
-        }
-        unsigned m = __ballot_sync(0xffffffffu, pass);
-        while (m) {
-            const int e = c + __ffs(m) - 1;
-            m &= m - 1;
-            if (p.done) continue;
-            if (COUNT) nev++;
-            const float4 q0 = s.q0[e];
-            const float4 q1 = s.q1[e];
-            float alpha;
-            if (!blend_alpha(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, g.pxc, g.pyc, alpha)) continue;
-            alpha = alpha > 0.99f ? 0.99f : alpha;     // keeps NaN
-            const float Tn = p.T * (1.0f - alpha);
-            if (Tn < 1e-4f) {
-                p.done = true;
-                if (TRACK) p.stop = base + (uint32_t)e;
-                continue;
-            }
-            const float w = alpha * p.T;
-            p.c0 = p.c0 + q1.z * w;
-            p.c1 = p.c1 + q1.w * w;
-            p.c2 = p.c2 + s.qb[e] * w;
-            p.T = Tn;
-        }
+        blend_chunk<COUNT, TRACK>(s.box, s.q0, s.q1, s.qb, c, cnt, base, g, p, nev);
     }
 }
 
 __device__ __forceinline__ float clamp01(float v) { return v > 0.0f ? (v < 1.0f ? v : 1.0f) : 0.0f; }
 
-// Compare this tile's pixels with the clean image and add to *acc.
+// One pixel's comparison terms: squared error of the [0,1]-clamped values in
+// fixed point (integer sums do not depend on the order of accumulation), peak
+// |difference|, footprint flag (> 1/255), non-finite flag of the new value.
+struct PixCmp {
+    unsigned long long fx;
+    float m;
+    bool foot, nonfin;
+};
+
+__device__ __forceinline__ PixCmp pixel_compare(float v0, float v1, float v2, const float* c) {
+    PixCmp r;
+    const float d0 = clamp01(v0) - clamp01(c[0]);
+    const float d1 = clamp01(v1) - clamp01(c[1]);
+    const float d2 = clamp01(v2) - clamp01(c[2]);
+    const float sq = d0 * d0 + d1 * d1 + d2 * d2;
+    r.fx = __float2ull_rn(sq * 549755813888.0f);   // 2^kSseFracBits
+    r.m = fmaxf(fmaxf(fabsf(d0), fabsf(d1)), fabsf(d2));   // differences are finite
+    r.foot = r.m > 1.0f / 255.0f;
+    r.nonfin = !(isfinite(v0) && isfinite(v1) && isfinite(v2));
+    return r;
+}
+
+// Compare this tile's pixels with the clean image and add to *acc (whole block).
 __device__ __forceinline__ void compare_tile(const PixGeo& g, float v0, float v1, float v2, const float* clean, int W,
                                              CmpAcc* acc) {
-    __shared__ float wsse[kBT / 32];
+    __shared__ unsigned long long wsse[kBT / 32];
     __shared__ float wmax[kBT / 32];
-    float sq = 0.0f, m = 0.0f;
-    bool foot = false, nonfin = false;
-    if (g.inside) {
-        const float* c = clean + ((size_t)g.py * W + g.px) * 3;
-        float d0 = clamp01(v0) - clamp01(c[0]);
-        float d1 = clamp01(v1) - clamp01(c[1]);
-        float d2 = clamp01(v2) - clamp01(c[2]);
-        sq = d0 * d0 + d1 * d1 + d2 * d2;
-        m = fmaxf(fmaxf(fabsf(d0), fabsf(d1)), fabsf(d2));   // differences are finite
-        foot = m > 1.0f / 255.0f;
-        nonfin = !(isfinite(v0) && isfinite(v1) && isfinite(v2));
-    }
+    PixCmp r{0ull, 0.0f, false, false};
+    if (g.inside) r = pixel_compare(v0, v1, v2, clean + ((size_t)g.py * W + g.px) * 3);
+    unsigned long long fx = r.fx;
+    float m = r.m;
     for (int o = 16; o > 0; o >>= 1) {
-        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        wsse[warp] = sq;
+        wsse[warp] = fx;
         wmax[warp] = m;
     }
-    int nfoot = __syncthreads_count(foot);
-    int nbad = __syncthreads_count(nonfin);
+    int nfoot = __syncthreads_count(r.foot);
+    int nbad = __syncthreads_count(r.nonfin);
     if (threadIdx.x == 0) {
-        float t = 0.0f, mm = 0.0f;
+        unsigned long long t = 0;
+        float mm = 0.0f;
 #pragma unroll
         for (int w = 0; w < kBT / 32; w++) {
             t += wsse[w];
             mm = fmaxf(mm, wmax[w]);
         }
-        if (t > 0.0f) atomicAdd(&acc->sse_fx, __float2ull_rn(t * 549755813888.0f));   // 2^kSseFracBits
+        if (t) atomicAdd(&acc->sse_fx, t);
         if (mm > 0.0f) atomicMax(&acc->maxabs_bits, __float_as_uint(mm));
         if (nfoot) atomicAdd(&acc->footprint, (unsigned)nfoot);
         if (nbad) atomicAdd(&acc->nonfinite, (unsigned)nbad);
@@ -259,7 +290,8 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
                                                    CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop,
                                                    uint32_t* __restrict__ tile_stop, float4* __restrict__ ck,
                                                    const uint32_t* __restrict__ ck_off,
-                                                   const uint32_t* __restrict__ ck_cnt) {
+                                                   const uint32_t* __restrict__ ck_cnt,
+                                                   unsigned int* __restrict__ clean_nonfin) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
     const CkWrite ckw{ck, ck ? ck_off[tile] : 0u, ck ? ck_cnt[tile] : 0u};
@@ -277,7 +309,7 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
         if (__syncthreads_count(p.done) == kBT) break;
     }
     if (COUNT) add_work(work, nev, staged);
-    const float v0 = p.c0 + p.T * 1.0f, v1 = p.c1 + p.T * 1.0f, v2 = p.c2 + p.T * 1.0f;
+    const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
     if (MODE != 1) {
         if (g.inside) {
             const size_t px = (size_t)g.py * W + g.px;
@@ -286,6 +318,11 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
             o[1] = v1;
             o[2] = v2;
             if (MODE == 2) stop[px] = p.stop;
+        }
+        if (MODE == 2 && clean_nonfin) {
+            const bool bad = g.inside && !(isfinite(v0) && isfinite(v1) && isfinite(v2));
+            const int nbad = __syncthreads_count(bad);
+            if (threadIdx.x == 0 && nbad) atomicAdd(clean_nonfin, (unsigned)nbad);
         }
         if (MODE == 2) {
             // the tile's largest stop index: a change at or after it leaves every pixel as it is
@@ -318,7 +355,9 @@ __global__ __launch_bounds__(kBT) void k_compare(const float* __restrict__ a, co
     compare_tile(g, v0, v1, v2, b, W, acc);
 }
 
-__global__ void k_finalize(const CmpAcc* acc, int count, gs_result* out) {
+// clean_nonfin (dirty engine only): per view, the clean image's non-finite
+// pixels, which count for every variant except where a pixel was re-blended.
+__global__ void k_finalize(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     CmpAcc a = acc[i];
@@ -326,14 +365,14 @@ __global__ void k_finalize(const CmpAcc* acc, int count, gs_result* out) {
     r.sse = (double)a.sse_fx * (1.0 / 549755813888.0);
     r.maxabs = __uint_as_float(a.maxabs_bits);
     r.footprint = a.footprint;
-    r.nonfinite = a.nonfinite;
+    r.nonfinite = a.nonfinite + (clean_nonfin ? clean_nonfin[i % K] - a.clean_nonfinite_replaced : 0u);
     r.clamps = a.clamps;
     out[i] = r;
 }
 
 __global__ void k_zero_acc(CmpAcc* acc, int count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u};
+    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u, 0u, 0u};
 }
 
 // ---------------------------------------------------------------------------
@@ -382,12 +421,14 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
     return lo + __popc(__ballot_sync(0xffffffffu, less));
 }
 
-// One dirty tile that needs re-blending (128 B).  ins is the insertion position
+// One dirty tile that needs re-blending (160 B).  ins is the insertion position
 // in the clean list without the primitive's old entry; cut is the first changed
-// position of the clean list; rec is the corrupted record (when flags bit 1).
+// position of the clean list; rec is the corrupted record (when flags bit 1);
+// mask marks the tile's active pixels (natural order, 8 x 32 bits).
 struct __align__(16) PlanItem {
     BlendRec rec;
     BlendRec orec;    // clean (old) record
+    uint32_t mask[kBT / 32];
     uint32_t bk;      // (variant, view) = variant * K + view
     uint32_t tile;
     uint32_t s, e;    // clean list range
@@ -401,6 +442,42 @@ struct __align__(16) PlanItem {
 // alpha < 1/255, decided by the blend's own arithmetic): the state changes of
 // its blend are then those of the clean blend.  Every other pixel is "active"
 // and must be re-blended.
+// Conservative tile test, all in fp32: false only if the blend cannot reach
+// alpha >= 1/255 for record q at any pixel centre of the rectangle
+// [x0, x1] x [y0, y1].  The blend's offsets d = mean - pixel are fp32
+// differences, and rounding is monotone, so every pixel's d lies in the box
+// spanned by the rounded corner offsets.  Its power is -q(d)/2 for
+// q(d) = ca dx^2 + 2 cb dx dy + cc dy^2 up to a few ulps of
+// M = ((|ca| + |cb|) max dx^2 + (|cc| + |cb|) max dy^2)/2 >= the sum of |terms|;
+// g = 1e-5 covers that and the rounding of this test's own q (both about
+// 1e-6 M).  alpha >= 1/255 needs -q/2 + g M >= -L with L = ln(255 opacity)
+// + 1e-3 (the margin covers the fast log and exp2), so the rectangle is
+// unreachable when the minimum of q over it exceeds 2 L + 2 g M.  With ca, cc > 0
+// the minimum over each edge is that of a convex 1-D quadratic; it is 0 if the
+// mean lies inside (then: reachable).  NaN opacity, or terms near overflow
+// (where the blend's own power can be NaN, which it blends): reachable.
+__device__ __forceinline__ bool tile_reachable(const BlendRec& q, float x0, float x1, float y0, float y1) {
+    const float ca = q.ca, cb = q.cb, cc = q.cc;
+    const float L = __logf(255.0f * q.opac) + 1e-3f;
+    if (L < 0.0f) return false;   // alpha <= opacity < 1/255 everywhere (with margin); NaN falls through
+    if (!(ca > 0.0f) || !(cc > 0.0f) || !(L < 3.0e38f)) return true;
+    const float dx0 = q.mx - x1, dx1 = q.mx - x0;
+    const float dy0 = q.my - y1, dy1 = q.my - y0;
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
+    const float mdx = fmaxf(dx0 * dx0, dx1 * dx1), mdy = fmaxf(dy0 * dy0, dy1 * dy1);
+    const float M = 0.5f * ((ca + fabsf(cb)) * mdx + (cc + fabsf(cb)) * mdy);
+    if (!(M < 1.0e37f)) return true;   // terms near overflow: the blend's power may be NaN
+    auto qf = [&](float dx, float dy) { return ca * dx * dx + 2.0f * cb * dx * dy + cc * dy * dy; };
+    const float rca = 1.0f / ca, rcc = 1.0f / cc;
+    // the nearest point of each edge (dx fixed: dy = -cb dx / cc; dy fixed: dx = -cb dy / ca), clamped to it
+    const float e0 = qf(dx0, fminf(fmaxf(-cb * dx0 * rcc, dy0), dy1));
+    const float e1 = qf(dx1, fminf(fmaxf(-cb * dx1 * rcc, dy0), dy1));
+    const float e2 = qf(fminf(fmaxf(-cb * dy0 * rca, dx0), dx1), dy0);
+    const float e3 = qf(fminf(fmaxf(-cb * dy1 * rca, dx0), dx1), dy1);
+    const float qmin = fminf(fminf(e0, e1), fminf(e2, e3));
+    return !(qmin > 2.0f * L + 2.0e-5f * M);
+}
+
 __device__ __forceinline__ bool affects(const BlendRec& q, float x, float y) {
     float alpha;
     return blend_alpha(q.mx, q.my, q.ca, q.cb, q.cc, q.opac, x, y, alpha);
@@ -417,10 +494,11 @@ __device__ __forceinline__ bool pixel_active(int px, int py, int W, int H, uint3
 // Decodes the tile, finds the removal and insertion positions with warp
 // searches, and drops the tile when none of its pixels is active (Delta = 0
 // there); the rest are appended to the plan.
+// counts[1]: plan items (tiles), zeroed by the injector.
 template <bool COUNT>
 __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
                                              const uint32_t* __restrict__ item_off, int BK, int K,
-                                             PlanItem* __restrict__ plan, unsigned int* __restrict__ plan_count,
+                                             PlanItem* __restrict__ plan, unsigned int* __restrict__ counts,
                                              unsigned long long* work) {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -472,6 +550,17 @@ __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views
         // first without the list positions: is any pixel reached by the old or the new record?
         unsigned reach[kBT / 32];
         bool any = false;
+        {
+            const float rx0 = (float)(tx * kTile) + 0.5f, ry0 = (float)(ty * kTile) + 0.5f;
+            const float rx1 = fminf((float)(tx * kTile + kTile - 1), (float)(v.W - 1)) + 0.5f;
+            const float ry1 = fminf((float)(ty * kTile + kTile - 1), (float)(v.H - 1)) + 0.5f;
+            const bool near_old = has_old && tile_reachable(orec, rx0, rx1, ry0, ry1);
+            const bool near_new = has_new && tile_reachable(d.rec, rx0, rx1, ry0, ry1);
+            if (!near_old && !near_new) {
+                skipped++;
+                continue;
+            }
+        }
 #pragma unroll
         for (int c = 0; c < kBT / 32; c++) {
             int px, py;
@@ -504,7 +593,8 @@ __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views
                     pix_of(tx, ty, c * 32 + lane, px, py);
                     bool a = false;
                     if ((reach[c] >> lane) & 1u) a = v.stop[(size_t)py * v.W + px] >= cut;
-                    any |= __any_sync(0xffffffffu, a);
+                    reach[c] = __ballot_sync(0xffffffffu, a);   // now: active pixels
+                    any |= reach[c] != 0u;
                 }
             }
         }
@@ -516,6 +606,8 @@ __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views
             PlanItem it;
             it.rec = d.rec;
             it.orec = orec;
+#pragma unroll
+            for (int c = 0; c < kBT / 32; c++) it.mask[c] = reach[c];
             it.bk = (uint32_t)bk;
             it.tile = (uint32_t)tile;
             it.s = rg.x;
@@ -524,7 +616,7 @@ __global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views
             it.ins = ins;
             it.cut = cut;
             it.flags = (has_old ? 1u : 0u) | (has_new ? 2u : 0u);
-            plan[atomicAdd(plan_count, 1u)] = it;
+            plan[atomicAdd(&counts[1], 1u)] = it;
         }
     }
     if (COUNT && lane == 0 && skipped) atomicAdd(&work[3], (unsigned long long)skipped);
@@ -552,7 +644,7 @@ __device__ __forceinline__ void fetch_plan_async(PlanItem* dst, const PlanItem* 
 template <bool COUNT>
 __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ views, int K,
                                                  const PlanItem* __restrict__ plan,
-                                                 const unsigned int* __restrict__ plan_count,
+                                                 const unsigned int* __restrict__ counts,
                                                  CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
                                                  unsigned long long* work) {
     __shared__ Stage s;
@@ -561,7 +653,7 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
     __shared__ uint32_t s_wcnt[kBT / 32];
     __shared__ uint16_t s_pix[kBT];
     __shared__ float3 s_out[kBT];
-    const uint32_t total = *plan_count;
+    const uint32_t total = counts[1];
     bool have = false;   // thread 0: pbuf[cur] holds (or is receiving) an item
     int cur = 0;
     if (threadIdx.x == 0) {
@@ -590,8 +682,7 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         const bool has_old = it.flags & 1u, has_new = it.flags & 2u;
         const uint32_t L = (it.e - it.s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         const size_t npx = g.inside ? (size_t)g.py * v.W + g.px : 0;
-        const bool active = g.inside && pixel_active(g.px, g.py, v.W, v.H, v.stop[npx], cut, has_old, it.orec,
-                                                     has_new, it.rec);
+        const bool active = (it.mask[threadIdx.x >> 5] >> (threadIdx.x & 31)) & 1u;   // decided by the plan
         // compact the active pixels into the first threads (in natural order)
         const unsigned am = __ballot_sync(0xffffffffu, active);
         if ((threadIdx.x & 31) == 0) s_wcnt[threadIdx.x >> 5] = __popc(am);
@@ -656,22 +747,26 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
             if (__syncthreads_count(p.done) == kBT) break;
         }
         if (COUNT) add_work(work, nev, staged);
-        if (mine) s_out[u] = make_float3(p.c0 + p.T * 1.0f, p.c1 + p.T * 1.0f, p.c2 + p.T * 1.0f);
+        if (mine) s_out[u] = make_float3(__fadd_rn(p.c0, p.T), __fadd_rn(p.c1, p.T), __fadd_rn(p.c2, p.T));
         __syncthreads();
-        // back in natural order: active pixels take their new value, the others
-        // their clean one (Delta = 0)
+        // back in natural order: only the active pixels are compared; every other
+        // pixel keeps its clean value (Delta = 0), and the clean image's non-finite
+        // pixels are counted once per view at finalize
         float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
         if (active) {
             const float3 o = s_out[threadIdx.x];
             v0 = o.x;
             v1 = o.y;
             v2 = o.z;
-        } else if (g.inside) {
-            v0 = v.clean[npx * 3 + 0];
-            v1 = v.clean[npx * 3 + 1];
-            v2 = v.clean[npx * 3 + 2];
         }
-        compare_tile(g, v0, v1, v2, v.clean, v.W, &acc[bk]);
+        PixGeo gc = g;
+        gc.inside = active;
+        compare_tile(gc, v0, v1, v2, v.clean, v.W, &acc[bk]);
+        // re-blended pixels whose clean value was non-finite (their clean count is withdrawn at finalize)
+        const bool clean_bad = active && !(isfinite(v.clean[npx * 3]) && isfinite(v.clean[npx * 3 + 1]) &&
+                                           isfinite(v.clean[npx * 3 + 2]));
+        const int ncb = __syncthreads_count(clean_bad);
+        if (threadIdx.x == 0 && ncb) atomicAdd(&acc[bk].clean_nonfinite_replaced, (unsigned)ncb);
         __syncthreads();
         cur ^= 1;
     }
@@ -715,7 +810,7 @@ gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const ui
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr,
-                                                     nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -726,21 +821,21 @@ gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const 
     if (tx * ty == 0) return GS_OK;
     if (work)
         k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work, nullptr,
-                                                       nullptr, nullptr, nullptr, nullptr);
+                                                       nullptr, nullptr, nullptr, nullptr, nullptr);
     else
         k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr,
-                                                        nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
-                                  const uint32_t* ck_cnt, cudaStream_t st) {
+                                  const uint32_t* ck_cnt, unsigned int* clean_nonfin, cudaStream_t st) {
     int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tx * ty == 0) return GS_OK;
     k_blend_full<2, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr, stop,
-                                                     tile_stop, ck, ck_off, ck_cnt);
+                                                     tile_stop, ck, ck_off, ck_cnt, clean_nonfin);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -762,7 +857,15 @@ gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st) {
 
 gs_status launch_finalize(const CmpAcc* acc, int count, gs_result* out, cudaStream_t st) {
     if (count <= 0) return GS_OK;
-    k_finalize<<<(count + 255) / 256, 256, 0, st>>>(acc, count, out);
+    k_finalize<<<(count + 255) / 256, 256, 0, st>>>(acc, count, out, nullptr, 1);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_finalize_dirty(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K,
+                                cudaStream_t st) {
+    if (count <= 0) return GS_OK;
+    k_finalize<<<(count + 255) / 256, 256, 0, st>>>(acc, count, out, clean_nonfin, K);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -780,18 +883,18 @@ int dirty_grid() {
 
 size_t plan_item_size() { return sizeof(PlanItem); }
 
-// queue[0]: blend work queue, queue[1]: plan item count (both zeroed by the injector)
+// queue[0]: blend work queue, queue[1]: plan items (both zeroed by the injector)
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
                              void* plan, CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st) {
     const ViewPtrs* views = (const ViewPtrs*)dev_views;
     PlanItem* pl = (PlanItem*)plan;
     const int plan_blocks = num_sms() * 8;
     if (work) {
-        k_plan<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue + 1, work);
-        k_dirty<true><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue + 1, acc, queue, work);
+        k_plan<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue, work);
+        k_dirty<true><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, work);
     } else {
-        k_plan<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue + 1, nullptr);
-        k_dirty<false><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue + 1, acc, queue, nullptr);
+        k_plan<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue, nullptr);
+        k_dirty<false><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, nullptr);
     }
     GS_CUDA(cudaGetLastError());
     return GS_OK;

@@ -413,6 +413,8 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     z.footprint = 0u;
     z.nonfinite = 0u;
     z.clamps = (k == 0) ? clamps : 0u;   // clamps reported once per variant, on view 0
+    z.clean_nonfinite_replaced = 0u;
+    z.pad = 0u;
     acc[bk] = z;
 }
 
