@@ -282,7 +282,7 @@ def main():
             ev[j][0].record(stream)
             step(args.warmup + j)
             ev[j][1].record(stream)
-            kern_ms.append(G.gs_read_kernel_ms(h))
+            kern_ms.append(G.gs_read_kernel_ms(h))   # (plan, blend + compare)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         torch.cuda.nvtx.range_pop()
@@ -340,7 +340,8 @@ def main():
     sm_mhz = clocks["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    kavg = sum(kern_ms) / len(kern_ms) / 1000.0
+    kavg = sum(k[1] for k in kern_ms) / len(kern_ms) / 1000.0
+    plan_avg = sum(k[0] for k in kern_ms) / len(kern_ms) / 1000.0
     evals_per_launch = work["evaluations"] / args.steps
     achieved = evals_per_launch * FLOP_PER_EVAL / kavg / 1e12
     tr = traffic_record()
@@ -349,8 +350,13 @@ def main():
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x median SM clock {sm_mhz:.0f} MHz under load",
                 "work_per_launch": {"evaluations": evals_per_launch, "flop_per_eval": FLOP_PER_EVAL,
-                                    "tiles": work["tiles"] / args.steps, "entries": work["entries"] / args.steps},
-                "kernel_ms_avg": kavg * 1000.0, "kernel_share_of_step": kavg * 1000.0 / (sum(step_ms) / len(step_ms))}
+                                    "tiles": work["tiles"] / args.steps, "entries": work["entries"] / args.steps,
+                                    "tiles_dropped_by_plan": work["tiles_unchanged"] / args.steps,
+                                    "plan_drops": {k: work[k] / args.steps for k in
+                                                   ("dropped_stop_key", "dropped_tile_reach", "dropped_no_reach",
+                                                    "dropped_pixel_stop")}},
+                "kernel_ms_avg": kavg * 1000.0, "kernel_share_of_step": kavg * 1000.0 / (sum(step_ms) / len(step_ms)),
+                "plan_kernel_ms_avg": plan_avg * 1000.0}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

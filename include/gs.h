@@ -199,22 +199,27 @@ GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_f
                                     int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
 /* Enable (default) or disable CUDA-graph replay of the batched dirty-tile step. */
 GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
-/* Work counters for measurement: while enabled, the blend kernels count
- * pixel-primitive evaluations, tiles blended, list entries staged and dirty
- * tiles left untouched because every pixel stopped before the change (graphs
- * are bypassed).  gs_read_work copies those 4 counts and resets them
+/* Work counters for measurement: while enabled, the dirty-tile kernels add
+ * up, per batch: [0] pixel-primitive evaluations, [1] tiles blended, [2] list
+ * entries staged, [3] dirty tiles dropped by the plan (every pixel keeps its
+ * clean value), of which [4] by the stop-key test, [5] by the tile reach
+ * test, [6] because no pixel is reached, [7] because every reached pixel
+ * stopped before the change (graphs are bypassed while counting).
+ * gs_read_work copies those 8 counts into host_counts[8] and resets them
  * (synchronises). */
 GS_API gs_status gs_count_work(gs_scene* scene, int enable);
 GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
-/* Kernel timing for measurement: while enabled, CUDA events bracket the
- * dirty-tile kernel of each batch on the caller's stream (also inside the
- * captured graph); gs_read_kernel_ms returns the last batch's kernel time. */
+/* Kernel timing for measurement: while enabled, CUDA events bracket the two
+ * dirty-tile kernels of each batch on the caller's stream (also inside the
+ * captured graph).  gs_read_kernel_ms waits for the last batch and writes
+ * ms[0] = the two plan kernels' time, ms[1] = the blend + compare kernel's time
+ * (host array of 2 floats).  GS_ERR_STATE while timing is off. */
 GS_API gs_status gs_time_kernels(gs_scene* scene, int enable);
 GS_API gs_status gs_read_kernel_ms(gs_scene* scene, float* ms);
-/* Variants per dirty-tile launch (0 = largest allowed, min(64, 1024 / K)). */
+/* Variants per dirty-tile launch (0 = largest allowed, min(256, 1024 / K)). */
 GS_API gs_status gs_set_batch(gs_scene* scene, int batch);
 /* Autotuner: times the campaign over dev_flips[0, count) at batch sizes
- * 8, 16, 32, 64 (those <= 1024 / K), keeps the fastest for this scene and
+ * 8, 16, 32, 64, 128, 256 (those <= min(256, 1024 / K)), keeps the fastest for this scene and
  * returns it (and its time per variant in microseconds, may be NULL).
  * Synchronises the stream. */
 GS_API gs_status gs_autotune(gs_scene* scene, const gs_flip* dev_flips, int count, int guard_mode, uint64_t word_mask,

@@ -18,20 +18,25 @@ gs_status launch_apply_flips(void* planes, int fmt, uint64_t n, int nwords, cons
 gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects, uint32_t* keys,
                             uint32_t* vals, gs_record* dbg, cudaStream_t st);
 gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,
-                             int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects, DirtyDesc* desc,
-                             uint32_t* item_off, CmpAcc* acc, unsigned int* queue, cudaStream_t st);
+                             int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects,
+                             const BlendRec* const* dev_clean_recs, DirtyDesc* desc, uint32_t* item_off, CmpAcc* acc,
+                             unsigned int* queue, cudaStream_t st);
 gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, uint32_t** ids_out, cudaStream_t st);
 gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* offsets, const unsigned long long* total,
                                    cudaStream_t st);
 gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             void* plan, CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st);
+                             void* plan, uint2* cand, CmpAcc* acc, unsigned int* queue, unsigned long long* work,
+                             cudaEvent_t ev_mid, cudaStream_t st);
 gs_status launch_finalize_dirty(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K,
                                 cudaStream_t st);
 size_t plan_item_size();
 size_t view_ptrs_size();
+gs_status launch_stop_keys(const uint2* ranges, const uint32_t* tile_stop, const uint32_t* dk, const uint32_t* ids,
+                           int ntiles, unsigned long long* out, cudaStream_t st);
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, const float4* ck,
+                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop,
+                    const unsigned long long* stop_key, const float4* ck,
                     const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H);
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
@@ -127,6 +132,7 @@ void free_views(gs_scene* s) {
         cudaFree(v.clean);
         cudaFree(v.stop);
         cudaFree(v.tile_stop);
+        cudaFree(v.stop_key);
         cudaFree(v.ck);
         cudaFree(v.ck_off);
         cudaFree(v.ck_cnt);
@@ -136,11 +142,13 @@ void free_views(gs_scene* s) {
     cudaFree(s->dev_cams);
     cudaFree(s->dev_views);
     cudaFree(s->dev_clean_rects);
+    cudaFree(s->dev_clean_recs);
     cudaFree(s->clean_nonfin);
     s->clean_nonfin = nullptr;
     s->dev_cams = nullptr;
     s->dev_views = nullptr;
     s->dev_clean_rects = nullptr;
+    s->dev_clean_recs = nullptr;
 }
 
 gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
@@ -155,7 +163,9 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     cudaFree(s->queue);
     cudaFree(s->saved);
     cudaFree(s->plan);
+    cudaFree(s->cand);
     s->plan = nullptr;
+    s->cand = nullptr;
     int cb = std::max(B, s->cap_B);
     int cf = std::max(fpv * B, s->cap_flips);
     GS_TRY(dmalloc((void**)&s->flip_stage, sizeof(gs_flip) * cf));
@@ -168,10 +178,15 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     // every (variant, view) can dirty at most every tile of its view
     s->plan_cap = (uint64_t)cb * K * (uint64_t)std::max(s->max_tiles, 1);
     GS_TRY(dmalloc(&s->plan, plan_item_size() * s->plan_cap));
+    GS_TRY(dmalloc((void**)&s->cand, sizeof(uint2) * s->plan_cap));
     s->cap_B = cb;
     s->cap_flips = cf;
     return GS_OK;
 }
+
+// Variants per dirty-tile launch: the injector's scan covers at most 1024
+// (variant, view) pairs in one block.
+int max_batch(int K) { return std::max(1, std::min(kMaxBatch, 1024 / K)); }
 
 gs_status check_flip_args(gs_scene* s, const gs_flip* flips, int B, int fpv, int guard_mode, uint64_t mask) {
     if (!s || (!flips && B > 0) || B < 0 || fpv < 1) return set_error(GS_ERR_ARG, "bad campaign arguments");
@@ -189,11 +204,12 @@ gs_status check_flip_args(gs_scene* s, const gs_flip* flips, int B, int fpv, int
 gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaStream_t st) {
     int K = s->K;
     GS_TRY(launch_inject_prep(s, s->dev_cams, K, s->flip_stage, B, guard_mode, mask,
-                              (const uint2* const*)s->dev_clean_rects, s->desc, s->item_off, s->acc, s->queue, st));
+                              (const uint2* const*)s->dev_clean_rects, (const BlendRec* const*)s->dev_clean_recs,
+                              s->desc, s->item_off, s->acc, s->queue, st));
     // external records: inside a stream capture they become event-record nodes of the graph
     if (s->ev_k0) GS_CUDA(cudaEventRecordWithFlags(s->ev_k0, st, cudaEventRecordExternal));
-    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->acc, s->queue, s->work_ctr,
-                              st));
+    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->cand, s->acc, s->queue,
+                              s->work_ctr, s->ev_kp, st));
     if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
     GS_TRY(launch_finalize_dirty(s->acc, B * K, s->res_stage, s->clean_nonfin, K, st));
     return GS_OK;
@@ -333,9 +349,11 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->queue);
     cudaFree(s->saved);
     cudaFree(s->plan);
+    cudaFree(s->cand);
     cudaFree(s->clean_nonfin);
     cudaFree(s->work_ctr);
     if (s->ev_k0) cudaEventDestroy(s->ev_k0);
+    if (s->ev_kp) cudaEventDestroy(s->ev_kp);
     if (s->ev_k1) cudaEventDestroy(s->ev_k1);
     delete s;
     return GS_OK;
@@ -456,6 +474,7 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
     std::vector<DevCamera> dcams(K);
     std::vector<char> vptrs(view_ptrs_size() * K);
     std::vector<const uint2*> crects(K);
+    std::vector<const BlendRec*> crecs(K);
     GS_TRY(dmalloc((void**)&s->clean_nonfin, sizeof(unsigned int) * K));
     GS_CUDA(cudaMemsetAsync(s->clean_nonfin, 0, sizeof(unsigned int) * K, st));
     uint64_t max_pairs = 0;
@@ -476,6 +495,7 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
         GS_TRY(dmalloc((void**)&v.clean, sizeof(float) * (size_t)v.cam.W * v.cam.H * 3));
         GS_TRY(dmalloc((void**)&v.stop, sizeof(uint32_t) * (size_t)v.cam.W * v.cam.H));
         GS_TRY(dmalloc((void**)&v.tile_stop, sizeof(uint32_t) * ntiles));
+        GS_TRY(dmalloc((void**)&v.stop_key, sizeof(unsigned long long) * ntiles));
         GS_CUDA(cudaMemcpyAsync(v.recs, s->work.recs, sizeof(BlendRec) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.rects, s->work.rects, sizeof(uint2) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
@@ -511,19 +531,23 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
                                            v.ck, v.ck_off, v.ck_cnt, nullptr, st));
             GS_CUDA(cudaStreamSynchronize(st));
         }
+        GS_TRY(launch_stop_keys(v.ranges, v.tile_stop, v.dk, v.ids, ntiles, v.stop_key, st));
         v.npairs = np;
         fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.dk, v.ranges, v.clean, v.stop,
-                       v.tile_stop, v.ck, v.ck_off, v.ck_cnt, v.cam.W, v.cam.H);
+                       v.tile_stop, v.stop_key, v.ck, v.ck_off, v.ck_cnt, v.cam.W, v.cam.H);
         crects[k] = v.rects;
+        crecs[k] = v.recs;
         max_pairs = std::max(max_pairs, np);
         max_tiles = std::max(max_tiles, ntiles);
     }
     GS_TRY(dmalloc((void**)&s->dev_cams, sizeof(DevCamera) * K));
     GS_TRY(dmalloc(&s->dev_views, vptrs.size()));
     GS_TRY(dmalloc((void**)&s->dev_clean_rects, sizeof(uint2*) * K));
+    GS_TRY(dmalloc((void**)&s->dev_clean_recs, sizeof(BlendRec*) * K));
     GS_CUDA(cudaMemcpyAsync(s->dev_cams, dcams.data(), sizeof(DevCamera) * K, cudaMemcpyHostToDevice, st));
     GS_CUDA(cudaMemcpyAsync(s->dev_views, vptrs.data(), vptrs.size(), cudaMemcpyHostToDevice, st));
     GS_CUDA(cudaMemcpyAsync(s->dev_clean_rects, crects.data(), sizeof(uint2*) * K, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(s->dev_clean_recs, crecs.data(), sizeof(BlendRec*) * K, cudaMemcpyHostToDevice, st));
     // the plain loop re-renders a single-flip variant: at most one primitive
     // changes, adding at most one grid's worth of pairs
     s->full_cap_pairs = max_pairs + (uint64_t)max_tiles + 1024;
@@ -552,7 +576,7 @@ gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int
         return gs_inject_and_render_full(s, dev_flips, B, flips_per_variant, guard_mode, word_mask, dev_out, stream);
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
-    const int max_chunk = std::max(1, std::min(64, 1024 / K));
+    const int max_chunk = max_batch(K);
     const int chunk = s->batch > 0 ? std::min(s->batch, max_chunk) : max_chunk;
     GS_TRY(ensure_batch_buffers(s, chunk, 1));
     for (int b0 = 0; b0 < B; b0 += chunk) {
@@ -672,8 +696,8 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
     if (count < 1 || !best_batch) return set_error(GS_ERR_ARG, "bad gs_autotune arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
-    const int max_chunk = std::max(1, std::min(64, 1024 / K));
-    const int cands[4] = {8, 16, 32, 64};
+    const int max_chunk = max_batch(K);
+    const int cands[6] = {8, 16, 32, 64, 128, 256};
     gs_result* out = nullptr;
     GS_CUDA(cudaMallocAsync((void**)&out, sizeof(gs_result) * (size_t)count * K, st));
     cudaEvent_t e0, e1;
@@ -728,7 +752,7 @@ gs_status gs_count_work(gs_scene* s, int enable) {
 gs_status gs_read_work(gs_scene* s, uint64_t* host_counts) {
     if (!s || !host_counts) return set_error(GS_ERR_ARG, "NULL argument");
     if (!s->work_ctr) return set_error(GS_ERR_STATE, "work counting is off");
-    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost));
     GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 8));
     return GS_OK;
 }
@@ -738,12 +762,14 @@ gs_status gs_time_kernels(gs_scene* s, int enable) {
     destroy_graphs(s);   // the event records are part of the captured graph
     if (enable && !s->ev_k0) {
         GS_CUDA(cudaEventCreate(&s->ev_k0));
+        GS_CUDA(cudaEventCreate(&s->ev_kp));
         GS_CUDA(cudaEventCreate(&s->ev_k1));
     }
     if (!enable && s->ev_k0) {
         cudaEventDestroy(s->ev_k0);
+        cudaEventDestroy(s->ev_kp);
         cudaEventDestroy(s->ev_k1);
-        s->ev_k0 = s->ev_k1 = nullptr;
+        s->ev_k0 = s->ev_kp = s->ev_k1 = nullptr;
     }
     return GS_OK;
 }
@@ -752,7 +778,8 @@ gs_status gs_read_kernel_ms(gs_scene* s, float* ms) {
     if (!s || !ms) return set_error(GS_ERR_ARG, "NULL argument");
     if (!s->ev_k0) return set_error(GS_ERR_STATE, "kernel timing is off");
     GS_CUDA(cudaEventSynchronize(s->ev_k1));
-    GS_CUDA(cudaEventElapsedTime(ms, s->ev_k0, s->ev_k1));
+    GS_CUDA(cudaEventElapsedTime(&ms[0], s->ev_k0, s->ev_kp));
+    GS_CUDA(cudaEventElapsedTime(&ms[1], s->ev_kp, s->ev_k1));
     return GS_OK;
 }
 

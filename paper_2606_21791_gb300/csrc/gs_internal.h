@@ -16,6 +16,7 @@ namespace gs {
 constexpr int kTile = 16;             // render tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;
 constexpr int kMaxWords = 59;
+constexpr int kMaxBatch = 256;        // variants per dirty-tile launch (also <= 1024 / views)
 constexpr int kSseFracBits = 39;      // fixed-point scale of per-pixel squared errors (3 * 2^39 * 5.1e6 px < 2^64)
 
 // ----------------------------------------------------------------------------
@@ -82,6 +83,8 @@ struct DirtyDesc {
     uint32_t n_items;      // dirty tiles
     uint16_t nx0, ny0, nx1, ny1;   // corrupted rect
     uint16_t ox0, oy0, ox1, oy1;   // clean rect
+    float old_depth;       // clean primitive's depth (when old_vis)
+    uint32_t pad[3];
 };
 
 // ----------------------------------------------------------------------------
@@ -97,6 +100,7 @@ struct ViewState {
     float* clean = nullptr;          // [H*W*3]
     uint32_t* stop = nullptr;        // [H*W] list index that stopped each clean pixel
     uint32_t* tile_stop = nullptr;   // [ntiles] largest stop index in each tile
+    unsigned long long* stop_key = nullptr;   // [ntiles] (depth bits << 32 | id) of the entry at tile_stop (~0: none)
     float4* ck = nullptr;            // clean-blend checkpoints [total][256 pixels]
     uint32_t* ck_off = nullptr;      // [ntiles]
     uint32_t* ck_cnt = nullptr;      // [ntiles]
@@ -157,6 +161,7 @@ struct gs_scene {
     gs::DevCamera* dev_cams = nullptr;
     void* dev_views = nullptr;              // ViewPtrs[K]
     void* dev_clean_rects = nullptr;        // const uint2*[K]
+    void* dev_clean_recs = nullptr;         // const BlendRec*[K]
     uint64_t full_cap_pairs = 0;
     int max_tiles = 0;
     gs::RenderWork work;                    // scratch of the full render pipeline
@@ -171,14 +176,16 @@ struct gs_scene {
     gs_result* res_stage = nullptr;
     unsigned int* queue = nullptr;
     void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
+    uint2* cand = nullptr;                  // candidate tiles of the plan's first pass [plan_cap]
     uint64_t plan_cap = 0;
     unsigned int* clean_nonfin = nullptr;   // [K] non-finite pixels of each clean view
     uint32_t* saved = nullptr;
     bool use_graphs = true;
     int batch = 0;                          // variants per dirty-tile launch (0: default)
     unsigned long long* work_ctr = nullptr; // work counters, non-NULL while counting is on (no graphs then)
-    cudaEvent_t ev_k0 = nullptr;            // bracket the dirty-tile kernel of the last batch (timing on)
-    cudaEvent_t ev_k1 = nullptr;
+    cudaEvent_t ev_k0 = nullptr;            // timing on: before the plan kernel of the last batch,
+    cudaEvent_t ev_kp = nullptr;            // between the plan and the blend kernel,
+    cudaEvent_t ev_k1 = nullptr;            // after the blend kernel
     std::vector<gs::GraphEntry> graphs;
 };
 

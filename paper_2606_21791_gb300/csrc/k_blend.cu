@@ -386,6 +386,7 @@ struct ViewPtrs {
     const float* clean;
     const uint32_t* stop;    // clean stop index of every pixel
     const uint32_t* tile_stop;   // largest stop index of each tile
+    const unsigned long long* stop_key;   // (depth bits, id) of the list entry at tile_stop; ~0 if none
     const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
     const uint32_t* ck_off;      // first checkpoint of each tile
     const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
@@ -421,13 +422,12 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
     return lo + __popc(__ballot_sync(0xffffffffu, less));
 }
 
-// One dirty tile that needs re-blending (160 B).  ins is the insertion position
+// One dirty tile that needs re-blending (112 B).  ins is the insertion position
 // in the clean list without the primitive's old entry; cut is the first changed
 // position of the clean list; rec is the corrupted record (when flags bit 1);
 // mask marks the tile's active pixels (natural order, 8 x 32 bits).
 struct __align__(16) PlanItem {
     BlendRec rec;
-    BlendRec orec;    // clean (old) record
     uint32_t mask[kBT / 32];
     uint32_t bk;      // (variant, view) = variant * K + view
     uint32_t tile;
@@ -435,6 +435,9 @@ struct __align__(16) PlanItem {
     uint32_t pp, ins, cut;
     uint32_t flags;   // bit 0: old entry in this tile, bit 1: corrupted entry in this tile
 };
+static_assert(sizeof(PlanItem) == 112 && offsetof(PlanItem, mask) == 48 && offsetof(PlanItem, bk) == 80 &&
+                  offsetof(PlanItem, pp) == 96,
+              "k_plan writes PlanItem as 7 16-byte parts");
 
 // A pixel of a dirty tile keeps its clean value, bit for bit, when its clean
 // blend stopped before the first changed list position, or when its blend skips
@@ -483,143 +486,210 @@ __device__ __forceinline__ bool affects(const BlendRec& q, float x, float y) {
     return blend_alpha(q.mx, q.my, q.ca, q.cb, q.cc, q.opac, x, y, alpha);
 }
 
-__device__ __forceinline__ bool pixel_active(int px, int py, int W, int H, uint32_t stop, uint32_t cut, bool has_old,
-                                             const BlendRec& orec, bool has_new, const BlendRec& nrec) {
-    if (px >= W || py >= H || stop < cut) return false;
-    const float x = (float)px + 0.5f, y = (float)py + 0.5f;
-    return (has_old && affects(orec, x, y)) || (has_new && affects(nrec, x, y));
+// (variant, view) of a work item: the last bk with off[bk] <= item.
+__device__ __forceinline__ int item_owner(const uint32_t* off, int BK, uint32_t item) {
+    int lo = 0, hi = BK - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
-// Plan: one warp per (variant, view, dirty tile) work item, grid-strided.
-// Decodes the tile, finds the removal and insertion positions with warp
-// searches, and drops the tile when none of its pixels is active (Delta = 0
-// there); the rest are appended to the plan.
-// counts[1]: plan items (tiles), zeroed by the injector.
+// Tile of the j-th dirty tile of a (variant, view): the corrupted rect row-major,
+// then the tiles of the clean rect outside it, row-major.  The clean rect minus
+// the corrupted one is three bands: the rows above their overlap (full width),
+// the overlapping rows (minus the overlap's columns) and the rows below.
+__device__ __forceinline__ void item_tile(const DirtyDesc& d, uint32_t j, int& tx, int& ty) {
+    const uint32_t wn = (uint32_t)d.nx1 - d.nx0;
+    const uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
+    if (j < an) {
+        tx = d.nx0 + (int)(j % wn);
+        ty = d.ny0 + (int)(j / wn);
+        return;
+    }
+    uint32_t r = j - an;
+    const uint32_t w0 = (uint32_t)d.ox1 - d.ox0;
+    const int lx = max((int)d.ox0, (int)d.nx0), hx = min((int)d.ox1, (int)d.nx1);
+    const int ly = max((int)d.oy0, (int)d.ny0), hy = min((int)d.oy1, (int)d.ny1);
+    if (d.new_vis && hx > lx && hy > ly) {
+        const uint32_t above = (uint32_t)(ly - d.oy0) * w0;
+        if (r >= above) {
+            r -= above;
+            const uint32_t wb = w0 - (uint32_t)(hx - lx), left = (uint32_t)(lx - d.ox0);
+            const uint32_t band = (uint32_t)(hy - ly) * wb;
+            if (r < band) {
+                const uint32_t q = r % wb;
+                ty = ly + (int)(r / wb);
+                tx = q < left ? d.ox0 + (int)q : hx + (int)(q - left);
+                return;
+            }
+            r -= band;
+            ty = hy + (int)(r / w0);
+            tx = d.ox0 + (int)(r % w0);
+            return;
+        }
+    }
+    ty = d.oy0 + (int)(r / w0);
+    tx = d.ox0 + (int)(r % w0);
+}
+
+// Plan, first pass: one (variant, view, dirty tile) work item per thread.
+// Decodes the tile and drops it when every pixel's clean blend stopped before
+// the first changed list position (stop-key test, exact) or when neither
+// changed record can reach it (conservative tile test); the others are
+// appended to cand as (bk, tx | ty << 16), counted in counts[2].
 template <bool COUNT>
-__global__ __launch_bounds__(256) void k_plan(const ViewPtrs* __restrict__ views, const DirtyDesc* __restrict__ desc,
-                                             const uint32_t* __restrict__ item_off, int BK, int K,
-                                             PlanItem* __restrict__ plan, unsigned int* __restrict__ counts,
-                                             unsigned long long* work) {
+__global__ __launch_bounds__(256) void k_plan_filter(const ViewPtrs* __restrict__ views,
+                                                    const DirtyDesc* __restrict__ desc,
+                                                    const uint32_t* __restrict__ item_off, int BK, int K,
+                                                    uint2* __restrict__ cand, unsigned int* __restrict__ counts,
+                                                    unsigned long long* work) {
+    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_off[1025];   // item_off[0, BK], BK <= 1024
+    for (int i = threadIdx.x; i <= BK; i += blockDim.x) s_off[i] = item_off[i];
+    __syncthreads();
+    const uint32_t total = s_off[BK];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned int drop_key = 0, drop_box = 0;
+    // warp-uniform trip count (the ballot below needs the whole warp)
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const uint32_t item = base + (uint32_t)lane;
+        bool keep = false;
+        int bk = 0, tx = 0, ty = 0;
+        if (item < total) {
+            bk = item_owner(s_off, BK, item);
+            const DirtyDesc& d = desc[bk];
+            item_tile(d, item - s_off[bk], tx, ty);
+            const ViewPtrs& v = views[bk % K];
+            const int tile = ty * v.tiles_x + tx;
+            const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
+            const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
+            // every pixel of the tile stopped before the first changed list position
+            // (tile_stop < cut) exactly when the entry at tile_stop sorts below the
+            // keys of both changed entries
+            unsigned long long kmin = ~0ull;
+            if (has_old) kmin = ((unsigned long long)__float_as_uint(d.old_depth) << 32) | d.prim;
+            if (has_new) kmin = min(kmin, ((unsigned long long)__float_as_uint(d.rec.depth) << 32) | d.prim);
+            const bool stopped = v.stop_key[tile] < kmin;
+            if (!stopped) {
+                const float rx0 = (float)(tx * kTile) + 0.5f, ry0 = (float)(ty * kTile) + 0.5f;
+                const float rx1 = fminf((float)(tx * kTile + kTile - 1), (float)(v.W - 1)) + 0.5f;
+                const float ry1 = fminf((float)(ty * kTile + kTile - 1), (float)(v.H - 1)) + 0.5f;
+                keep = (has_new && tile_reachable(d.rec, rx0, rx1, ry0, ry1)) ||
+                       (has_old && tile_reachable(v.recs[d.prim], rx0, rx1, ry0, ry1));
+            }
+            if (COUNT && !keep) (stopped ? drop_key : drop_box)++;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m) {
+            uint32_t b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&counts[2], (unsigned)__popc(m));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (keep)
+                cand[b0 + __popc(m & ((1u << lane) - 1u))] =
+                    make_uint2((uint32_t)bk, (uint32_t)tx | ((uint32_t)ty << 16));
+        }
+    }
+    if (COUNT) {
+        const unsigned k = __reduce_add_sync(0xffffffffu, drop_key), x = __reduce_add_sync(0xffffffffu, drop_box);
+        if (lane == 0 && (k + x)) {
+            atomicAdd(&work[3], (unsigned long long)(k + x));
+            atomicAdd(&work[4], (unsigned long long)k);
+            atomicAdd(&work[5], (unsigned long long)x);
+        }
+    }
+}
+
+// Plan, second pass: one warp per candidate tile (grid-strided, so the
+// expensive tiles spread over all warps).  The exact per-pixel reach test, the
+// removal and insertion positions (warp searches) and the per-pixel stop test;
+// a tile with an active pixel is appended to the plan (counts[1]), any other
+// keeps its clean values (Delta = 0).
+template <bool COUNT>
+__global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restrict__ views,
+                                                      const DirtyDesc* __restrict__ desc, int K,
+                                                      const uint2* __restrict__ cand, PlanItem* __restrict__ plan,
+                                                      unsigned int* __restrict__ counts, unsigned long long* work) {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t total = item_off[BK];
-    unsigned int skipped = 0;
-    for (uint32_t item = warp; item < total; item += nwarps) {
-        // (variant, view) of this item: last bk with item_off[bk] <= item
-        int lo = 0, hi = BK - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
-        }
-        const int bk = lo;
-        const DirtyDesc& d = desc[bk];
-        const uint32_t j = item - item_off[bk];
-        int tx = 0, ty = 0;
-        const uint32_t wn = (uint32_t)d.nx1 - d.nx0;
-        const uint32_t an = d.new_vis ? wn * ((uint32_t)d.ny1 - d.ny0) : 0u;
-        if (j < an) {
-            tx = d.nx0 + (int)(j % wn);
-            ty = d.ny0 + (int)(j / wn);
-        } else {
-            // tiles of the clean rect that are not in the corrupted rect, row-major
-            uint32_t r = j - an;
-            for (int y = d.oy0; y < d.oy1; y++) {
-                int ex0 = d.ox0, ex1 = d.ox0;   // excluded x range of this row
-                if (d.new_vis && y >= d.ny0 && y < d.ny1) {
-                    ex0 = max((int)d.ox0, (int)d.nx0);
-                    ex1 = min((int)d.ox1, (int)d.nx1);
-                    if (ex1 < ex0) ex1 = ex0;
-                }
-                const uint32_t left = (uint32_t)(ex0 - d.ox0);
-                const uint32_t row = (uint32_t)(d.ox1 - d.ox0) - (uint32_t)(ex1 - ex0);
-                if (r < row) {
-                    ty = y;
-                    tx = r < left ? d.ox0 + (int)r : ex1 + (int)(r - left);
-                    break;
-                }
-                r -= row;
-            }
-        }
-        const ViewPtrs v = views[bk % K];
-        const int tile = ty * v.tiles_x + tx;
-        const bool has_old = d.old_vis && tx >= d.ox0 && tx < d.ox1 && ty >= d.oy0 && ty < d.oy1;
-        const bool has_new = d.new_vis && tx >= d.nx0 && tx < d.nx1 && ty >= d.ny0 && ty < d.ny1;
-        BlendRec orec = d.rec;
-        if (has_old) orec = v.recs[d.prim];
-        // first without the list positions: is any pixel reached by the old or the new record?
+    const uint32_t n = counts[2];
+    unsigned int drop_reach = 0, drop_stop = 0;
+    for (uint32_t i = warp; i < n; i += nwarps) {
+        const uint2 c = cand[i];
+        const int ibk = (int)c.x, itx = (int)(c.y & 0xffffu), ity = (int)(c.y >> 16);
+        const DirtyDesc& d = desc[ibk];
+        const ViewPtrs& v = views[ibk % K];
+        const int tile = ity * v.tiles_x + itx;
+        const bool has_old = d.old_vis && itx >= d.ox0 && itx < d.ox1 && ity >= d.oy0 && ity < d.oy1;
+        const bool has_new = d.new_vis && itx >= d.nx0 && itx < d.nx1 && ity >= d.ny0 && ity < d.ny1;
+        const BlendRec nrec = d.rec;
+        const BlendRec orec = has_old ? v.recs[d.prim] : nrec;
+        const uint32_t prim = d.prim;
         unsigned reach[kBT / 32];
         bool any = false;
-        {
-            const float rx0 = (float)(tx * kTile) + 0.5f, ry0 = (float)(ty * kTile) + 0.5f;
-            const float rx1 = fminf((float)(tx * kTile + kTile - 1), (float)(v.W - 1)) + 0.5f;
-            const float ry1 = fminf((float)(ty * kTile + kTile - 1), (float)(v.H - 1)) + 0.5f;
-            const bool near_old = has_old && tile_reachable(orec, rx0, rx1, ry0, ry1);
-            const bool near_new = has_new && tile_reachable(d.rec, rx0, rx1, ry0, ry1);
-            if (!near_old && !near_new) {
-                skipped++;
-                continue;
-            }
-        }
 #pragma unroll
-        for (int c = 0; c < kBT / 32; c++) {
+        for (int q = 0; q < kBT / 32; q++) {
             int px, py;
-            pix_of(tx, ty, c * 32 + lane, px, py);
+            pix_of(itx, ity, q * 32 + lane, px, py);
             const float x = (float)px + 0.5f, y = (float)py + 0.5f;
             const bool r = px < v.W && py < v.H &&
-                           ((has_old && affects(orec, x, y)) || (has_new && affects(d.rec, x, y)));
-            reach[c] = __ballot_sync(0xffffffffu, r);
-            any |= reach[c] != 0u;
+                           ((has_old && affects(orec, x, y)) || (has_new && affects(nrec, x, y)));
+            reach[q] = __ballot_sync(0xffffffffu, r);
+            any |= reach[q] != 0u;
         }
         uint32_t pp = 0, ins = 0, cut = 0xffffffffu;
         uint2 rg = make_uint2(0u, 0u);
         if (any) {
             rg = v.ranges[tile];
             if (has_old) {
-                pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(orec.depth), d.prim) - rg.x;
+                pp = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(orec.depth), prim) - rg.x;
                 cut = pp;
             }
             if (has_new) {
-                ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(d.rec.depth), d.prim) - rg.x;
+                ins = warp_lower_bound(v.dk, v.ids, rg.x, rg.y, __float_as_uint(nrec.depth), prim) - rg.x;
                 cut = min(cut, ins);   // clean-list position of the insertion
                 if (has_old && pp < ins) ins -= 1;
             }
             // then the reached pixels whose clean blend had not stopped before the change
             any = false;
-            if (v.tile_stop[tile] >= cut) {
 #pragma unroll
-                for (int c = 0; c < kBT / 32; c++) {
-                    int px, py;
-                    pix_of(tx, ty, c * 32 + lane, px, py);
-                    bool a = false;
-                    if ((reach[c] >> lane) & 1u) a = v.stop[(size_t)py * v.W + px] >= cut;
-                    reach[c] = __ballot_sync(0xffffffffu, a);   // now: active pixels
-                    any |= reach[c] != 0u;
-                }
+            for (int q = 0; q < kBT / 32; q++) {
+                int px, py;
+                pix_of(itx, ity, q * 32 + lane, px, py);
+                bool a = false;
+                if ((reach[q] >> lane) & 1u) a = v.stop[(size_t)py * v.W + px] >= cut;
+                reach[q] = __ballot_sync(0xffffffffu, a);   // now: active pixels
+                any |= reach[q] != 0u;
             }
         }
         if (!any) {   // every pixel keeps its clean value
-            skipped++;
+            if (COUNT) (cut == 0xffffffffu ? drop_reach : drop_stop)++;
             continue;
         }
-        if (lane == 0) {
-            PlanItem it;
-            it.rec = d.rec;
-            it.orec = orec;
-#pragma unroll
-            for (int c = 0; c < kBT / 32; c++) it.mask[c] = reach[c];
-            it.bk = (uint32_t)bk;
-            it.tile = (uint32_t)tile;
-            it.s = rg.x;
-            it.e = rg.y;
-            it.pp = pp;
-            it.ins = ins;
-            it.cut = cut;
-            it.flags = (has_old ? 1u : 0u) | (has_new ? 2u : 0u);
-            plan[atomicAdd(&counts[1], 1u)] = it;
+        // the item's 7 16-byte parts, one per lane
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(&counts[1], 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        uint4* dst = reinterpret_cast<uint4*>(&plan[slot]);
+        if (lane < 3) {
+            dst[lane] = reinterpret_cast<const uint4*>(&d.rec)[lane];
+        } else if (lane == 3) {
+            dst[3] = make_uint4(reach[0], reach[1], reach[2], reach[3]);
+        } else if (lane == 4) {
+            dst[4] = make_uint4(reach[4], reach[5], reach[6], reach[7]);
+        } else if (lane == 5) {
+            dst[5] = make_uint4((uint32_t)ibk, (uint32_t)tile, rg.x, rg.y);
+        } else if (lane == 6) {
+            dst[6] = make_uint4(pp, ins, cut, (has_old ? 1u : 0u) | (has_new ? 2u : 0u));
         }
     }
-    if (COUNT && lane == 0 && skipped) atomicAdd(&work[3], (unsigned long long)skipped);
+    if (COUNT && lane == 0 && (drop_reach + drop_stop)) {   // warp-uniform counts
+        atomicAdd(&work[3], (unsigned long long)(drop_reach + drop_stop));
+        atomicAdd(&work[6], (unsigned long long)drop_reach);
+        atomicAdd(&work[7], (unsigned long long)drop_stop);
+    }
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -883,19 +953,28 @@ int dirty_grid() {
 
 size_t plan_item_size() { return sizeof(PlanItem); }
 
-// queue[0]: blend work queue, queue[1]: plan items (both zeroed by the injector)
+// ev_mid (optional): recorded between the plan kernels and the blend kernel.
+// queue[0]: blend work queue, queue[1]: plan items, queue[2]: candidate tiles
+// (all zeroed by the injector); cand holds as many entries as plan.
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             void* plan, CmpAcc* acc, unsigned int* queue, unsigned long long* work, cudaStream_t st) {
+                             void* plan, uint2* cand, CmpAcc* acc, unsigned int* queue, unsigned long long* work,
+                             cudaEvent_t ev_mid, cudaStream_t st) {
     const ViewPtrs* views = (const ViewPtrs*)dev_views;
     PlanItem* pl = (PlanItem*)plan;
     const int plan_blocks = num_sms() * 8;
     if (work) {
-        k_plan<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue, work);
-        k_dirty<true><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, work);
+        k_plan_filter<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, cand, queue, work);
+        k_plan_exact<true><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, queue, work);
     } else {
-        k_plan<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, pl, queue, nullptr);
-        k_dirty<false><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, nullptr);
+        k_plan_filter<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, cand, queue, nullptr);
+        k_plan_exact<false><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, queue, nullptr);
     }
+    if (ev_mid) {
+        cudaError_t e = cudaEventRecordWithFlags(ev_mid, st, cudaEventRecordExternal);
+        if (e != cudaSuccess) return set_error(GS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (work) k_dirty<true><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, work);
+    else k_dirty<false><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -912,8 +991,32 @@ gs_status launch_gather_depth(const BlendRec* recs, const uint32_t* ids, uint64_
 int ck_stride_value() { return kCkStride; }
 int ck_max_per_tile() { return kCkMaxPerTile; }
 
+// Per tile: the sort key (depth bits << 32 | id) of the list entry at which the
+// last of its pixels stopped; ~0 when some pixel never stopped.  Every pixel of
+// the tile stopped before a change whose key is above it.
+__global__ void k_stop_keys(const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_stop,
+                            const uint32_t* __restrict__ dk, const uint32_t* __restrict__ ids, int ntiles,
+                            unsigned long long* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint2 rg = ranges[t];
+    const uint32_t ts = tile_stop[t];
+    unsigned long long key = ~0ull;
+    if (ts != 0xffffffffu && ts < rg.y - rg.x)
+        key = ((unsigned long long)dk[rg.x + ts] << 32) | (unsigned long long)ids[rg.x + ts];
+    out[t] = key;
+}
+
+gs_status launch_stop_keys(const uint2* ranges, const uint32_t* tile_stop, const uint32_t* dk, const uint32_t* ids,
+                           int ntiles, unsigned long long* out, cudaStream_t st) {
+    if (ntiles > 0) k_stop_keys<<<(ntiles + 255) / 256, 256, 0, st>>>(ranges, tile_stop, dk, ids, ntiles, out);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
 void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop, const float4* ck,
+                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop,
+                    const unsigned long long* stop_key, const float4* ck,
                     const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H) {
     ViewPtrs v;
     v.recs = recs;
@@ -923,6 +1026,7 @@ void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, c
     v.clean = clean;
     v.stop = stop;
     v.tile_stop = tile_stop;
+    v.stop_key = stop_key;
     v.ck = ck;
     v.ck_off = ck_off;
     v.ck_cnt = ck_cnt;

@@ -338,7 +338,8 @@ template <int FMT>
 __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     const void* planes, uint64_t n, int nwords, int sh_degree, const DevCamera* cams, int K, const gs_flip* flips,
     int B, int guard_mode, uint64_t mask, const uint32_t* box, const void* pblo, const void* pbhi, int nbox,
-    const uint2* const* clean_rects, DirtyDesc* desc, uint32_t* n_items, CmpAcc* acc) {
+    const uint2* const* clean_rects, const BlendRec* const* clean_recs, DirtyDesc* desc, uint32_t* n_items,
+    CmpAcc* acc) {
     __shared__ float sv[kPrepWarps][kMaxWords];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int b = blockIdx.x * kPrepWarps + wib;
@@ -395,6 +396,8 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     const uint32_t items = an + ao - ix * iy;
     d.new_vis = nv;
     d.old_vis = ov;
+    d.old_depth = ov ? clean_recs[k][p].depth : 0.0f;
+    d.pad[0] = d.pad[1] = d.pad[2] = 0u;
     d.n_items = items;
     d.nx0 = (uint16_t)nx0;
     d.ny0 = (uint16_t)ny0;
@@ -447,6 +450,7 @@ __global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, in
     if (tid == 0) {
         queue[0] = 0u;
         queue[1] = 0u;
+        queue[2] = 0u;
     }
 }
 
@@ -484,8 +488,9 @@ gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* r
 }
 
 gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,
-                             int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects, DirtyDesc* desc,
-                             uint32_t* item_off, CmpAcc* acc, unsigned int* queue, cudaStream_t st) {
+                             int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects,
+                             const BlendRec* const* dev_clean_recs, DirtyDesc* desc, uint32_t* item_off, CmpAcc* acc,
+                             unsigned int* queue, cudaStream_t st) {
     if (B * K > 1024 || K > 32) return set_error(GS_ERR_ARG, "B * K must be <= 1024 and K <= 32");
     // the per-(variant, view) item counts go to the tail of item_off, past the B*K+1 offsets
     uint32_t* n_items = item_off + (B * K + 1);
@@ -493,8 +498,8 @@ gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K
 #define GS_PREP(F)                                                                                            \
     k_inject_prep<F><<<blocks, kPrepWarps * 32, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, dev_cams, K, \
                                                          flips, B, guard_mode, mask, s->dev_box, s->pbox_lo,    \
-                                                         s->pbox_hi, s->nbox_words, dev_clean_rects, desc,      \
-                                                         n_items, acc)
+                                                         s->pbox_hi, s->nbox_words, dev_clean_rects,            \
+                                                         dev_clean_recs, desc, n_items, acc)
     if (s->fmt == GS_FP32)
         GS_PREP(GS_FP32);
     else if (s->fmt == GS_FP16)

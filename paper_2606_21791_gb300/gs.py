@@ -266,19 +266,22 @@ def gs_count_work(scene, enable: bool):
 
 
 def gs_read_work(scene):
-    c = np.zeros(4, dtype=np.uint64)
+    c = np.zeros(8, dtype=np.uint64)
     _check(load_library().gs_read_work(scene, _ptr(c)), "gs_read_work")
-    return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2]), "tiles_unchanged": int(c[3])}
+    return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2]), "tiles_unchanged": int(c[3]),
+            "dropped_stop_key": int(c[4]), "dropped_tile_reach": int(c[5]), "dropped_no_reach": int(c[6]),
+            "dropped_pixel_stop": int(c[7])}
 
 
 def gs_time_kernels(scene, enable: bool):
     _check(load_library().gs_time_kernels(scene, int(bool(enable))), "gs_time_kernels")
 
 
-def gs_read_kernel_ms(scene) -> float:
-    ms = C.c_float()
-    _check(load_library().gs_read_kernel_ms(scene, C.byref(ms)), "gs_read_kernel_ms")
-    return ms.value
+def gs_read_kernel_ms(scene):
+    """(plan kernel ms, blend + compare kernel ms) of the last dirty-tile batch."""
+    ms = (C.c_float * 2)()
+    _check(load_library().gs_read_kernel_ms(scene, ms), "gs_read_kernel_ms")
+    return float(ms[0]), float(ms[1])
 
 
 def gs_set_batch(scene, batch: int):

@@ -405,3 +405,36 @@ def test_graphs_on_and_off_identical(G):
         assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
     finally:
         G.gs_free_scene(h)
+
+
+def test_clean_scene_with_nonfinite_pixels(G):
+    """A clean scene whose render already holds NaN pixels (NaN colour words
+    propagate through the blend): every variant's non-finite count includes the
+    clean image's NaN pixels that the variant leaves in place.  Dirty-tile records
+    equal full re-renders bit for bit and match the oracle's counts."""
+    sc, cams, flips = S.tiny_workload()
+    planes = sc.planes.copy()
+    rng = np.random.default_rng(S.SEED_BASE + 68)
+    bad = rng.choice(sc.n, 40, replace=False)
+    planes[11, bad] = np.uint32(0x7FC00000)   # DC red coefficient := NaN
+    sc = S.Scene(planes=planes, fmt=sc.fmt, sh_degree=sc.sh_degree)
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        clean_or = O.render(sc.planes, S.FP32, 0, cams[0])
+        n_clean_bad = int((~np.isfinite(clean_or)).any(axis=2).sum())
+        assert n_clean_bad > 0
+        a = _campaign_gpu(G, h, flips, 1)
+        b = _campaign_gpu(G, h, flips, 1, full=True)
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert np.array_equal(a[f], b[f]), f
+        o, _, _ = O.campaign(sc.planes, S.FP32, 0, cams, flips, nthreads=O.max_threads())
+        assert (a["nonfinite"] > 0).all()
+        dn = np.abs(a["nonfinite"].astype(np.int64) - o["nonfinite"].astype(np.int64))
+        assert (dn <= 2).all(), dn.max()
+        npx = 256 * 256 * 3
+        gp = np.array([_psnr(x, npx) for x in a["sse"].ravel()])
+        op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
+        assert np.abs(gp - op).max() <= PSNR_TOL
+    finally:
+        G.gs_free_scene(h)
