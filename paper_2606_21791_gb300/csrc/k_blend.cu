@@ -152,12 +152,11 @@ struct CkWrite {
     uint32_t count;  // checkpoints of this tile
 };
 
-// One list entry at one pixel: the front-to-back step.  Every operation has
-// explicit rounding, so the full-frame, clean and dirty-tile kernels compute the
-// same bits wherever this is inlined.  Returns true when the pixel stops here.
-__device__ __forceinline__ bool blend_entry(const float4 q0, const float4 q1, float qb, float pxc, float pyc, Pix& p) {
-    float alpha;
-    if (!blend_alpha(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, pxc, pyc, alpha)) return false;
+// One list entry at one pixel: the front-to-back step, given the entry's alpha
+// (blend_alpha accepted it).  Every operation has explicit rounding, so the
+// full-frame, clean and dirty-tile kernels compute the same bits wherever this
+// is inlined.  Returns true when the pixel stops here.
+__device__ __forceinline__ bool blend_apply(float alpha, float r, float g, float b, Pix& p) {
     alpha = alpha > 0.99f ? 0.99f : alpha;     // keeps NaN
     const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
     if (Tn < 1e-4f) {
@@ -165,12 +164,16 @@ __device__ __forceinline__ bool blend_entry(const float4 q0, const float4 q1, fl
         return true;
     }
     const float w = __fmul_rn(alpha, p.T);
-    p.c0 = __fmaf_rn(q1.z, w, p.c0);
-    p.c1 = __fmaf_rn(q1.w, w, p.c1);
-    p.c2 = __fmaf_rn(qb, w, p.c2);
+    p.c0 = __fmaf_rn(r, w, p.c0);
+    p.c1 = __fmaf_rn(g, w, p.c1);
+    p.c2 = __fmaf_rn(b, w, p.c2);
     p.T = Tn;
     return false;
 }
+
+// Survivors a warp takes at a time: their alphas do not depend on the pixel
+// state, so they are computed as independent chains, then applied in list order.
+constexpr int kAlphaGroup = 4;
 
 // Entries [c, c + 32) of a staged batch for one warp: cull 32 boxes against the
 // warp's pixel block with one ballot, then walk the survivors in list order.  An
@@ -189,11 +192,29 @@ __device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s
     }
     unsigned m = __ballot_sync(0xffffffffu, pass);
     while (m) {
-        const int e = c + __ffs(m) - 1;
-        m &= m - 1;
-        if (p.done) continue;
-        if (COUNT) nev++;
-        if (blend_entry(q0s[e], q1s[e], qbs[e], g.pxc, g.pyc, p) && TRACK) p.stop = base + (uint32_t)e;
+        int e[kAlphaGroup];
+        bool v[kAlphaGroup], ok[kAlphaGroup];
+        float a[kAlphaGroup], cr[kAlphaGroup], cg[kAlphaGroup], cb[kAlphaGroup];
+#pragma unroll
+        for (int k = 0; k < kAlphaGroup; k++) {
+            v[k] = m != 0u;
+            e[k] = v[k] ? c + __ffs(m) - 1 : c;
+            m &= m - 1u;
+        }
+#pragma unroll
+        for (int k = 0; k < kAlphaGroup; k++) {
+            const float4 q0 = q0s[e[k]], q1 = q1s[e[k]];
+            ok[k] = v[k] && !p.done && blend_alpha(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, g.pxc, g.pyc, a[k]);
+            cr[k] = q1.z;
+            cg[k] = q1.w;
+            cb[k] = qbs[e[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < kAlphaGroup; k++) {
+            if (!v[k] || p.done) continue;
+            if (COUNT) nev++;
+            if (ok[k] && blend_apply(a[k], cr[k], cg[k], cb[k], p) && TRACK) p.stop = base + (uint32_t)e[k];
+        }
     }
 }
 
