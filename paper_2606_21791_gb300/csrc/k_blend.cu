@@ -152,27 +152,12 @@ struct CkWrite {
     uint32_t count;  // checkpoints of this tile
 };
 
-// One list entry at one pixel: the front-to-back step, given the entry's alpha
-// (blend_alpha accepted it).  Every operation has explicit rounding, so the
-// full-frame, clean and dirty-tile kernels compute the same bits wherever this
-// is inlined.  Returns true when the pixel stops here.
-__device__ __forceinline__ bool blend_apply(float alpha, float r, float g, float b, Pix& p) {
-    alpha = alpha > 0.99f ? 0.99f : alpha;     // keeps NaN
-    const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
-    if (Tn < 1e-4f) {
-        p.done = true;
-        return true;
-    }
-    const float w = __fmul_rn(alpha, p.T);
-    p.c0 = __fmaf_rn(r, w, p.c0);
-    p.c1 = __fmaf_rn(g, w, p.c1);
-    p.c2 = __fmaf_rn(b, w, p.c2);
-    p.T = Tn;
-    return false;
-}
-
 // Survivors a warp takes at a time: their alphas do not depend on the pixel
 // state, so they are computed as independent chains, then applied in list order.
+// The front-to-back step of one entry at one pixel (alpha capped at 0.99, NaN
+// kept; stop when T would drop below 1e-4; C += colour * alpha * T) has explicit
+// rounding in every operation, so the full-frame, clean and dirty-tile kernels
+// compute the same bits wherever it is inlined.
 constexpr int kAlphaGroup = 4;
 
 // Entries [c, c + 32) of a staged batch for one warp: cull 32 boxes against the
@@ -209,11 +194,23 @@ __device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s
             cg[k] = q1.w;
             cb[k] = qbs[e[k]];
         }
+        // apply in list order with selects (no divergent branch per entry)
 #pragma unroll
         for (int k = 0; k < kAlphaGroup; k++) {
-            if (!v[k] || p.done) continue;
-            if (COUNT) nev++;
-            if (ok[k] && blend_apply(a[k], cr[k], cg[k], cb[k], p) && TRACK) p.stop = base + (uint32_t)e[k];
+            const bool live = v[k] && !p.done;
+            if (COUNT) nev += live ? 1u : 0u;
+            const bool act = live && ok[k];
+            const float al = a[k] > 0.99f ? 0.99f : a[k];   // keeps NaN
+            const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, al));
+            const bool stop_here = act && Tn < 1e-4f;
+            const bool upd = act && !(Tn < 1e-4f);
+            const float w = __fmul_rn(al, p.T);
+            p.c0 = upd ? __fmaf_rn(cr[k], w, p.c0) : p.c0;
+            p.c1 = upd ? __fmaf_rn(cg[k], w, p.c1) : p.c1;
+            p.c2 = upd ? __fmaf_rn(cb[k], w, p.c2) : p.c2;
+            p.T = upd ? Tn : p.T;
+            if (TRACK) p.stop = stop_here ? base + (uint32_t)e[k] : p.stop;
+            p.done = p.done || stop_here;
         }
     }
 }
