@@ -730,7 +730,7 @@ __device__ __forceinline__ void fetch_plan_async(PlanItem* dst, const PlanItem* 
 // clean list with the old entry removed and the corrupted record merged in,
 // and compared on the fly with the clean tile.
 template <bool COUNT>
-__global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ views, int K,
+__global__ __launch_bounds__(kBT, 4) void k_dirty(const ViewPtrs* __restrict__ views, int K,
                                                  const PlanItem* __restrict__ plan,
                                                  const unsigned int* __restrict__ counts,
                                                  CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
@@ -738,9 +738,6 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
     __shared__ Stage s;
     __shared__ PlanItem pbuf[2];
     __shared__ int sh_ok;
-    __shared__ uint32_t s_wcnt[kBT / 32];
-    __shared__ uint16_t s_pix[kBT];
-    __shared__ float3 s_out[kBT];
     const uint32_t total = counts[1];
     bool have = false;   // thread 0: pbuf[cur] holds (or is receiving) an item
     int cur = 0;
@@ -771,38 +768,18 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
         const uint32_t L = (it.e - it.s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         const size_t npx = g.inside ? (size_t)g.py * v.W + g.px : 0;
         const bool active = (it.mask[threadIdx.x >> 5] >> (threadIdx.x & 31)) & 1u;   // decided by the plan
-        // compact the active pixels into the first threads (in natural order)
-        const unsigned am = __ballot_sync(0xffffffffu, active);
-        if ((threadIdx.x & 31) == 0) s_wcnt[threadIdx.x >> 5] = __popc(am);
-        __syncthreads();
-        uint32_t before = 0, n_active = 0;
-#pragma unroll
-        for (int w = 0; w < kBT / 32; w++) {
-            const uint32_t c = s_wcnt[w];
-            if (w < (int)(threadIdx.x >> 5)) before += c;
-            n_active += c;
+        // each warp keeps its 8x4 block of the tile; its cull box is the bounding box
+        // of the block's active pixels (warps without one only help staging)
+        PixGeo ga = g;
+        const bool mine = active;
+        const uint32_t u = threadIdx.x;
+        const uint32_t n_active = __syncthreads_count(active);
+        if (__any_sync(0xffffffffu, active)) {
+            ga.wx0 = (float)__reduce_min_sync(0xffffffffu, active ? g.px : 0x7fffffff) + 0.5f;
+            ga.wx1 = (float)__reduce_max_sync(0xffffffffu, active ? g.px : -1) + 0.5f;
+            ga.wy0 = (float)__reduce_min_sync(0xffffffffu, active ? g.py : 0x7fffffff) + 0.5f;
+            ga.wy1 = (float)__reduce_max_sync(0xffffffffu, active ? g.py : -1) + 0.5f;
         }
-        if (active) s_pix[before + __popc(am & ((1u << (threadIdx.x & 31)) - 1u))] = (uint16_t)threadIdx.x;
-        __syncthreads();
-        // thread t blends the t-th active pixel; its warp culls against the bounding
-        // box of the warp's active pixels
-        PixGeo ga;
-        const bool mine = threadIdx.x < n_active;
-        int ax = 0x7fffffff, ay = 0x7fffffff, bx = -1, by = -1;
-        uint32_t u = 0;
-        if (mine) {
-            u = s_pix[threadIdx.x];
-            pix_of(tx, ty, (int)u, ga.px, ga.py);
-            ax = bx = ga.px;
-            ay = by = ga.py;
-        }
-        ga.pxc = (float)ga.px + 0.5f;
-        ga.pyc = (float)ga.py + 0.5f;
-        ga.wx0 = (float)__reduce_min_sync(0xffffffffu, ax) + 0.5f;
-        ga.wx1 = (float)__reduce_max_sync(0xffffffffu, bx) + 0.5f;
-        ga.wy0 = (float)__reduce_min_sync(0xffffffffu, ay) + 0.5f;
-        ga.wy1 = (float)__reduce_max_sync(0xffffffffu, by) + 0.5f;
-        ga.inside = mine;
         Pix p{1.0f, 0.0f, 0.0f, 0.0f, !mine, 0u};
         // The merged list equals the clean list before `cut`, so an active pixel
         // (not stopped before `cut`) can resume from the clean blend's state at the
@@ -835,18 +812,10 @@ __global__ __launch_bounds__(kBT, 5) void k_dirty(const ViewPtrs* __restrict__ v
             if (__syncthreads_count(p.done) == kBT) break;
         }
         if (COUNT) add_work(work, nev, staged);
-        if (mine) s_out[u] = make_float3(__fadd_rn(p.c0, p.T), __fadd_rn(p.c1, p.T), __fadd_rn(p.c2, p.T));
-        __syncthreads();
-        // back in natural order: only the active pixels are compared; every other
-        // pixel keeps its clean value (Delta = 0), and the clean image's non-finite
-        // pixels are counted once per view at finalize
-        float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
-        if (active) {
-            const float3 o = s_out[threadIdx.x];
-            v0 = o.x;
-            v1 = o.y;
-            v2 = o.z;
-        }
+        // only the active pixels are compared; every other pixel keeps its clean
+        // value (Delta = 0), and the clean image's non-finite pixels are counted once
+        // per view at finalize
+        const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
         PixGeo gc = g;
         gc.inside = active;
         compare_tile(gc, v0, v1, v2, v.clean, v.W, &acc[bk]);
