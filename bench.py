@@ -352,6 +352,9 @@ def main():
                 "work_per_launch": {"evaluations": evals_per_launch, "flop_per_eval": FLOP_PER_EVAL,
                                     "tiles": work["tiles"] / args.steps, "entries": work["entries"] / args.steps,
                                     "tiles_dropped_by_plan": work["tiles_unchanged"] / args.steps,
+                                    "blocks_blended": work["blocks_blended"] / args.steps,
+                                    "warp_steps": work["warp_steps"] / args.steps,
+                                    "warp_steps_blending": work["warp_steps_blending"] / args.steps,
                                     "plan_drops": {k: work[k] / args.steps for k in
                                                    ("dropped_stop_key", "dropped_tile_reach", "dropped_no_reach",
                                                     "dropped_pixel_stop")}},

@@ -204,9 +204,11 @@ GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
  * entries staged, [3] dirty tiles dropped by the plan (every pixel keeps its
  * clean value), of which [4] by the stop-key test, [5] by the tile reach
  * test, [6] because no pixel is reached, [7] because every reached pixel
- * stopped before the change (graphs are bypassed while counting).
- * gs_read_work copies those 8 counts into host_counts[8] and resets them
- * (synchronises). */
+ * stopped before the change, [8] list entries walked by a warp of the
+ * dirty-tile blend (survivors of its box cull), [9] of them blended by at
+ * least one of its pixels, [10] 8x4 pixel blocks re-blended, [11] reserved
+ * (graphs are bypassed while counting).  gs_read_work copies those 12 counts
+ * into host_counts[12] and resets them (synchronises). */
 GS_API gs_status gs_count_work(gs_scene* scene, int enable);
 GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
 /* Kernel timing for measurement: while enabled, CUDA events bracket the two

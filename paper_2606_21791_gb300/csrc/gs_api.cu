@@ -26,8 +26,8 @@ gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* of
                                    cudaStream_t st);
 gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             void* plan, uint2* cand, CmpAcc* acc, unsigned int* queue, unsigned long long* work,
-                             cudaEvent_t ev_mid, cudaStream_t st);
+                             void* plan, uint2* cand, uint32_t* groups, uint32_t gcap, CmpAcc* acc,
+                             unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, cudaStream_t st);
 gs_status launch_finalize_dirty(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K,
                                 cudaStream_t st);
 size_t plan_item_size();
@@ -164,8 +164,10 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     cudaFree(s->saved);
     cudaFree(s->plan);
     cudaFree(s->cand);
+    cudaFree(s->groups);
     s->plan = nullptr;
     s->cand = nullptr;
+    s->groups = nullptr;
     int cb = std::max(B, s->cap_B);
     int cf = std::max(fpv * B, s->cap_flips);
     GS_TRY(dmalloc((void**)&s->flip_stage, sizeof(gs_flip) * cf));
@@ -173,12 +175,15 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     GS_TRY(dmalloc((void**)&s->item_off, sizeof(uint32_t) * (2 * cb * K + 1)));   // offsets + per-pair counts
     GS_TRY(dmalloc((void**)&s->acc, sizeof(CmpAcc) * cb * K));
     GS_TRY(dmalloc((void**)&s->res_stage, sizeof(gs_result) * cb * K));
-    GS_TRY(dmalloc((void**)&s->queue, sizeof(unsigned int) * 4));
+    GS_TRY(dmalloc((void**)&s->queue, sizeof(unsigned int) * 8));
     GS_TRY(dmalloc((void**)&s->saved, sizeof(uint32_t) * cf));
     // every (variant, view) can dirty at most every tile of its view
     s->plan_cap = (uint64_t)cb * K * (uint64_t)std::max(s->max_tiles, 1);
+    // groups are coded (plan slot << 3) | block in 32 bits
+    if (s->plan_cap >= (1ull << 29)) return set_error(GS_ERR_CAPACITY, "too many dirty tiles per batch for this view size");
     GS_TRY(dmalloc(&s->plan, plan_item_size() * s->plan_cap));
     GS_TRY(dmalloc((void**)&s->cand, sizeof(uint2) * s->plan_cap));
+    GS_TRY(dmalloc((void**)&s->groups, sizeof(uint32_t) * (kTilePix / 32) * s->plan_cap));
     s->cap_B = cb;
     s->cap_flips = cf;
     return GS_OK;
@@ -208,8 +213,8 @@ gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaS
                               s->desc, s->item_off, s->acc, s->queue, st));
     // external records: inside a stream capture they become event-record nodes of the graph
     if (s->ev_k0) GS_CUDA(cudaEventRecordWithFlags(s->ev_k0, st, cudaEventRecordExternal));
-    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->cand, s->acc, s->queue,
-                              s->work_ctr, s->ev_kp, st));
+    GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->cand, s->groups,
+                              (uint32_t)((kTilePix / 32) * s->plan_cap), s->acc, s->queue, s->work_ctr, s->ev_kp, st));
     if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
     GS_TRY(launch_finalize_dirty(s->acc, B * K, s->res_stage, s->clean_nonfin, K, st));
     return GS_OK;
@@ -350,6 +355,7 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->saved);
     cudaFree(s->plan);
     cudaFree(s->cand);
+    cudaFree(s->groups);
     cudaFree(s->clean_nonfin);
     cudaFree(s->work_ctr);
     if (s->ev_k0) cudaEventDestroy(s->ev_k0);
@@ -739,8 +745,8 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
 gs_status gs_count_work(gs_scene* s, int enable) {
     if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
     if (enable && !s->work_ctr) {
-        GS_TRY(dmalloc((void**)&s->work_ctr, sizeof(unsigned long long) * 8));
-        GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 8));
+        GS_TRY(dmalloc((void**)&s->work_ctr, sizeof(unsigned long long) * 16));
+        GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 16));
     }
     if (!enable && s->work_ctr) {
         cudaFree(s->work_ctr);
@@ -752,8 +758,8 @@ gs_status gs_count_work(gs_scene* s, int enable) {
 gs_status gs_read_work(gs_scene* s, uint64_t* host_counts) {
     if (!s || !host_counts) return set_error(GS_ERR_ARG, "NULL argument");
     if (!s->work_ctr) return set_error(GS_ERR_STATE, "work counting is off");
-    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost));
-    GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 8));
+    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 12, cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 16));
     return GS_OK;
 }
 

@@ -177,6 +177,7 @@ struct gs_scene {
     unsigned int* queue = nullptr;
     void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
     uint2* cand = nullptr;                  // candidate tiles of the plan's first pass [plan_cap]
+    uint32_t* groups = nullptr;             // 8x4 pixel blocks to re-blend, (item << 3) | block [8 * plan_cap]
     uint64_t plan_cap = 0;
     unsigned int* clean_nonfin = nullptr;   // [K] non-finite pixels of each clean view
     uint32_t* saved = nullptr;

@@ -160,22 +160,19 @@ struct CkWrite {
 // compute the same bits wherever it is inlined.
 constexpr int kAlphaGroup = 4;
 
-// Entries [c, c + 32) of a staged batch for one warp: cull 32 boxes against the
-// warp's pixel block with one ballot, then walk the survivors in list order.  An
-// entry culled here cannot reach alpha >= 1/255 at any of the warp's pixels, so
-// skipping it changes no pixel; a NaN box never culls.
-template <bool COUNT, bool TRACK>
-__device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s, const float4* q1s, const float* qbs,
-                                            int c, int cnt, uint32_t base, const PixGeo& g, Pix& p,
-                                            unsigned int& nev) {
-    const int lane = threadIdx.x & 31;
-    const int j = c + lane;
-    bool pass = false;
-    if (j < cnt) {
-        const float4 bx = box[j];
-        pass = !(bx.y < g.wx0 || bx.x > g.wx1 || bx.w < g.wy0 || bx.z > g.wy1);
-    }
-    unsigned m = __ballot_sync(0xffffffffu, pass);
+// A staged entry as the walk needs it.
+struct EntryQ {
+    float4 q0;          // mx, my, ca, cb
+    float cc, opac, r, g, b;
+};
+
+// Walk the survivors m (bit i: entry c + i) in list order for this lane's pixel.
+// steps (measurement builds only): [0] entries walked by the warp, [1] of them
+// blended by at least one lane.
+template <bool COUNT, bool TRACK, class Fetch>
+__device__ __forceinline__ void walk_survivors(unsigned m, int c, const Fetch& fetch, const PixGeo& g, Pix& p,
+                                               unsigned int& nev, uint32_t base, unsigned* steps = nullptr) {
+    if (COUNT && steps) steps[0] += __popc(m);
     while (m) {
         int e[kAlphaGroup];
         bool v[kAlphaGroup], ok[kAlphaGroup];
@@ -188,11 +185,11 @@ __device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s
         }
 #pragma unroll
         for (int k = 0; k < kAlphaGroup; k++) {
-            const float4 q0 = q0s[e[k]], q1 = q1s[e[k]];
-            ok[k] = v[k] && !p.done && blend_alpha(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, g.pxc, g.pyc, a[k]);
-            cr[k] = q1.z;
-            cg[k] = q1.w;
-            cb[k] = qbs[e[k]];
+            const EntryQ q = fetch(e[k]);
+            ok[k] = v[k] && !p.done && blend_alpha(q.q0.x, q.q0.y, q.q0.z, q.q0.w, q.cc, q.opac, g.pxc, g.pyc, a[k]);
+            cr[k] = q.r;
+            cg[k] = q.g;
+            cb[k] = q.b;
         }
         // apply in list order with selects (no divergent branch per entry)
 #pragma unroll
@@ -200,6 +197,7 @@ __device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s
             const bool live = v[k] && !p.done;
             if (COUNT) nev += live ? 1u : 0u;
             const bool act = live && ok[k];
+            if (COUNT && steps) steps[1] += __any_sync(0xffffffffu, act) ? 1u : 0u;
             const float al = a[k] > 0.99f ? 0.99f : a[k];   // keeps NaN
             const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, al));
             const bool stop_here = act && Tn < 1e-4f;
@@ -213,6 +211,27 @@ __device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s
             p.done = p.done || stop_here;
         }
     }
+}
+
+// Entries [c, c + 32) of a staged batch for one warp: cull 32 boxes against the
+// warp's pixel block with one ballot, then walk the survivors in list order.
+template <bool COUNT, bool TRACK>
+__device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s, const float4* q1s, const float* qbs,
+                                            int c, int cnt, uint32_t base, const PixGeo& g, Pix& p,
+                                            unsigned int& nev) {
+    const int lane = threadIdx.x & 31;
+    const int j = c + lane;
+    bool pass = false;
+    if (j < cnt) {
+        const float4 bx = box[j];
+        pass = !(bx.y < g.wx0 || bx.x > g.wx1 || bx.w < g.wy0 || bx.z > g.wy1);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    auto fetch = [&](int e) {
+        const float4 q1 = q1s[e];
+        return EntryQ{q0s[e], q1.x, q1.y, q1.z, q1.w, qbs[e]};
+    };
+    walk_survivors<COUNT, TRACK>(m, c, fetch, g, p, nev, base);
 }
 
 template <bool COUNT, bool TRACK>
@@ -477,13 +496,13 @@ static_assert(sizeof(PlanItem) == 112 && offsetof(PlanItem, mask) == 48 && offse
 // the minimum over each edge is that of a convex 1-D quadratic; it is 0 if the
 // mean lies inside (then: reachable).  NaN opacity, or terms near overflow
 // (where the blend's own power can be NaN, which it blends): reachable.
-__device__ __forceinline__ bool tile_reachable(const BlendRec& q, float x0, float x1, float y0, float y1) {
-    const float ca = q.ca, cb = q.cb, cc = q.cc;
-    const float L = __logf(255.0f * q.opac) + 1e-3f;
+__device__ __forceinline__ bool rect_reachable(float mx, float my, float ca, float cb, float cc, float opac, float x0,
+                                               float x1, float y0, float y1) {
+    const float L = __logf(255.0f * opac) + 1e-3f;
     if (L < 0.0f) return false;   // alpha <= opacity < 1/255 everywhere (with margin); NaN falls through
     if (!(ca > 0.0f) || !(cc > 0.0f) || !(L < 3.0e38f)) return true;
-    const float dx0 = q.mx - x1, dx1 = q.mx - x0;
-    const float dy0 = q.my - y1, dy1 = q.my - y0;
+    const float dx0 = mx - x1, dx1 = mx - x0;
+    const float dy0 = my - y1, dy1 = my - y0;
     if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
     const float mdx = fmaxf(dx0 * dx0, dx1 * dx1), mdy = fmaxf(dy0 * dy0, dy1 * dy1);
     const float M = 0.5f * ((ca + fabsf(cb)) * mdx + (cc + fabsf(cb)) * mdy);
@@ -497,6 +516,10 @@ __device__ __forceinline__ bool tile_reachable(const BlendRec& q, float x0, floa
     const float e3 = qf(fminf(fmaxf(-cb * dy1 * rca, dx0), dx1), dy1);
     const float qmin = fminf(fminf(e0, e1), fminf(e2, e3));
     return !(qmin > 2.0f * L + 2.0e-5f * M);
+}
+
+__device__ __forceinline__ bool tile_reachable(const BlendRec& q, float x0, float x1, float y0, float y1) {
+    return rect_reachable(q.mx, q.my, q.ca, q.cb, q.cc, q.opac, x0, x1, y0, y1);
 }
 
 __device__ __forceinline__ bool affects(const BlendRec& q, float x, float y) {
@@ -622,12 +645,15 @@ __global__ __launch_bounds__(256) void k_plan_filter(const ViewPtrs* __restrict_
 // Plan, second pass: one warp per candidate tile (grid-strided, so the
 // expensive tiles spread over all warps).  The exact per-pixel reach test, the
 // removal and insertion positions (warp searches) and the per-pixel stop test;
-// a tile with an active pixel is appended to the plan (counts[1]), any other
-// keeps its clean values (Delta = 0).
+// a tile with an active pixel is appended to the plan (counts[1]) with its
+// groups (counts[3] heavy, counts[4] light), any other keeps its clean values
+// (Delta = 0).
+constexpr int kHeavyWalk = 1024;   // list entries
 template <bool COUNT>
 __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restrict__ views,
                                                       const DirtyDesc* __restrict__ desc, int K,
                                                       const uint2* __restrict__ cand, PlanItem* __restrict__ plan,
+                                                      uint32_t* __restrict__ groups, uint32_t gcap,
                                                       unsigned int* __restrict__ counts, unsigned long long* work) {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -686,10 +712,28 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
             if (COUNT) (cut == 0xffffffffu ? drop_reach : drop_stop)++;
             continue;
         }
-        // the item's 7 16-byte parts, one per lane
-        uint32_t slot = 0;
-        if (lane == 0) slot = atomicAdd(&counts[1], 1u);
+        // the item's 7 16-byte parts, one per lane; one group per 8x4 block with an
+        // active pixel, (slot << 3) | block.  Groups of tiles with a long walk
+        // ahead (from the checkpoint the blend resumes at) go to the front of the
+        // group array and are blended first, the others to the back.
+        uint32_t word = 0;
+#pragma unroll
+        for (int q = 0; q < kBT / 32; q++) word = lane == q ? reach[q] : word;
+        const unsigned gm = __ballot_sync(0xffffffffu, lane < kBT / 32 && word != 0u);
+        const uint32_t Lm = (rg.y - rg.x) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
+        const uint32_t walk = Lm - min(cut / (uint32_t)kCkStride, v.ck_cnt[tile]) * (uint32_t)kCkStride;
+        const bool heavy = walk >= (uint32_t)kHeavyWalk;
+        uint32_t slot = 0, gbase = 0;
+        if (lane == 0) {
+            slot = atomicAdd(&counts[1], 1u);
+            gbase = atomicAdd(&counts[heavy ? 3 : 4], (unsigned)__popc(gm));
+        }
         slot = __shfl_sync(0xffffffffu, slot, 0);
+        gbase = __shfl_sync(0xffffffffu, gbase, 0);
+        if ((gm >> lane) & 1u) {
+            const uint32_t gi = gbase + __popc(gm & ((1u << lane) - 1u));
+            groups[heavy ? gi : gcap - 1u - gi] = (slot << 3) | (uint32_t)lane;
+        }
         uint4* dst = reinterpret_cast<uint4*>(&plan[slot]);
         if (lane < 3) {
             dst[lane] = reinterpret_cast<const uint4*>(&d.rec)[lane];
@@ -714,119 +758,190 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-__device__ __forceinline__ void fetch_plan_async(PlanItem* dst, const PlanItem* src) {
-#pragma unroll
-    for (int i = 0; i < (int)(sizeof(PlanItem) / 16); i++)
-        cp_async16(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i);
-    cp_async_commit();
+// Dirty-tile blend, one warp per work unit: an 8x4 pixel block of a planned
+// tile that holds an active pixel (the plan's groups, (item << 3) | block).
+// The warp streams the tile's merged list -- the clean list with the old entry
+// removed and the corrupted record inserted -- through a ring of kWarpRing
+// chunks of 32 entries in shared memory, filled by cp.async gathers issued
+// kWarpRing - 1 chunks ahead, so the gathers overlap the blend.  Each chunk is
+// culled against the box of the block's active pixels with one ballot and the
+// survivors are walked in list order (the same arithmetic as the full-frame
+// blend).  Active pixels resume from the clean blend's last checkpoint at or
+// before the first changed position; the result is compared with the clean
+// image on the fly.  Warps are independent: no block barrier.
+constexpr int kWarpRing = 4;
+constexpr int kDirtyWarps = 4;   // warps per block
+struct WarpRing {
+    float4 q[kWarpRing][3][32];   // [chunk slot][16-byte part of the record][entry]
+};
+
+// Entry m of the merged list: the inserted record (returns true) or the clean
+// list entry ci (relative to the tile's range).
+__device__ __forceinline__ bool merged_entry(uint32_t m, bool has_old, bool has_new, uint32_t pp, uint32_t ins,
+                                             uint32_t& ci) {
+    if (has_new && m == ins) return true;
+    const uint32_t j = (has_new && m > ins) ? m - 1u : m;
+    ci = (has_old && j >= pp) ? j + 1u : j;
+    return false;
 }
 
-// Dirty-tile blend: persistent; each block takes plan items from a queue.  The
-// next item is copied into the other half of a shared double buffer
-// (cp.async) while the current one is blended.  A tile is re-blended from the
-// clean list with the old entry removed and the corrupted record merged in,
-// and compared on the fly with the clean tile.
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <bool COUNT>
-__global__ __launch_bounds__(kBT, 4) void k_dirty(const ViewPtrs* __restrict__ views, int K,
-                                                 const PlanItem* __restrict__ plan,
-                                                 const unsigned int* __restrict__ counts,
-                                                 CmpAcc* __restrict__ acc, unsigned int* __restrict__ queue,
-                                                 unsigned long long* work) {
-    __shared__ Stage s;
-    __shared__ PlanItem pbuf[2];
-    __shared__ int sh_ok;
-    const uint32_t total = counts[1];
-    bool have = false;   // thread 0: pbuf[cur] holds (or is receiving) an item
-    int cur = 0;
-    if (threadIdx.x == 0) {
-        const uint32_t i0 = atomicAdd(&queue[0], 1u);
-        have = i0 < total;
-        if (have) fetch_plan_async(&pbuf[0], &plan[i0]);
-    }
+__global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* __restrict__ views, int K,
+                                                              const PlanItem* __restrict__ plan,
+                                                              const uint32_t* __restrict__ groups, uint32_t gcap,
+                                                              const unsigned int* __restrict__ counts,
+                                                              CmpAcc* __restrict__ acc,
+                                                              unsigned int* __restrict__ queue,
+                                                              unsigned long long* work) {
+    __shared__ WarpRing rings[kDirtyWarps];
+    const int lane = threadIdx.x & 31;
+    WarpRing& R = rings[threadIdx.x >> 5];
+    const uint32_t nheavy = counts[3], ngroups = counts[3] + counts[4];
     while (true) {
-        if (threadIdx.x == 0) {
-            cp_async_wait_all();
-            sh_ok = have;
-            if (have) {
-                const uint32_t i1 = atomicAdd(&queue[0], 1u);
-                have = i1 < total;
-                if (have) fetch_plan_async(&pbuf[cur ^ 1], &plan[i1]);
-            }
-        }
-        __syncthreads();
-        if (!sh_ok) break;
-        const PlanItem& it = pbuf[cur];
-        const int bk = (int)it.bk;
-        const ViewPtrs v = views[bk % K];
-        const int tx = (int)(it.tile % (uint32_t)v.tiles_x), ty = (int)(it.tile / (uint32_t)v.tiles_x);
-        const PixGeo g = pix_geo(tx, ty, v.W, v.H);   // this thread's natural pixel
-        const uint32_t s0 = it.s, pp = it.pp, ins = it.ins, cut = it.cut;
-        const bool has_old = it.flags & 1u, has_new = it.flags & 2u;
-        const uint32_t L = (it.e - it.s) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
-        const size_t npx = g.inside ? (size_t)g.py * v.W + g.px : 0;
-        const bool active = (it.mask[threadIdx.x >> 5] >> (threadIdx.x & 31)) & 1u;   // decided by the plan
-        // each warp keeps its 8x4 block of the tile; its cull box is the bounding box
-        // of the block's active pixels (warps without one only help staging)
-        PixGeo ga = g;
-        const bool mine = active;
-        const uint32_t u = threadIdx.x;
-        const uint32_t n_active = __syncthreads_count(active);
-        if (__any_sync(0xffffffffu, active)) {
-            ga.wx0 = (float)__reduce_min_sync(0xffffffffu, active ? g.px : 0x7fffffff) + 0.5f;
-            ga.wx1 = (float)__reduce_max_sync(0xffffffffu, active ? g.px : -1) + 0.5f;
-            ga.wy0 = (float)__reduce_min_sync(0xffffffffu, active ? g.py : 0x7fffffff) + 0.5f;
-            ga.wy1 = (float)__reduce_max_sync(0xffffffffu, active ? g.py : -1) + 0.5f;
-        }
-        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !mine, 0u};
+        uint32_t gi = 0;
+        if (lane == 0) gi = atomicAdd(&queue[0], 1u);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= ngroups) break;
+        // heavy groups first (front of the array), then the light ones (from the back)
+        const uint32_t code = groups[gi < nheavy ? gi : gcap - 1u - (gi - nheavy)];
+        const PlanItem* it = &plan[code >> 3];
+        const int w = (int)(code & 7u);
+        const uint4 f5 = reinterpret_cast<const uint4*>(it)[5];   // bk, tile, s, e
+        const uint4 f6 = reinterpret_cast<const uint4*>(it)[6];   // pp, ins, cut, flags
+        const uint32_t amask = it->mask[w];
+        const int bk = (int)f5.x;
+        const uint32_t tile = f5.y, s0 = f5.z, pp = f6.x, ins = f6.y, cut = f6.z;
+        const bool has_old = f6.w & 1u, has_new = f6.w & 2u;
+        const uint32_t L = (f5.w - f5.z) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
+        const ViewPtrs& v = views[bk % K];
+        const int tx = (int)(tile % (uint32_t)v.tiles_x), ty = (int)(tile / (uint32_t)v.tiles_x);
+        PixGeo g;
+        pix_of(tx, ty, w * 32 + lane, g.px, g.py);
+        g.pxc = (float)g.px + 0.5f;
+        g.pyc = (float)g.py + 0.5f;
+        const bool active = (amask >> lane) & 1u;   // decided by the plan (inside the image)
+        g.inside = active;
+        g.wx0 = (float)__reduce_min_sync(0xffffffffu, active ? g.px : 0x7fffffff) + 0.5f;
+        g.wx1 = (float)__reduce_max_sync(0xffffffffu, active ? g.px : -1) + 0.5f;
+        g.wy0 = (float)__reduce_min_sync(0xffffffffu, active ? g.py : 0x7fffffff) + 0.5f;
+        g.wy1 = (float)__reduce_max_sync(0xffffffffu, active ? g.py : -1) + 0.5f;
+        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !active, 0u};
         // The merged list equals the clean list before `cut`, so an active pixel
         // (not stopped before `cut`) can resume from the clean blend's state at the
         // last checkpoint at or before `cut`.
-        const uint32_t cstar = min(cut / (uint32_t)kCkStride, v.ck_cnt[it.tile]);
+        const uint32_t cstar = min(cut / (uint32_t)kCkStride, v.ck_cnt[tile]);
         const uint32_t start = cstar * (uint32_t)kCkStride;
-        if (mine && cstar > 0) {
-            const float4 st = v.ck[(size_t)(v.ck_off[it.tile] + cstar - 1) * kBT + u];
+        if (active && cstar > 0) {
+            const float4 st = v.ck[(size_t)(v.ck_off[tile] + cstar - 1) * kBT + (uint32_t)(w * 32 + lane)];
             p.T = st.x;
             p.c0 = st.y;
             p.c1 = st.z;
             p.c2 = st.w;
         }
-        unsigned int nev = 0, staged = 0;
-        for (uint32_t base = start; base < L && n_active > 0; base += kBT) {
-            int cnt = (int)min((uint32_t)kBT, L - base);
-            if ((int)threadIdx.x < cnt) {
-                uint32_t m = base + threadIdx.x;
-                if (has_new && m == ins) {
-                    stage_put(s, threadIdx.x, it.rec);
-                } else {
-                    uint32_t j = (has_new && m > ins) ? m - 1 : m;
-                    uint32_t ci = (has_old && j >= pp) ? j + 1 : j;
-                    stage_put(s, threadIdx.x, load_rec(v.recs, v.ids[s0 + ci]));
-                }
+        const uint32_t nch = L > start ? (L - start + 31u) / 32u : 0u;
+        // source of this lane's entry in chunk c (NULL past the end)
+        auto src_of = [&](uint32_t c) -> const BlendRec* {
+            const uint32_t m = start + c * 32u + (uint32_t)lane;
+            if (c >= nch || m >= L) return nullptr;
+            uint32_t ci = 0;
+            if (merged_entry(m, has_old, has_new, pp, ins, ci)) return &it->rec;
+            return v.recs + v.ids[s0 + ci];
+        };
+        auto issue = [&](uint32_t c, const BlendRec* src) {
+            if (src) {
+                const int slot = (int)(c % (uint32_t)kWarpRing);
+#pragma unroll
+                for (int part = 0; part < 3; part++)
+                    cp_async16(&R.q[slot][part][lane], reinterpret_cast<const float4*>(src) + part);
             }
-            __syncthreads();
-            staged += cnt;
-            blend_batch<COUNT, false>(s, cnt, base, ga, p, nev);
-            if (__syncthreads_count(p.done) == kBT) break;
+            cp_async_commit_group();
+        };
+        // the previous unit's copies may still be landing in the ring
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < kWarpRing - 1; c++) issue((uint32_t)c, src_of((uint32_t)c));
+        const BlendRec* next_src = src_of(kWarpRing - 1);
+        unsigned int nev = 0, staged = 0;
+        unsigned steps[2] = {0u, 0u};
+        for (uint32_t c = 0; c < nch; c++) {
+            __syncwarp();   // every lane is done with the slot the next issue overwrites
+            issue(c + kWarpRing - 1, next_src);
+            next_src = src_of(c + kWarpRing);
+            cp_async_wait_group<kWarpRing - 1>();   // this lane's copies of chunk c have landed
+            __syncwarp();                            // and every other lane's
+            const int slot = (int)(c % (uint32_t)kWarpRing);
+            const uint32_t base = start + c * 32u;
+            const int cnt = (int)min(32u, L - base);
+            staged += (uint32_t)cnt;
+            bool pass = false;
+            if (lane < cnt) {
+                const float4 a = R.q[slot][0][lane], b = R.q[slot][1][lane];
+                // the entry's box [mx - ex, mx + ex] x [my - ey, my + ey] against the block's,
+                // then the conservative conic test over the block's pixel centres
+                pass = !(a.x + b.z < g.wx0 || a.x - b.z > g.wx1 || a.y + b.w < g.wy0 || a.y - b.w > g.wy1) &&
+                       rect_reachable(a.x, a.y, a.z, a.w, b.x, b.y, g.wx0, g.wx1, g.wy0, g.wy1);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            auto fetch = [&](int e) {
+                const float4 q1 = R.q[slot][1][e], q2 = R.q[slot][2][e];
+                return EntryQ{R.q[slot][0][e], q1.x, q1.y, q2.x, q2.y, q2.z};
+            };
+            walk_survivors<COUNT, false>(m, 0, fetch, g, p, nev, base, steps);
+            if (__all_sync(0xffffffffu, p.done)) break;
         }
-        if (COUNT) add_work(work, nev, staged);
-        // only the active pixels are compared; every other pixel keeps its clean
-        // value (Delta = 0), and the clean image's non-finite pixels are counted once
-        // per view at finalize
+        // compare the active pixels with the clean image; every other pixel keeps
+        // its clean value (Delta = 0), and the clean image's non-finite pixels are
+        // counted once per view at finalize
         const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
-        PixGeo gc = g;
-        gc.inside = active;
-        compare_tile(gc, v0, v1, v2, v.clean, v.W, &acc[bk]);
-        // re-blended pixels whose clean value was non-finite (their clean count is withdrawn at finalize)
-        const bool clean_bad = active && !(isfinite(v.clean[npx * 3]) && isfinite(v.clean[npx * 3 + 1]) &&
-                                           isfinite(v.clean[npx * 3 + 2]));
-        const int ncb = __syncthreads_count(clean_bad);
-        if (threadIdx.x == 0 && ncb) atomicAdd(&acc[bk].clean_nonfinite_replaced, (unsigned)ncb);
-        __syncthreads();
-        cur ^= 1;
+        PixCmp r{0ull, 0.0f, false, false};
+        bool clean_bad = false;
+        if (active) {
+            const float* c = v.clean + ((size_t)g.py * v.W + g.px) * 3;
+            r = pixel_compare(v0, v1, v2, c);
+            clean_bad = !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]));
+        }
+        unsigned long long fx = r.fx;
+        float mx = r.m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        const unsigned nfoot = __popc(__ballot_sync(0xffffffffu, r.foot));
+        const unsigned nbad = __popc(__ballot_sync(0xffffffffu, r.nonfin));
+        const unsigned ncb = __popc(__ballot_sync(0xffffffffu, clean_bad));
+        if (lane == 0) {
+            CmpAcc* A = &acc[bk];
+            if (fx) atomicAdd(&A->sse_fx, fx);
+            if (mx > 0.0f) atomicMax(&A->maxabs_bits, __float_as_uint(mx));
+            if (nfoot) atomicAdd(&A->footprint, nfoot);
+            if (nbad) atomicAdd(&A->nonfinite, nbad);
+            if (ncb) atomicAdd(&A->clean_nonfinite_replaced, ncb);
+        }
+        if (COUNT) {
+            const unsigned wn = __reduce_add_sync(0xffffffffu, nev);
+            // a tile counts once, on its first group (lowest block with an active pixel)
+            const bool first = __ballot_sync(0xffffffffu, lane < w && it->mask[lane & 7] != 0u) == 0u;
+            if (lane == 0) {
+                if (wn) atomicAdd(&work[0], (unsigned long long)wn);
+                if (first) atomicAdd(&work[1], 1ull);
+                atomicAdd(&work[2], (unsigned long long)staged);
+                atomicAdd(&work[8], (unsigned long long)steps[0]);
+                atomicAdd(&work[9], (unsigned long long)steps[1]);
+                atomicAdd(&work[10], 1ull);
+            }
+        }
     }
+    cp_async_wait_all();   // leave no copy in flight
 }
 
 __global__ void k_records_to_blend(const gs_record* in, uint64_t n, BlendRec* out) {
@@ -931,7 +1046,7 @@ int dirty_grid() {
     static int blocks = 0;
     if (!blocks) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dirty<false>, kBT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dirty<false>, kDirtyWarps * 32, 0);
         if (per_sm < 1) per_sm = 1;
         blocks = per_sm * num_sms();
     }
@@ -941,27 +1056,31 @@ int dirty_grid() {
 size_t plan_item_size() { return sizeof(PlanItem); }
 
 // ev_mid (optional): recorded between the plan kernels and the blend kernel.
-// queue[0]: blend work queue, queue[1]: plan items, queue[2]: candidate tiles
-// (all zeroed by the injector); cand holds as many entries as plan.
+// queue[0]: blend work queue, queue[1]: plan items, queue[2]: candidate tiles,
+// queue[3] / queue[4]: heavy / light groups (all zeroed by the injector); cand
+// holds as many entries as plan, groups gcap = 8 per plan entry.
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
-                             void* plan, uint2* cand, CmpAcc* acc, unsigned int* queue, unsigned long long* work,
-                             cudaEvent_t ev_mid, cudaStream_t st) {
+                             void* plan, uint2* cand, uint32_t* groups, uint32_t gcap, CmpAcc* acc,
+                             unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, cudaStream_t st) {
     const ViewPtrs* views = (const ViewPtrs*)dev_views;
     PlanItem* pl = (PlanItem*)plan;
     const int plan_blocks = num_sms() * 8;
     if (work) {
         k_plan_filter<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, cand, queue, work);
-        k_plan_exact<true><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, queue, work);
+        k_plan_exact<true><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, groups, gcap, queue, work);
     } else {
         k_plan_filter<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, cand, queue, nullptr);
-        k_plan_exact<false><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, queue, nullptr);
+        k_plan_exact<false><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, groups, gcap, queue, nullptr);
     }
     if (ev_mid) {
         cudaError_t e = cudaEventRecordWithFlags(ev_mid, st, cudaEventRecordExternal);
         if (e != cudaSuccess) return set_error(GS_ERR_CUDA, cudaGetErrorString(e));
     }
-    if (work) k_dirty<true><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, work);
-    else k_dirty<false><<<dirty_grid(), kBT, 0, st>>>(views, K, pl, queue, acc, queue, nullptr);
+    if (work)
+        k_dirty<true><<<dirty_grid(), kDirtyWarps * 32, 0, st>>>(views, K, pl, groups, gcap, queue, acc, queue, work);
+    else
+        k_dirty<false><<<dirty_grid(), kDirtyWarps * 32, 0, st>>>(views, K, pl, groups, gcap, queue, acc, queue,
+                                                                 nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

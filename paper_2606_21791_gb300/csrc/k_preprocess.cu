@@ -451,6 +451,8 @@ __global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, in
         queue[0] = 0u;
         queue[1] = 0u;
         queue[2] = 0u;
+        queue[3] = 0u;
+        queue[4] = 0u;
     }
 }
 
