@@ -67,6 +67,7 @@ def lib():
             L.or_campaign.argtypes = [vp, i32, u64, i32, i32, vp, i32, i32, i32, vp, vp, i64, i32, i32,
                                       u64, vp, vp, i32, vp, vp, i32]
             L.or_sh_basis.argtypes = [C.c_float, C.c_float, C.c_float, i32, vp]
+            L.or_exp_f32.argtypes = [vp, vp, i64]
             L.or_max_threads.restype = i32
             _lib = L
     return _lib
@@ -200,6 +201,14 @@ def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: i
     if rc != 0:
         raise ValueError("campaign failed (flip site or box out of range)")
     return out.reshape(nvar, K), clamps, clean_imgs
+
+
+def exp_f32(x: np.ndarray) -> np.ndarray:
+    """The activations' fp32 exponential (Cody-Waite reduction + degree-7 Taylor)."""
+    x = _c(x, np.float32)
+    y = np.empty_like(x)
+    lib().or_exp_f32(_p(x), _p(y), x.size)
+    return y
 
 
 def sh_basis(x: float, y: float, z: float, degree: int = 3) -> np.ndarray:

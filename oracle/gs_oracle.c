@@ -284,12 +284,50 @@ void or_sh_basis(float x, float y, float z, int degree, float* Y) { sh_basis(x, 
 static int finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
 
 /* The exponential of the activations (exp of the log-scale, the logistic of the
- * opacity) is the fp32 rounding of the double-precision exponential: correctly
- * rounded except for inputs within ~2^-29 relative of a rounding midpoint.  A
- * plain expf differs between math libraries by an ulp on many inputs, and for
- * needle-like primitives the 2x2 determinant a c - b^2 cancels so strongly that
- * one ulp in a scale decides whether the primitive is culled. */
-static float exp_f32(float x) { return (float)exp((double)x); }
+ * opacity).  The paper fixes fp32 rendering but no exp; a plain expf differs
+ * between math libraries by an ulp on many inputs, and for needle-like
+ * primitives the 2x2 determinant a c - b^2 cancels so strongly that one ulp in a
+ * scale decides whether the primitive is culled.  So the exponential is defined
+ * here as one fixed fp32 evaluation: Cody and Waite's argument reduction,
+ * exp(x) = 2^k exp(r) with k the nearest integer to x / ln 2 and
+ * r = x - k ln 2 (ln 2 split into a head with 12 trailing zero bits, so k times
+ * the head is exact, and a tail), then the Taylor polynomial of exp(r) to
+ * degree 7 in Horner form with correctly rounded fused multiply-adds.  |r| is
+ * at most about 0.347, so the truncation error is below 0.1 ulp and the result
+ * is within about 1 ulp of exp(x) (pinned against the double exponential).  Any
+ * fp32 evaluation of the same steps gives the same bits. */
+static float pow2i(int e) { /* 2^e, -126 <= e <= 127 */
+    const uint32_t b = (uint32_t)(e + 127) << 23;
+    float f;
+    memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+static float exp_f32(float x) {
+    if (isnan(x)) return x;
+    if (x > 89.0f) return INFINITY;
+    if (x < -104.0f) return 0.0f; /* below half the smallest subnormal */
+    const float k = rintf(x * 1.44269502f); /* 1 / ln 2 */
+    float r = fmaf(-k, 0.693115234375f, x); /* head of ln 2 */
+    r = fmaf(-k, 3.19461833e-05f, r);       /* tail of ln 2 */
+    float p = 1.98412701e-04f;              /* 1/7! */
+    p = fmaf(p, r, 1.38888892e-03f);        /* 1/6! */
+    p = fmaf(p, r, 8.33333377e-03f);        /* 1/5! */
+    p = fmaf(p, r, 4.16666679e-02f);        /* 1/4! */
+    p = fmaf(p, r, 1.66666672e-01f);        /* 1/3! */
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    const int ki = (int)k; /* -150 ... 128 */
+    if (ki > 127) return (p * pow2i(127)) * pow2i(ki - 127);
+    if (ki < -126) return (p * pow2i(ki + 100)) * pow2i(-100); /* one rounding into the subnormals */
+    return p * pow2i(ki);
+}
+
+/* exposed for the pin test */
+void or_exp_f32(const float* x, float* y, int64_t n) {
+    for (int64_t i = 0; i < n; i++) y[i] = exp_f32(x[i]);
+}
 
 void or_preprocess_one(const void* planes, int fmt, uint64_t n, int sh_degree, uint64_t i, const or_camera* cam,
                        int tile_w, int tile_h, or_rec* out) {

@@ -646,3 +646,59 @@ def test_off_centre_covariance_uses_projection_jacobian():
         np.testing.assert_allclose(np.linalg.inv(conic), cov, rtol=1e-4, atol=1e-5)
         np.testing.assert_allclose([rec["mx"], rec["my"]], pix(pc), atol=2e-4)
         assert abs(rec["depth"] - pc[2]) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# the activations' fp32 exponential (Cody-Waite reduction + degree-7 Taylor)
+# ---------------------------------------------------------------------------
+def _exp_ulp_error(x):
+    """ulp error of the oracle's exp against the double exponential; where the
+    double result rounds past the largest float the oracle must give +inf (or
+    the largest float: one ulp)."""
+    y = O.exp_f32(x).astype(np.float64)
+    ref = np.exp(x.astype(np.float64))
+    over = ~np.isfinite(ref.astype(np.float32))
+    assert ((y[over] == np.inf) | (y[over] == np.finfo(np.float32).max)).all()
+    y, ref = y[~over], ref[~over]
+    # spacing of fp32 at the reference value (the smallest subnormal step below 2^-126)
+    sp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    sp = np.maximum(sp, 2.0 ** -149)
+    return np.abs(y - ref) / sp
+
+
+def test_exp_f32_within_one_ulp_sweep():
+    # every 97th fp32 value in [-104, 89] (positive and negative halves)
+    pos = np.arange(0, int(np.float32(89.0).view(np.uint32)), 97, dtype=np.uint32).view(np.float32)
+    neg = np.arange(0x80000000, int(np.float32(-104.0).view(np.uint32)), 97, dtype=np.uint32).view(np.float32)
+    x = np.concatenate([pos, neg])
+    err = _exp_ulp_error(x)
+    assert err.max() <= 1.0, (err.max(), x[err.argmax()])
+
+
+@pytest.mark.parametrize("lo", [0.25, 0.5, 1.0, 2.0, 32.0, 64.0])
+def test_exp_f32_within_one_ulp_exhaustive_binades(lo):
+    # every fp32 value of [lo, 2 lo) and of (-2 lo, -lo]
+    a = int(np.float32(lo).view(np.uint32))
+    b = int(np.float32(2 * lo).view(np.uint32))
+    x = np.arange(a, b, dtype=np.uint32).view(np.float32)
+    x = np.concatenate([x, -x])
+    x = x[x <= 89.0]
+    err = _exp_ulp_error(x)
+    assert err.max() <= 1.0, (err.max(), x[err.argmax()])
+
+
+def test_exp_f32_special_values():
+    x = np.array([np.nan, np.inf, -np.inf, 0.0, -0.0, 88.72283, 88.7229, 89.5, -87.3, -100.0, -103.2, -103.9,
+                  -104.1, 1e-30, -1e-30], dtype=np.float32)
+    y = O.exp_f32(x)
+    assert np.isnan(y[0])
+    assert y[1] == np.inf and y[2] == 0.0
+    assert y[3] == 1.0 and y[4] == 1.0
+    assert np.isfinite(y[5]) and y[6] == np.inf and y[7] == np.inf
+    assert 0 < y[8] < 2.0 ** -125   # near the normal/subnormal boundary
+    assert 0 < y[9] < 2.0 ** -126 and 0 < y[10] < 2.0 ** -126   # subnormal results
+    assert y[11] == np.float32(2.0 ** -149)   # 7.5e-46 rounds up to the smallest subnormal
+    assert y[12] == 0.0
+    assert y[13] == 1.0 and y[14] == 1.0
+    err = _exp_ulp_error(x[[5, 8, 9, 10, 11]])
+    assert err.max() <= 1.0
