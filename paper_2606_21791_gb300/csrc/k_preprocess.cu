@@ -50,12 +50,37 @@ __device__ __forceinline__ bool finite3(float a, float b, float c) {
     return isfinite(a) && isfinite(b) && isfinite(c);
 }
 
-// Exponential of the activations, rounded once to fp32 from the double-precision
-// exponential (correctly rounded except within ~2^-29 of a rounding midpoint), so
-// that it agrees with any other correctly rounded evaluation: for needle-like
+// Exponential of the activations, one fixed fp32 evaluation: Cody and Waite's
+// argument reduction, exp(x) = 2^k exp(r) with k the nearest integer to x / ln 2
+// and r = x - k ln 2 (ln 2 as a head with 12 trailing zero bits, so k times the
+// head is exact, plus a tail), then the degree-7 Taylor polynomial of exp(r) in
+// Horner form with correctly rounded fused multiply-adds (|r| <= ~0.347: within
+// about 1 ulp of exp).  Every fp32 evaluation of these steps gives the same
+// bits, so cull decisions agree with any other such evaluation: for needle-like
 // primitives the determinant a c - b^2 cancels so strongly that one ulp in a
-// scale decides whether the primitive is culled.
-__device__ __forceinline__ float exp_f32(float x) { return (float)exp((double)x); }
+// scale decides whether the primitive is culled.  No FP64 (slow on this part).
+__device__ __forceinline__ float pow2i(int e) { return __int_as_float((e + 127) << 23); }   // -126 <= e <= 127
+
+__device__ __forceinline__ float exp_f32(float x) {
+    if (isnan(x)) return x;
+    if (x > 89.0f) return INFINITY;
+    if (x < -104.0f) return 0.0f;   // below half the smallest subnormal
+    const float k = rintf(__fmul_rn(x, 1.44269502f));   // 1 / ln 2
+    float r = __fmaf_rn(-k, 0.693115234375f, x);         // head of ln 2
+    r = __fmaf_rn(-k, 3.19461833e-05f, r);               // tail of ln 2
+    float p = 1.98412701e-04f;                           // 1/7!
+    p = __fmaf_rn(p, r, 1.38888892e-03f);                // 1/6!
+    p = __fmaf_rn(p, r, 8.33333377e-03f);                // 1/5!
+    p = __fmaf_rn(p, r, 4.16666679e-02f);                // 1/4!
+    p = __fmaf_rn(p, r, 1.66666672e-01f);                // 1/3!
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const int ki = (int)k;   // -150 ... 128
+    if (ki > 127) return __fmul_rn(__fmul_rn(p, pow2i(127)), pow2i(ki - 127));
+    if (ki < -126) return __fmul_rn(__fmul_rn(p, pow2i(ki + 100)), pow2i(-100));   // one rounding into the subnormals
+    return __fmul_rn(p, pow2i(ki));
+}
 
 // Conservative half extents of a box that contains every pixel centre where the
 // blend can compute alpha >= 1/255 for this primitive.  The blend evaluates
@@ -80,20 +105,24 @@ __device__ __forceinline__ void cull_extent(float ca, float cb, float cc, float 
         *ey = NAN;
         return;
     }
-    const double g = 1e-6;
-    const double acb = fabs((double)cb);
-    const double qxx = (double)ca - g * (fabs((double)ca) + acb);
-    const double qyy = (double)cc - g * (fabs((double)cc) + acb);
-    const double qxy = (double)cb;
-    const double det = qxx * qyy - qxy * qxy;
-    if (!(qxx > 0.0) || !(det > 0.0)) {
+    // Q'' in fp32: the margin is doubled (2g) so that the fp32 rounding of these
+    // few operations (~1e-7 relative) stays inside it, and the determinant is
+    // lowered by a bound on its own rounding error, so the box can only grow.
+    const float acb = fabsf(cb);
+    const float qxx = ca - 2e-6f * (fabsf(ca) + acb);
+    const float qyy = cc - 2e-6f * (fabsf(cc) + acb);
+    const float pxy = qxx * qyy, pcb = cb * cb;
+    const float det = (pxy - pcb) - 4.8e-7f * (fabsf(pxy) + pcb);
+    // huge terms: the blend's own power can overflow (and be NaN, which it
+    // blends), so such a record is never culled
+    if (!(qxx > 0.0f) || !(det > 0.0f) || !(pxy < 1e37f) || !(fmaxf(fmaxf(fabsf(ca), fabsf(cc)), acb) < 1e30f)) {
         *ex = INFINITY;
         *ey = INFINITY;
         return;
     }
-    const double q = 2.0 * ((double)fmaxf(lim, 0.0f) + 1e-3);
-    *ex = (float)(sqrt(q * qyy / det) * (1.0 + 1e-6)) + 0.01f;
-    *ey = (float)(sqrt(q * qxx / det) * (1.0 + 1e-6)) + 0.01f;
+    const float q = 2.0f * (fmaxf(lim, 0.0f) + 1e-3f);
+    *ex = sqrtf(q * qyy / det) * (1.0f + 1e-5f) + 0.01f;
+    *ey = sqrtf(q * qxx / det) * (1.0f + 1e-5f) + 0.01f;
 }
 
 // Preprocess one primitive.  `src(w)` returns the float value of word w.
