@@ -257,24 +257,52 @@ __global__ void k_emit(const uint32_t* __restrict__ sorted_ids, const uint2* __r
                        const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off, uint64_t n, int tiles_x,
                        const unsigned long long* __restrict__ total, uint32_t* __restrict__ pkey,
                        uint32_t* __restrict__ pval, uint32_t* big_list, unsigned int* big_count) {
-    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n || total[1]) return;   // nothing is emitted when the pairs overflow the capacity
-    uint32_t c = cnt[j];
-    if (c == 0) return;
-    if (c > kBigPrim) {
+    // one warp per 32 consecutive primitives (depth order); their pairs are
+    // written by consecutive lanes, so the stores coalesce
+    const int lane = threadIdx.x & 31;
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (total[1]) return;   // nothing is emitted when the pairs overflow the capacity (uniform)
+    uint32_t c = j < n ? cnt[j] : 0u;
+    if (c > kBigPrim) {   // emitted by k_emit_big
         big_list[atomicAdd(big_count, 1u)] = (uint32_t)j;
-        return;
+        c = 0u;
     }
-    uint32_t p = sorted_ids[j];
-    uint2 r = rects[p];
-    uint32_t x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
-    uint32_t o = off[j];
-    for (uint32_t y = y0; y < y1; y++)
-        for (uint32_t x = x0; x < x1; x++) {
-            pkey[o] = y * (uint32_t)tiles_x + x;
-            pval[o] = p;
-            o++;
+    uint32_t p = 0, o = 0, x0 = 0, y0 = 0, w = 1;
+    if (c) {
+        p = sorted_ids[j];
+        const uint2 r = rects[p];
+        x0 = r.x & 0xffff;
+        y0 = r.x >> 16;
+        w = (r.y & 0xffff) - x0;
+        o = off[j];
+    }
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const uint32_t excl = incl - c;
+    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t b = 0; b < wtotal; b += 32) {
+        const uint32_t q = b + (uint32_t)lane;
+        // source lane: the last lane whose exclusive offset is <= q (lanes without
+        // pairs share their neighbour's offset and are skipped by taking the last)
+        int s = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int m = s + step;
+            if (__shfl_sync(0xffffffffu, excl, m) <= q) s = m;
         }
+        const uint32_t t = q - __shfl_sync(0xffffffffu, excl, s);
+        const uint32_t so = __shfl_sync(0xffffffffu, o, s), sp = __shfl_sync(0xffffffffu, p, s);
+        const uint32_t sx = __shfl_sync(0xffffffffu, x0, s), sy = __shfl_sync(0xffffffffu, y0, s);
+        const uint32_t sw = __shfl_sync(0xffffffffu, w, s);
+        if (q < wtotal) {
+            pkey[so + t] = (sy + t / sw) * (uint32_t)tiles_x + sx + t % sw;
+            pval[so + t] = sp;
+        }
+    }
 }
 
 __global__ void k_emit_big(const uint32_t* __restrict__ sorted_ids, const uint2* __restrict__ rects,
