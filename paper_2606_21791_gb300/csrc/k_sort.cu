@@ -40,9 +40,17 @@ __global__ __launch_bounds__(kRT) void k_radix_hist(const uint32_t* __restrict__
     __syncthreads();
     uint64_t count = item_count(dcount, scount);
     uint64_t base = (uint64_t)blockIdx.x * kRTile;
+    // all loads first (kRI in flight per thread), then the shared counts
+    uint32_t kk[kRI];
+#pragma unroll
     for (int r = 0; r < kRI; r++) {
-        uint64_t i = base + (uint64_t)r * kRT + threadIdx.x;
-        if (i < count) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        const uint64_t i = base + (uint64_t)r * kRT + threadIdx.x;
+        kk[r] = i < count ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRI; r++) {
+        const uint64_t i = base + (uint64_t)r * kRT + threadIdx.x;
+        if (i < count) atomicAdd(&h[(kk[r] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -53,13 +61,14 @@ __global__ __launch_bounds__(kRT) void k_radix_scatter(const uint32_t* __restric
                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                       const unsigned long long* dcount, uint64_t scount, int shift,
                                                       const uint32_t* __restrict__ hist, int nblocks) {
+    // Stable block-local ranking with warp-private digit counters: warp w owns
+    // the contiguous items [w * 32 kRI, (w + 1) * 32 kRI) of the block's tile, so
+    // ordering by (digit, warp, rank inside the warp) keeps input order.
     __shared__ uint32_t sk[kRTile];
     __shared__ uint32_t sv[VALS ? kRTile : 1];
-    __shared__ uint32_t bcnt[256];
+    __shared__ uint16_t wh[kRT / 32][256];   // per-warp digit counts, then per-warp digit offsets
     __shared__ uint32_t bexcl[256];
     __shared__ uint32_t gbase[256];
-    __shared__ uint16_t wcnt[kRT / 32][256];
-    __shared__ uint16_t pref[kRT / 32][256];
     __shared__ uint32_t wsum[kRT / 32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -68,65 +77,67 @@ __global__ __launch_bounds__(kRT) void k_radix_scatter(const uint32_t* __restric
     if (base >= count) return;
     const uint32_t nitems = (uint32_t)(count - base < (uint64_t)kRTile ? count - base : (uint64_t)kRTile);
 
-    uint32_t kr[kRI], vr[kRI];
-    bcnt[tid] = 0;
 #pragma unroll
-    for (int w = 0; w < kRT / 32; w++) wcnt[w][tid] = 0;
-    __syncthreads();
+    for (int w = 0; w < kRT / 32; w++) wh[w][tid] = 0;
+    // all loads first (kRI in flight per thread)
+    uint32_t kr[kRI], vr[kRI];
+    const uint32_t wbase = (uint32_t)warp * 32u * kRI;
 #pragma unroll
     for (int r = 0; r < kRI; r++) {
-        uint32_t i = (uint32_t)r * kRT + tid;
-        if (i < nitems) {
-            kr[r] = kin[base + i];
-            vr[r] = VALS ? vin[base + i] : 0u;
-            atomicAdd(&bcnt[(kr[r] >> shift) & 255u], 1u);
-        } else {
-            kr[r] = 0u;
-            vr[r] = 0u;
-        }
+        const uint32_t i = wbase + (uint32_t)r * 32u + (uint32_t)lane;
+        kr[r] = i < nitems ? kin[base + i] : 0u;
+        vr[r] = (VALS && i < nitems) ? vin[base + i] : 0u;
     }
     __syncthreads();
-    // block-local exclusive scan over digits
+    // rank inside the warp, round by round (the rounds are in item order)
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t lrank[kRI];
+#pragma unroll
+    for (int r = 0; r < kRI; r++) {
+        const bool valid = wbase + (uint32_t)r * 32u + (uint32_t)lane < nitems;
+        const uint32_t d = valid ? ((kr[r] >> shift) & 255u) : 256u;
+        // lanes holding the same digit (9 bits, so the invalid sentinel 256 stands apart)
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < 9; bit++) {
+            const unsigned m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? m : ~m;
+        }
+        const uint32_t before = valid ? wh[warp][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0u) wh[warp][d] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        lrank[r] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    // thread tid = digit: offsets of each warp inside the digit, digit totals,
+    // block-exclusive scan of the totals
     {
-        uint32_t c = bcnt[tid];
-        uint32_t x = c;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kRT / 32; w++) {
+            const uint32_t c = wh[w][tid];
+            wh[w][tid] = (uint16_t)tot;
+            tot += c;
+        }
+        uint32_t x = tot;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) wsum[warp] = x;
         __syncthreads();
         uint32_t add = 0;
         for (int w = 0; w < warp; w++) add += wsum[w];
-        bexcl[tid] = x - c + add;
+        bexcl[tid] = x - tot + add;
         gbase[tid] = hist[(uint64_t)tid * nblocks + blockIdx.x];
-        bcnt[tid] = 0;   // reused as the running per-digit count
     }
     __syncthreads();
-    const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < kRI; r++) {
-        uint32_t i = (uint32_t)r * kRT + tid;
-        bool valid = i < nitems;
-        uint32_t d = valid ? ((kr[r] >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) wcnt[warp][d] = (uint16_t)__popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = bcnt[tid];
-#pragma unroll
-            for (int w = 0; w < kRT / 32; w++) {
-                uint32_t c = wcnt[w][tid];
-                pref[w][tid] = (uint16_t)acc;
-                wcnt[w][tid] = 0;
-                acc += c;
-            }
-            bcnt[tid] = acc;
-        }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = bexcl[d] + pref[warp][d] + rank;
+        if (wbase + (uint32_t)r * 32u + (uint32_t)lane < nitems) {
+            const uint32_t d = (kr[r] >> shift) & 255u;
+            const uint32_t pos = bexcl[d] + wh[warp][d] + lrank[r];
             sk[pos] = kr[r];
             if (VALS) sv[pos] = vr[r];
         }
