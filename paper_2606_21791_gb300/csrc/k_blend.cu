@@ -500,7 +500,7 @@ __device__ __forceinline__ bool rect_reachable(float mx, float my, float ca, flo
                                                float x1, float y0, float y1) {
     const float L = __logf(255.0f * opac) + 1e-3f;
     if (L < 0.0f) return false;   // alpha <= opacity < 1/255 everywhere (with margin); NaN falls through
-    if (!(ca > 0.0f) || !(cc > 0.0f) || !(L < 3.0e38f)) return true;
+    if (!(ca > 1e-30f) || !(cc > 1e-30f) || !(L < 3.0e38f)) return true;
     const float dx0 = mx - x1, dx1 = mx - x0;
     const float dy0 = my - y1, dy1 = my - y0;
     if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
@@ -508,7 +508,9 @@ __device__ __forceinline__ bool rect_reachable(float mx, float my, float ca, flo
     const float M = 0.5f * ((ca + fabsf(cb)) * mdx + (cc + fabsf(cb)) * mdy);
     if (!(M < 1.0e37f)) return true;   // terms near overflow: the blend's power may be NaN
     auto qf = [&](float dx, float dy) { return ca * dx * dx + 2.0f * cb * dx * dy + cc * dy * dy; };
-    const float rca = 1.0f / ca, rcc = 1.0f / cc;
+    // approximate reciprocals: they only place the nearest point of an edge, and
+    // a relative error e there raises q by about e^2 M, far inside the margin
+    const float rca = __fdividef(1.0f, ca), rcc = __fdividef(1.0f, cc);
     // the nearest point of each edge (dx fixed: dy = -cb dx / cc; dy fixed: dx = -cb dy / ca), clamped to it
     const float e0 = qf(dx0, fminf(fmaxf(-cb * dx0 * rcc, dy0), dy1));
     const float e1 = qf(dx1, fminf(fmaxf(-cb * dx1 * rcc, dy0), dy1));
@@ -770,7 +772,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 // blend).  Active pixels resume from the clean blend's last checkpoint at or
 // before the first changed position; the result is compared with the clean
 // image on the fly.  Warps are independent: no block barrier.
-constexpr int kWarpRing = 4;
+constexpr int kWarpRing = 2;
 constexpr int kDirtyWarps = 4;   // warps per block
 struct WarpRing {
     float4 q[kWarpRing][3][32];   // [chunk slot][16-byte part of the record][entry]
