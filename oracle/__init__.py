@@ -68,6 +68,8 @@ def lib():
                                       u64, vp, vp, i32, vp, vp, i32]
             L.or_sh_basis.argtypes = [C.c_float, C.c_float, C.c_float, i32, vp]
             L.or_exp_f32.argtypes = [vp, vp, i64]
+            L.or_ecc_first_bit.argtypes = [i32]
+            L.or_ecc_corrects.argtypes = [i32, u64, vp]
             L.or_max_threads.restype = i32
             _lib = L
     return _lib
@@ -182,6 +184,8 @@ def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: i
              guard_mode: int = -1, word_mask: int = (1 << 14) - 1, box_lo=None, box_hi=None,
              clean_imgs=None, tile=(16, 16), nthreads: int = 1):
     """Per variant: copy, flip, (guard), render each view, compare with clean.
+    guard_mode: -1 off, 0 FIELD box, 1 PRIM boxes, 2 ECC emulation (upsets on
+    the sign/exponent bits of the words in word_mask are corrected).
     Returns (metrics[nvar, K], clamps[nvar], clean_imgs)."""
     p = _c(planes)
     c = _cam(cams)
@@ -201,6 +205,17 @@ def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: i
     if rc != 0:
         raise ValueError("campaign failed (flip site or box out of range)")
     return out.reshape(nvar, K), clamps, clean_imgs
+
+
+def ecc_first_bit(fmt: int) -> int:
+    """First bit the sign+exponent code protects (fp32 23, fp16 10, bf16 7)."""
+    return int(lib().or_ecc_first_bit(fmt))
+
+
+def ecc_corrects(fmt: int, word_mask: int, flips: np.ndarray) -> np.ndarray:
+    """Per flip: corrected by the sign+exponent code over the words in word_mask."""
+    f = _c(flips)
+    return np.array([bool(lib().or_ecc_corrects(fmt, word_mask, f[i:i + 1].ctypes.data)) for i in range(len(f))])
 
 
 def exp_f32(x: np.ndarray) -> np.ndarray:

@@ -685,6 +685,19 @@ int or_render(const void* planes, int fmt, uint64_t n, int sh_degree, const or_c
 /* same precision.  out: nvar*K metrics, clamps_out: nvar (may be NULL).       */
 /* Variants run in parallel over nthreads OpenMP threads (each owns a copy).  */
 /* ------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------- */
+/* ECC emulation (Sec. 5 "Alternative defenses", Table 4, "ECC sign+exp"): a  */
+/* code that protects the sign and exponent bits of the stored words corrects */
+/* any single upset there, so such an upset leaves the model unchanged;       */
+/* mantissa upsets are not covered.  Protected bits: fp32 23-31, fp16 10-15,  */
+/* bf16 7-15, of the words in word_mask.                                       */
+/* ------------------------------------------------------------------------- */
+int or_ecc_first_bit(int fmt) { return fmt == OR_FP32 ? 23 : (fmt == OR_FP16 ? 10 : 7); }
+
+int or_ecc_corrects(int fmt, uint64_t word_mask, const or_flip* f) {
+    return f->word < 64 && ((word_mask >> f->word) & 1ull) && (int)f->bit >= or_ecc_first_bit(fmt);
+}
+
 int or_campaign(const void* clean, int fmt, uint64_t n, int nwords, int sh_degree, const or_camera* cams, int K,
                 int tile_w, int tile_h, const float* clean_imgs, const or_flip* flips, int64_t nvar,
                 int flips_per_variant, int guard_mode, uint64_t word_mask, const void* box_lo, const void* box_hi,
@@ -705,12 +718,17 @@ int or_campaign(const void* clean, int fmt, uint64_t n, int nwords, int sh_degre
 #endif
         for (int64_t v = 0; v < nvar; v++) {
             memcpy(work, clean, bytes);
-            if (or_apply_flips(work, fmt, n, nwords, flips + v * flips_per_variant, flips_per_variant) != 0) {
+            const or_flip* fv = flips + v * flips_per_variant;
+            if (guard_mode == 2) { /* ECC: corrected upsets are not applied */
+                for (int f = 0; f < flips_per_variant; f++)
+                    if (!or_ecc_corrects(fmt, word_mask, &fv[f]) && or_apply_flips(work, fmt, n, nwords, &fv[f], 1) != 0)
+                        err = 1;
+            } else if (or_apply_flips(work, fmt, n, nwords, fv, flips_per_variant) != 0) {
                 err = 1;
                 continue;
             }
             uint64_t cl = 0;
-            if (guard_mode >= 0) {
+            if (guard_mode == 0 || guard_mode == 1) {
                 if (or_guard(work, fmt, n, nwords, word_mask, guard_mode, box_lo, box_hi, nbox_words, &cl) != 0) err = 1;
             }
             if (clamps_out) clamps_out[v] = cl;

@@ -702,3 +702,47 @@ def test_exp_f32_special_values():
     assert y[13] == 1.0 and y[14] == 1.0
     err = _exp_ulp_error(x[[5, 8, 9, 10, 11]])
     assert err.max() <= 1.0
+
+
+# ---------------------------------------------------------------------------
+# ECC sign+exponent emulation (Sec. 5 "Alternative defenses", Table 4)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fmtname,fmt", [("fp32", S.FP32), ("fp16", S.FP16), ("bf16", S.BF16)])
+def test_ecc_protects_exactly_the_sign_and_exponent_bits(fmtname, fmt):
+    lay = GOLD["ieee_layout"][fmtname]
+    assert O.ecc_first_bit(fmt) == lay["mantissa_p"]
+    assert lay["mantissa_p"] + lay["exp_bits"] + 1 == lay["bits"]
+    fl = np.zeros(lay["bits"] * 3, dtype=S.FLIP_DTYPE)
+    fl["bit"] = np.tile(np.arange(lay["bits"]), 3)
+    fl["word"] = np.repeat([3, 10, 20], lay["bits"])
+    got = O.ecc_corrects(fmt, (1 << 14) - 1, fl)   # words 0-13 protected, word 20 not
+    want = (fl["bit"] >= lay["mantissa_p"]) & (fl["word"] < 14)
+    assert np.array_equal(got, want)
+
+
+def test_ecc_campaign_is_plain_campaign_on_mantissa_flips_and_clean_elsewhere():
+    sc, cams, _ = S.tiny_workload()
+    fl = S.flips_stratified(14 * 32, sc.n, sc.nwords, S.FP32, S.SEED_BASE + 69)
+    mask = (1 << 14) - 1
+    e, _, clean = O.campaign(sc.planes, S.FP32, 0, cams, fl, guard_mode=2, word_mask=mask, nthreads=O.max_threads())
+    p, _, _ = O.campaign(sc.planes, S.FP32, 0, cams, fl, clean_imgs=clean, nthreads=O.max_threads())
+    corr = fl["bit"] >= 23
+    assert corr.any() and (~corr).any()
+    for f in ("sse", "maxabs", "footprint", "nonfinite"):
+        assert np.array_equal(e[~corr][f], p[~corr][f]), f
+        assert (e[corr][f] == 0).all(), f
+
+
+def test_ecc_removes_catastrophes_table4():
+    """Table 4: the sign+exponent code drives the catastrophe rate to zero, while
+    the unprotected model has catastrophic upsets on the same grid."""
+    sc, cams, _ = S.tiny_workload()
+    fl = S.flips_stratified(14 * 32 * 4, sc.n, sc.nwords, S.FP32, S.SEED_BASE + 70)
+    npx = 256 * 256
+    thr = GOLD["definition2_catastrophe_percent"]["percent"] / 100.0
+    e, _, clean = O.campaign(sc.planes, S.FP32, 0, cams, fl, guard_mode=2, word_mask=(1 << 14) - 1,
+                             nthreads=O.max_threads())
+    p, _, _ = O.campaign(sc.planes, S.FP32, 0, cams, fl, clean_imgs=clean, nthreads=O.max_threads())
+    cat = lambda r: (r["nonfinite"] > 0) | (r["footprint"] / npx > thr)
+    assert cat(p).sum() > 0
+    assert cat(e).sum() == 0
