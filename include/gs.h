@@ -50,7 +50,11 @@ typedef enum { GS_FP32 = 0, GS_FP16 = 1, GS_BF16 = 2 } gs_format;
 
 /* Guard box modes (Algorithm 1): FIELD = one [lo, hi] per word index over all
  * primitives (the Algorithm 1 precompute); PRIM = per-primitive boxes. */
-typedef enum { GS_GUARD_OFF = -1, GS_GUARD_FIELD = 0, GS_GUARD_PRIM = 1 } gs_guard_mode;
+typedef enum { GS_GUARD_OFF = -1, GS_GUARD_FIELD = 0, GS_GUARD_PRIM = 1, GS_GUARD_ECC = 2 } gs_guard_mode;
+/* GS_GUARD_ECC is not a clamp: it emulates an error-correcting code over the
+ * sign and exponent bits of the words in word_mask (Sec. 5 "Alternative
+ * defenses", Table 4): an upset on such a bit (fp32 bits 23-31, fp16 10-15,
+ * bf16 7-15) is corrected and leaves the scene unchanged; other upsets apply. */
 
 /* One single-bit upset site (Sec. 3: a fault site is (field, primitive,
  * component, bit)); `word` is the field/component word index, `bit` counts from
@@ -182,8 +186,9 @@ GS_API gs_status gs_compare_noalloc(const float* dev_a, const float* dev_b, int 
  * resident (preprocessed records, sorted tile lists, clean image); the scene
  * must be clean (no persistent upsets) while a campaign runs.
  * gs_inject_and_render evaluates B variants: variant b is the clean scene with
- * flips [b*fpv, (b+1)*fpv) XOR-ed in (fpv = flips_per_variant), then guarded
- * when guard_mode >= 0, rendered in every view and compared with the clean
+ * flips [b*fpv, (b+1)*fpv) XOR-ed in (fpv = flips_per_variant; with
+ * GS_GUARD_ECC the corrected ones are skipped), then guarded when guard_mode is
+ * FIELD or PRIM, rendered in every view and compared with the clean
  * frame; dev_out gets B*K records [b][k].  Single-flip variants run on the
  * batched dirty-tile engine (only tiles the flipped primitive covers before or
  * after the upset are re-blended; bit-identical to a full re-render);
@@ -253,12 +258,14 @@ GS_API gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uin
  * registered with their resident device bytes, which must fit the HBM budget.
  * Requests:
  *   RENDER   render `cam` of the scene into dev_rgb (H*W*3 float32, may be
- *            NULL); with guard_mode >= 0 the guard (Algorithm 1) is applied to
- *            the resident scene first and its clamp count stored in *dev_clamps.
+ *            NULL); with guard_mode FIELD or PRIM the guard (Algorithm 1) is
+ *            applied to the resident scene first and its clamp count stored in
+ *            *dev_clamps (GS_GUARD_ECC: no guard).
  *   CAMPAIGN nflips single-flip variants through gs_inject_and_render;
  *            dev_results gets nflips*K records.
  *   STORM    one frame of an upset storm: the nflips upsets are XOR-ed into the
- *            resident scene (they accumulate), then guard (if on) and render.
+ *            resident scene (they accumulate; with GS_GUARD_ECC the corrected
+ *            ones are skipped), then guard (FIELD/PRIM) and render.
  * A free slot takes the first queued request whose scene allows it (guarded
  * renders and storm frames run alone on their scene; one campaign per scene)
  * and whose render scratch fits the budget; so requests that arrive while

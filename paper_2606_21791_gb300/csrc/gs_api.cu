@@ -14,7 +14,7 @@ namespace gs {
 
 // implemented in the kernel translation units
 gs_status launch_apply_flips(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int64_t count,
-                             unsigned int* err, cudaStream_t st);
+                             unsigned int* err, uint64_t ecc_mask, cudaStream_t st);
 gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects, uint32_t* keys,
                             uint32_t* vals, gs_record* dbg, cudaStream_t st);
 gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,
@@ -196,7 +196,7 @@ int max_batch(int K) { return std::max(1, std::min(kMaxBatch, 1024 / K)); }
 gs_status check_flip_args(gs_scene* s, const gs_flip* flips, int B, int fpv, int guard_mode, uint64_t mask) {
     if (!s || (!flips && B > 0) || B < 0 || fpv < 1) return set_error(GS_ERR_ARG, "bad campaign arguments");
     if (s->K == 0 || s->views.empty()) return set_error(GS_ERR_STATE, "gs_set_views was not called");
-    if (guard_mode < -1 || guard_mode > 1) return set_error(GS_ERR_ARG, "guard_mode must be -1, 0 or 1");
+    if (guard_mode < -1 || guard_mode > 2) return set_error(GS_ERR_ARG, "guard_mode must be -1, 0, 1 or 2");
     if (guard_mode == GS_GUARD_PRIM) {
         if (!s->pbox_lo) return set_error(GS_ERR_STATE, "no per-primitive box set");
         uint64_t allowed = s->nbox_words >= 64 ? ~0ull : ((1ull << s->nbox_words) - 1ull);
@@ -407,7 +407,8 @@ gs_status gs_scene_errors(gs_scene* s, uint32_t* host_flags) {
 
 gs_status gs_apply_flips(gs_scene* s, const gs_flip* dev_flips, int64_t count, void* stream) {
     if (!s || (count > 0 && !dev_flips) || count < 0) return set_error(GS_ERR_ARG, "bad gs_apply_flips arguments");
-    return launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, dev_flips, count, s->dev_err, (cudaStream_t)stream);
+    return launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, dev_flips, count, s->dev_err, 0ull,
+                              (cudaStream_t)stream);
 }
 
 gs_status gs_field_box(gs_scene* s, uint32_t* host_lo, uint32_t* host_hi) {
@@ -609,8 +610,9 @@ gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B
         const gs_flip* f = dev_flips + (size_t)b * fpv;
         GS_TRY(launch_zero_acc(s->acc, K, st));
         GS_TRY(launch_save_sites(s->planes, s->fmt, s->n, f, fpv, s->saved, st));
-        GS_TRY(launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->dev_err, st));
-        if (guard_mode >= 0) {
+        GS_TRY(launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->dev_err,
+                                  guard_mode == GS_GUARD_ECC ? word_mask : 0ull, st));
+        if (guard_mode == GS_GUARD_FIELD || guard_mode == GS_GUARD_PRIM) {
             GS_TRY(launch_guard(s, guard_mode, word_mask, s->dev_clamps, st));
             k_move_clamps<<<1, 32, 0, st>>>(s->dev_clamps, s->acc);
             GS_CUDA(cudaGetLastError());

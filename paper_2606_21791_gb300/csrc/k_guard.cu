@@ -19,8 +19,10 @@ namespace {
 constexpr int kGuardThreads = 256;
 constexpr int kGuardUnroll = 4;
 
+// ecc_mask: words whose sign and exponent bits an error-correcting code
+// protects; an upset there is corrected (not applied).  0: no code.
 __global__ void k_apply_flips(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int64_t count,
-                              unsigned int* err) {
+                              unsigned int* err, uint64_t ecc_mask) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
     gs_flip f = flips[j];
@@ -29,6 +31,7 @@ __global__ void k_apply_flips(void* planes, int fmt, uint64_t n, int nwords, con
         if (err) atomicOr(err, 1u);
         return;
     }
+    if (((ecc_mask >> f.word) & 1ull) && f.bit >= ecc_first_bit(fmt)) return;   // corrected
     uint64_t idx = (uint64_t)f.word * n + f.prim;
     if (fmt == GS_FP32) {
         atomicXor((unsigned int*)planes + idx, 1u << f.bit);
@@ -240,10 +243,10 @@ int num_sms() {
 }
 
 gs_status launch_apply_flips(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int64_t count,
-                             unsigned int* err, cudaStream_t st) {
+                             unsigned int* err, uint64_t ecc_mask, cudaStream_t st) {
     if (count <= 0) return GS_OK;
     int64_t blocks = (count + 255) / 256;
-    k_apply_flips<<<(unsigned)blocks, 256, 0, st>>>(planes, fmt, n, nwords, flips, count, err);
+    k_apply_flips<<<(unsigned)blocks, 256, 0, st>>>(planes, fmt, n, nwords, flips, count, err, ecc_mask);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

@@ -375,14 +375,17 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     if (b >= B) return;   // whole warps only; no block-wide barrier below
     const gs_flip f = flips[b];
     const int nbits = FMT == GS_FP32 ? 32 : 16;
-    const bool ok = f.prim < n && f.word < nwords && f.bit < nbits;
+    // an upset the sign+exponent code corrects leaves the variant clean (zero record)
+    const bool corrected =
+        guard_mode == GS_GUARD_ECC && f.word < 64 && ((mask >> f.word) & 1ull) && f.bit >= ecc_first_bit(FMT);
+    const bool ok = f.prim < n && f.word < nwords && f.bit < nbits && !corrected;
     const uint32_t p = ok ? f.prim : 0u;
     unsigned int clamps = 0;
     for (int w = lane; w < nwords; w += 32) {
         uint32_t bits = load_bits<FMT>(planes, n, w, p);
         if (ok && w == f.word) bits ^= (1u << f.bit);
         float x = decode<FMT>(bits);
-        if (guard_mode >= 0 && ((mask >> w) & 1ull)) {
+        if ((guard_mode == GS_GUARD_FIELD || guard_mode == GS_GUARD_PRIM) && ((mask >> w) & 1ull)) {
             uint32_t lb, hb;
             if (guard_mode == GS_GUARD_FIELD) {
                 lb = box[w];

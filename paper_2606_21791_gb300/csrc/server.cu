@@ -29,7 +29,7 @@ namespace gs {
 gs_status render_lists_sized_ext(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, uint64_t* npairs,
                                  cudaStream_t st);
 gs_status launch_apply_flips(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int64_t count,
-                             unsigned int* err, cudaStream_t st);
+                             unsigned int* err, uint64_t ecc_mask, cudaStream_t st);
 }  // namespace gs
 
 using namespace gs;
@@ -102,7 +102,8 @@ namespace {
 
 bool scene_allows(const SceneEntry& e, const gs_request& r) {
     if (e.writer) return false;
-    bool writes = r.kind == GS_REQ_STORM || (r.kind == GS_REQ_RENDER && r.guard_mode >= 0);
+    const bool guards = r.guard_mode == GS_GUARD_FIELD || r.guard_mode == GS_GUARD_PRIM;
+    bool writes = r.kind == GS_REQ_STORM || (r.kind == GS_REQ_RENDER && guards);
     if (writes) return e.readers == 0 && !e.campaign;
     if (r.kind == GS_REQ_CAMPAIGN) return !e.campaign;
     return true;
@@ -134,8 +135,9 @@ gs_status execute(gs_server* sv, Slot& sl, Req* q) {
         return GS_OK;
     }
     if (r.kind == GS_REQ_STORM && r.nflips > 0)
-        GS_TRY(launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, r.dev_flips, r.nflips, s->dev_err, st));
-    if (r.guard_mode >= 0) {
+        GS_TRY(launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, r.dev_flips, r.nflips, s->dev_err,
+                                  r.guard_mode == GS_GUARD_ECC ? r.word_mask : 0ull, st));
+    if (r.guard_mode == GS_GUARD_FIELD || r.guard_mode == GS_GUARD_PRIM) {
         GS_CUDA(cudaMemsetAsync(sl.clamps, 0, sizeof(unsigned long long), st));
         GS_TRY(launch_guard(s, r.guard_mode, r.word_mask, sl.clamps, st));
         if (r.dev_clamps)
@@ -192,7 +194,9 @@ void worker(gs_server* sv, int slot_id) {
             }
         }
         SceneEntry& e = sv->scenes[pick->r.scene];
-        bool writes = pick->r.kind == GS_REQ_STORM || (pick->r.kind == GS_REQ_RENDER && pick->r.guard_mode >= 0);
+        bool writes = pick->r.kind == GS_REQ_STORM ||
+                      (pick->r.kind == GS_REQ_RENDER &&
+                       (pick->r.guard_mode == GS_GUARD_FIELD || pick->r.guard_mode == GS_GUARD_PRIM));
         if (writes) e.writer = true;
         else if (pick->r.kind == GS_REQ_CAMPAIGN) e.campaign = true;
         else e.readers++;

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgs.so")
 
 GS_OK, GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_BUSY, GS_ERR_STATE, GS_ERR_CAPACITY = range(8)
-GS_GUARD_OFF, GS_GUARD_FIELD, GS_GUARD_PRIM = -1, 0, 1
+GS_GUARD_OFF, GS_GUARD_FIELD, GS_GUARD_PRIM, GS_GUARD_ECC = -1, 0, 1, 2
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_ARG", 2: "GS_ERR_OOM", 3: "GS_ERR_CUDA", 4: "GS_ERR_TIMEOUT",
                 5: "GS_ERR_BUSY", 6: "GS_ERR_STATE", 7: "GS_ERR_CAPACITY"}
 

@@ -329,10 +329,10 @@ def test_campaign_tiny_matches_oracle(G):
 
 
 @pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
-@pytest.mark.parametrize("guard", [-1, 0, 1])
+@pytest.mark.parametrize("guard", [-1, 0, 1, 2])
 def test_dirty_tile_equals_full_rerender(G, fmt, guard):
     """Batched dirty-tile records are bit-identical to one-variant-at-a-time full
-    re-renders of the same variants (guard off, FIELD, PRIM)."""
+    re-renders of the same variants (guard off, FIELD, PRIM, ECC emulation)."""
     sc = S.make_scene(30000, 3, fmt, 61, layout="clusters")
     cams = S.ring_cameras(2, 320, 240)
     flips = S.flips_stratified(59 * S.FORMAT_BITS[fmt], sc.n, sc.nwords, fmt, 62)
@@ -436,5 +436,33 @@ def test_clean_scene_with_nonfinite_pixels(G):
         gp = np.array([_psnr(x, npx) for x in a["sse"].ravel()])
         op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
         assert np.abs(gp - op).max() <= PSNR_TOL
+    finally:
+        G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+def test_ecc_campaign_matches_oracle(G, fmt):
+    """ECC sign+exponent emulation (Table 4): corrected upsets give the clean
+    record exactly; the others match the oracle's campaign."""
+    sc = S.make_scene(20000, 3, fmt, 71, layout="clusters")
+    cams = S.ring_cameras(1, 240, 240)
+    nbits = S.FORMAT_BITS[fmt]
+    flips = S.flips_stratified(59 * nbits, sc.n, sc.nwords, fmt, 72)
+    mask = (1 << 59) - 1
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        g = _campaign_gpu(G, h, flips, 1, guard=2, mask=mask)
+        o, _, _ = O.campaign(sc.planes, fmt, 3, cams, flips, guard_mode=2, word_mask=mask, nthreads=O.max_threads())
+        corr = O.ecc_corrects(fmt, mask, flips)
+        assert corr.any() and (~corr).any()
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert (g[corr][f] == 0).all(), f
+        npx = 240 * 240 * 3
+        gp = np.array([_psnr(x, npx) for x in g["sse"].ravel()])
+        op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
+        assert np.abs(gp - op).max() <= PSNR_TOL
+        assert np.array_equal(g["nonfinite"] > 0, o["nonfinite"] > 0)
+        assert (g["footprint"] == o["footprint"]).mean() >= 0.99
     finally:
         G.gs_free_scene(h)
