@@ -65,7 +65,11 @@ def lib():
             L.or_compare.argtypes = [vp, vp, i32, i32, vp]
             L.or_render.argtypes = [vp, i32, u64, i32, vp, i32, i32, vp]
             L.or_campaign.argtypes = [vp, i32, u64, i32, i32, vp, i32, i32, i32, vp, vp, i64, i32, i32,
-                                      u64, vp, vp, i32, vp, vp, i32]
+                                      u64, vp, vp, i32, vp, vp, i32, vp, vp]
+            L.or_region_actual.argtypes = [vp, vp, i32, i32]
+            L.or_region_actual.restype = u64
+            L.or_region_rect.argtypes = [vp, i32, i32, i32, i32]
+            L.or_region_rect.restype = u64
             L.or_sh_basis.argtypes = [C.c_float, C.c_float, C.c_float, i32, vp]
             L.or_exp_f32.argtypes = [vp, vp, i64]
             L.or_ecc_first_bit.argtypes = [i32]
@@ -182,11 +186,13 @@ def compare(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: int = 1,
              guard_mode: int = -1, word_mask: int = (1 << 14) - 1, box_lo=None, box_hi=None,
-             clean_imgs=None, tile=(16, 16), nthreads: int = 1):
+             clean_imgs=None, tile=(16, 16), nthreads: int = 1, regions: bool = False):
     """Per variant: copy, flip, (guard), render each view, compare with clean.
     guard_mode: -1 off, 0 FIELD box, 1 PRIM boxes, 2 ECC emulation (upsets on
     the sign/exponent bits of the words in word_mask are corrected).
-    Returns (metrics[nvar, K], clamps[nvar], clean_imgs)."""
+    Returns (metrics[nvar, K], clamps[nvar], clean_imgs); with regions=True also
+    the contamination masks (actual[nvar, K], predicted[nvar, K]) over the 8x8
+    screen cells."""
     p = _c(planes)
     c = _cam(cams)
     K = len(c)
@@ -197,14 +203,32 @@ def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: i
     nvar = len(f) // flips_per_variant
     out = np.zeros(nvar * K, dtype=METRICS_DTYPE)
     clamps = np.zeros(nvar, dtype=np.uint64)
+    ra = np.zeros(nvar * K, dtype=np.uint64) if regions else None
+    rp = np.zeros(nvar * K, dtype=np.uint64) if regions else None
     lo, hi = _c(box_lo), _c(box_hi)
     nbox = 0 if lo is None else (p.shape[0] if guard_mode == 0 else lo.shape[0])
     rc = lib().or_campaign(_p(p), fmt, p.shape[1], p.shape[0], sh_degree, _p(c), K, tile[0], tile[1], _p(flat),
                            _p(f), nvar, flips_per_variant, guard_mode, word_mask, _p(lo), _p(hi), nbox,
-                           _p(out), _p(clamps), nthreads)
+                           _p(out), _p(clamps), nthreads, _p(ra), _p(rp))
     if rc != 0:
         raise ValueError("campaign failed (flip site or box out of range)")
+    if regions:
+        return out.reshape(nvar, K), clamps, clean_imgs, ra.reshape(nvar, K), rp.reshape(nvar, K)
     return out.reshape(nvar, K), clamps, clean_imgs
+
+
+def region_actual(a: np.ndarray, b: np.ndarray) -> int:
+    """8x8-cell mask of the footprint pixels of image a against image b."""
+    a = _c(a, np.float32)
+    b = _c(b, np.float32)
+    H, W = a.shape[0], a.shape[1]
+    return int(lib().or_region_actual(_p(a), _p(b), H, W))
+
+
+def region_rect(rec, width: int, height: int, tile=(16, 16)) -> int:
+    """8x8-cell mask of the pixels a preprocessed record's tile rect covers."""
+    r = np.ascontiguousarray(np.asarray(rec, dtype=REC_DTYPE).reshape(1))
+    return int(lib().or_region_rect(_p(r), width, height, tile[0], tile[1]))
 
 
 def ecc_first_bit(fmt: int) -> int:

@@ -698,10 +698,58 @@ int or_ecc_corrects(int fmt, uint64_t word_mask, const or_flip* f) {
     return f->word < 64 && ((word_mask >> f->word) & 1ull) && (int)f->bit >= or_ecc_first_bit(fmt);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Contamination of a sort-first partition (Sec. 5 "Cross-node contamination */
+/* in distributed rendering"): each node renders the primitives whose        */
+/* footprint overlaps its screen region, so an upset contaminates the regions */
+/* its primitive reaches.  Regions are unions of the cells of an 8x8 screen   */
+/* grid, cell of pixel (x, y) = (8x / W, 8y / H), bit 8 cy + cx; the 4-, 8-,  */
+/* 16-, 32- and 64-node partitions (2x2, 4x2, 4x4, 8x4, 8x8) are unions of    */
+/* cells.  Actual: cells holding a footprint pixel (Definition 1).            */
+/* Predicted: cells met by the tile rect of the changed primitive before or   */
+/* after the upset (the node that drew it and the one that draws it now).     */
+/* ------------------------------------------------------------------------- */
+static uint32_t or_load_bits(const void* planes, int fmt, uint64_t n, int w, uint64_t i) {
+    if (fmt == OR_FP32) return ((const uint32_t*)planes)[(uint64_t)w * n + i];
+    return ((const uint16_t*)planes)[(uint64_t)w * n + i];
+}
+
+static uint64_t cell_bit(int x, int y, int W, int H) {
+    const int cx = (int)(((int64_t)x * 8) / W), cy = (int)(((int64_t)y * 8) / H);
+    return 1ull << (cy * 8 + cx);
+}
+
+uint64_t or_region_actual(const float* a, const float* b, int H, int W) {
+    uint64_t m = 0;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            const int64_t p = ((int64_t)y * W + x) * 3;
+            float mx = 0.0f;
+            for (int ch = 0; ch < 3; ch++) {
+                const float d = fabsf(clamp01(a[p + ch]) - clamp01(b[p + ch]));
+                if (d > mx) mx = d;
+            }
+            if (mx > 1.0f / 255.0f) m |= cell_bit(x, y, W, H);
+        }
+    return m;
+}
+
+uint64_t or_region_rect(const or_rec* r, int W, int H, int tile_w, int tile_h) {
+    if (!r->visible || r->x1 <= r->x0 || r->y1 <= r->y0) return 0;
+    const int px0 = r->x0 * tile_w, py0 = r->y0 * tile_h;
+    const int px1 = (r->x1 * tile_w < W ? r->x1 * tile_w : W) - 1; /* inclusive */
+    const int py1 = (r->y1 * tile_h < H ? r->y1 * tile_h : H) - 1;
+    uint64_t m = 0;
+    for (int y = py0; y <= py1; y++)
+        for (int x = px0; x <= px1; x++) m |= cell_bit(x, y, W, H);
+    return m;
+}
+
 int or_campaign(const void* clean, int fmt, uint64_t n, int nwords, int sh_degree, const or_camera* cams, int K,
                 int tile_w, int tile_h, const float* clean_imgs, const or_flip* flips, int64_t nvar,
                 int flips_per_variant, int guard_mode, uint64_t word_mask, const void* box_lo, const void* box_hi,
-                int nbox_words, or_metrics* out, uint64_t* clamps_out, int nthreads) {
+                int nbox_words, or_metrics* out, uint64_t* clamps_out, int nthreads, uint64_t* reg_actual,
+                uint64_t* reg_pred) {
     size_t bytes = (size_t)n * (size_t)nwords * (size_t)or_word_bytes(fmt);
     int64_t px = 0;
     for (int k = 0; k < K; k++) px += (int64_t)cams[k].width * cams[k].height * 3;
@@ -737,6 +785,25 @@ int or_campaign(const void* clean, int fmt, uint64_t n, int nwords, int sh_degre
                 int64_t sz = (int64_t)cams[k].width * cams[k].height * 3;
                 if (or_render(work, fmt, n, sh_degree, &cams[k], tile_w, tile_h, img + off) != 0) err = 1;
                 or_compare(img + off, clean_imgs + off, cams[k].height, cams[k].width, &out[v * K + k]);
+                if (reg_actual)
+                    reg_actual[v * K + k] = or_region_actual(img + off, clean_imgs + off, cams[k].height, cams[k].width);
+                if (reg_pred) {
+                    uint64_t m = 0;
+                    for (int f = 0; f < flips_per_variant; f++) {
+                        const uint64_t p = fv[f].prim;
+                        if (p >= n) continue;
+                        int changed = 0;
+                        for (int w = 0; w < nwords; w++)
+                            if (or_load_bits(work, fmt, n, w, p) != or_load_bits(clean, fmt, n, w, p)) changed = 1;
+                        if (!changed) continue;
+                        or_rec rc, rv;
+                        or_preprocess_one(clean, fmt, n, sh_degree, p, &cams[k], tile_w, tile_h, &rc);
+                        or_preprocess_one(work, fmt, n, sh_degree, p, &cams[k], tile_w, tile_h, &rv);
+                        m |= or_region_rect(&rc, cams[k].width, cams[k].height, tile_w, tile_h);
+                        m |= or_region_rect(&rv, cams[k].width, cams[k].height, tile_w, tile_h);
+                    }
+                    reg_pred[v * K + k] = m;
+                }
                 off += sz;
             }
         }

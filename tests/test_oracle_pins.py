@@ -746,3 +746,70 @@ def test_ecc_removes_catastrophes_table4():
     cat = lambda r: (r["nonfinite"] > 0) | (r["footprint"] / npx > thr)
     assert cat(p).sum() > 0
     assert cat(e).sum() == 0
+
+
+# ---------------------------------------------------------------------------
+# contamination of a sort-first partition (Sec. 5, cross-node contamination)
+# ---------------------------------------------------------------------------
+from paper_2606_21791_gb300 import contamination as CT
+
+
+def test_region_cells_of_known_pixels():
+    W, H = 800, 1040          # cells of 100 x 130 pixels
+    base = np.full((H, W, 3), 0.5, np.float32)
+    cases = [((99, 0), 0), ((100, 0), 1), ((0, 129), 0), ((0, 130), 8), ((799, 1039), 63), ((450, 600), 4 * 8 + 4)]
+    for (x, y), cell in cases:
+        img = base.copy()
+        img[y, x, 1] = 0.9
+        assert O.region_actual(img, base) == 1 << cell, (x, y)
+    # strict 1/255 threshold (Definition 1) and a NaN pixel (clamped to 0 against 0.5)
+    img = base.copy()
+    img[0, 0, 0] = np.float32(0.5) + np.float32(1.0 / 255.0)
+    assert O.region_actual(img, base) == (1 << 0 if abs(float(img[0, 0, 0]) - 0.5) > np.float32(1 / 255) else 0)
+    img = base.copy()
+    img[1039, 0, 2] = np.nan
+    assert O.region_actual(img, base) == 1 << 56
+
+
+def test_region_rect_cells():
+    rec = np.zeros(1, dtype=O.REC_DTYPE)
+    rec["visible"] = 1
+    rec["x0"], rec["x1"], rec["y0"], rec["y1"] = 6, 8, 7, 10   # pixels 96..127 x 112..159 of 800 x 1040
+    assert O.region_rect(rec, 800, 1040) == (1 << 0) | (1 << 1) | (1 << 8) | (1 << 9)
+    rec["visible"] = 0
+    assert O.region_rect(rec, 800, 1040) == 0
+
+
+@pytest.mark.parametrize("nodes", [4, 8, 16, 32, 64])
+def test_partition_regions_equal_direct_pixel_regions(nodes):
+    rng = np.random.default_rng(S.SEED_BASE + 73)
+    W, H = 320, 240
+    rx, ry = CT.PARTITIONS[nodes]
+    for _ in range(20):
+        b = rng.random((H, W, 3), dtype=np.float32)
+        a = b.copy()
+        k = rng.integers(1, 6)
+        ys, xs = rng.integers(0, H, k), rng.integers(0, W, k)
+        a[ys, xs, 0] = np.where(b[ys, xs, 0] > 0.5, 0.0, 1.0)
+        direct = 0
+        for y, x in zip(ys, xs):
+            direct |= 1 << int((y * ry // H) * rx + (x * rx // W))
+        got = int(CT.region_masks(np.array([O.region_actual(a, b)], np.uint64), nodes)[0])
+        assert got == direct
+
+
+def test_campaign_actual_contamination_within_prediction():
+    """A pixel outside both tile rects of the flipped primitive keeps its tile
+    list, so it cannot change: actual cells are a subset of predicted cells.
+    Corrected (ECC) upsets predict no contamination."""
+    sc, cams, flips = S.tiny_workload()
+    m, _, clean, act, pred = O.campaign(sc.planes, S.FP32, 0, cams, flips, nthreads=O.max_threads(), regions=True)
+    assert ((act & ~pred) == 0).all()
+    assert ((act != 0) == (m["footprint"] > 0)).all()
+    assert (pred != 0).sum() > (act != 0).sum() > 0
+    s = CT.summary(act.ravel(), pred.ravel())
+    assert all(v["actual_outside_predicted"] == 0 for v in s.values())
+    e, _, _, act_e, pred_e = O.campaign(sc.planes, S.FP32, 0, cams, flips, guard_mode=2, word_mask=(1 << 14) - 1,
+                                        clean_imgs=clean, nthreads=O.max_threads(), regions=True)
+    corr = O.ecc_corrects(S.FP32, (1 << 14) - 1, flips)
+    assert corr.any() and (pred_e[corr] == 0).all() and (act_e[corr] == 0).all()
