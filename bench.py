@@ -335,6 +335,9 @@ def main():
     plain = {"value": nplain / plain_s, "unit": UNIT, "sample": f"{nplain} upsets, {K_views} views each",
              "mpix_s": nplain * K_views * Wd * Hd / plain_s / 1e6}
 
+    # sort-first contamination (nodes a scale-sign upset corrupts), guard off / FIELD guard
+    contam = contamination(G, S, h, scene, K_views, dev)
+
     # roofline of the dominant kernel (dirty-tile blend): FP32-pipe bound
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
@@ -374,6 +377,7 @@ def main():
         "gpu_launches": 3 * args.steps,
         "mpix_s_effective": value * K_views * Wd * Hd / 1e6,
         "plain_loop": plain,
+        "contamination": contam,
         "speedup_vs_plain_loop": value / plain["value"],
         "batch_latency_ms": {"p50": p50, "p99": p99, "what": f"one launch of {B} variants x {K_views} views"},
         "wall_s_timed_region": wall,
@@ -399,6 +403,28 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def contamination(G, S, h, scene, K_views, dev, count=256):
+    """Sort-first partition of the screen into 4-64 nodes: the fraction of nodes
+    that log-scale sign-bit upsets contaminate (actual: nodes whose pixels
+    change; predicted: nodes the primitive's footprint reaches), with the guard
+    off and with the FIELD guard, and the IoU of predicted and actual."""
+    import torch
+    from paper_2606_21791_gb300 import contamination as CT
+    rng = np.random.default_rng(S.SEED_BASE + 110)
+    fl = S.flips_at(rng.integers(0, scene.n, count).astype(np.uint32), rng.integers(3, 6, count), 31)
+    d = G.to_device(fl, dev)
+    out = G.device_bytes(count * K_views * 24, dev)
+    reg = torch.zeros(count * K_views * 2, dtype=torch.int64, device=dev)
+    res = {"upsets": f"{count} log-scale sign-bit upsets (words 3-5, bit 31), {K_views} views each",
+           "cells": "8x8 screen grid; partitions 2x2, 4x2, 4x4, 8x4, 8x8"}
+    for name, mode in (("no_guard", G.GS_GUARD_OFF), ("field_guard", G.GS_GUARD_FIELD)):
+        G.gs_inject_and_render_regions(h, d, count, mode, S.GUARD_WORDS_DEFAULT, out, reg)
+        torch.cuda.synchronize()
+        r = reg.cpu().numpy().view(np.uint64).reshape(count * K_views, 2)
+        res[name] = {str(k): v for k, v in CT.summary(r[:, 0], r[:, 1]).items()}
+    return res
 
 
 def _pct(xs, q):

@@ -202,6 +202,19 @@ GS_API gs_status gs_inject_and_render(gs_scene* scene, const gs_flip* dev_flips,
                                int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
 GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_flips, int B, int flips_per_variant,
                                     int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
+/* gs_inject_and_render for single-flip variants, also reporting how a
+ * sort-first partition is contaminated (Sec. 5 "Cross-node contamination in
+ * distributed rendering").  The screen is an 8x8 grid of cells, cell of pixel
+ * (x, y) = (8x / W, 8y / H), bit 8 cy + cx; the 4-, 8-, 16-, 32- and 64-node
+ * partitions (2x2, 4x2, 4x4, 8x4, 8x8 regions) are unions of cells.  For each
+ * (variant, view), dev_regions (device, B*K*2 uint64, caller-owned) gets
+ * [actual, predicted]: actual = cells holding a footprint pixel (Definition
+ * 1), predicted = cells met by the flipped primitive's tile rect before or
+ * after the upset when its stored words changed (0 for a corrected or
+ * clamped-back upset).  Errors as gs_inject_and_render. */
+GS_API gs_status gs_inject_and_render_regions(gs_scene* scene, const gs_flip* dev_flips, int B, int guard_mode,
+                                              uint64_t word_mask, gs_result* dev_out, uint64_t* dev_regions,
+                                              void* stream);
 /* Enable (default) or disable CUDA-graph replay of the batched dirty-tile step. */
 GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
 /* Work counters for measurement: while enabled, the dirty-tile kernels add

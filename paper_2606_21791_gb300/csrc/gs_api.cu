@@ -28,6 +28,7 @@ gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
                              void* plan, uint2* cand, uint32_t* groups, uint32_t gcap, CmpAcc* acc,
                              unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, cudaStream_t st);
+gs_status launch_regions_out(const CmpAcc* acc, int count, unsigned long long* out, cudaStream_t st);
 gs_status launch_finalize_dirty(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K,
                                 cudaStream_t st);
 size_t plan_item_size();
@@ -575,12 +576,30 @@ gs_status gs_clean_image(gs_scene* s, int k, float* dev_rgb, void* stream) {
     return GS_OK;
 }
 
+namespace {
+gs_status inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode, uint64_t word_mask,
+                            gs_result* dev_out, uint64_t* dev_regions, void* stream);
+}
+
 gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int flips_per_variant, int guard_mode,
                                uint64_t word_mask, gs_result* dev_out, void* stream) {
     GS_TRY(check_flip_args(s, dev_flips, B, flips_per_variant, guard_mode, word_mask));
     if (!dev_out && B > 0) return set_error(GS_ERR_ARG, "dev_out is NULL");
     if (flips_per_variant != 1)
         return gs_inject_and_render_full(s, dev_flips, B, flips_per_variant, guard_mode, word_mask, dev_out, stream);
+    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, nullptr, stream);
+}
+
+gs_status gs_inject_and_render_regions(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode,
+                                       uint64_t word_mask, gs_result* dev_out, uint64_t* dev_regions, void* stream) {
+    GS_TRY(check_flip_args(s, dev_flips, B, 1, guard_mode, word_mask));
+    if ((!dev_out || !dev_regions) && B > 0) return set_error(GS_ERR_ARG, "dev_out or dev_regions is NULL");
+    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, dev_regions, stream);
+}
+
+namespace {
+gs_status inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode, uint64_t word_mask,
+                            gs_result* dev_out, uint64_t* dev_regions, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
     const int max_chunk = max_batch(K);
@@ -592,9 +611,12 @@ gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int
         GS_TRY(run_dirty_batch(s, nb, guard_mode, word_mask, st));
         GS_CUDA(cudaMemcpyAsync(dev_out + (size_t)b0 * K, s->res_stage, sizeof(gs_result) * nb * K,
                                 cudaMemcpyDeviceToDevice, st));
+        if (dev_regions)
+            GS_TRY(launch_regions_out(s->acc, nb * K, (unsigned long long*)dev_regions + (size_t)2 * b0 * K, st));
     }
     return GS_OK;
 }
+}  // namespace
 
 gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B, int flips_per_variant,
                                     int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream) {

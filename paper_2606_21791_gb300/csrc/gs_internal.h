@@ -74,7 +74,28 @@ struct CmpAcc {
     unsigned int clamps;
     unsigned int clean_nonfinite_replaced;   // dirty engine: re-blended pixels whose clean value was non-finite
     unsigned int pad;
+    unsigned long long reg_actual;   // dirty engine: 8x8 screen cells holding a footprint pixel
+    unsigned long long reg_pred;     // dirty engine: cells met by the changed primitive's tile rects
 };
+
+// Screen cells of the contamination masks: an 8x8 grid, cell of pixel (x, y) =
+// (8x / W, 8y / H), bit 8 cy + cx.
+__host__ __device__ inline unsigned long long cell_bit(int x, int y, int W, int H) {
+    const int cx = (int)(((long long)x * 8) / W), cy = (int)(((long long)y * 8) / H);
+    return 1ull << (cy * 8 + cx);
+}
+// cells met by the pixels of a tile rect (packed x0 | y0 << 16, x1 | y1 << 16, half open in tiles)
+__host__ __device__ inline unsigned long long rect_cells(uint2 rect, int W, int H, int tile) {
+    const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
+    if (x1 <= x0 || y1 <= y0) return 0ull;
+    const int px1 = min(x1 * tile, W) - 1, py1 = min(y1 * tile, H) - 1;
+    const int cx0 = (int)(((long long)x0 * tile * 8) / W), cx1 = (int)(((long long)px1 * 8) / W);
+    const int cy0 = (int)(((long long)y0 * tile * 8) / H), cy1 = (int)(((long long)py1 * 8) / H);
+    unsigned long long m = 0ull;
+    for (int cy = cy0; cy <= cy1; cy++)
+        for (int cx = cx0; cx <= cx1; cx++) m |= 1ull << (cy * 8 + cx);
+    return m;
+}
 
 // Dirty-tile work descriptor of one (variant, view).
 struct DirtyDesc {

@@ -409,7 +409,7 @@ __global__ void k_finalize(const CmpAcc* acc, int count, gs_result* out, const u
 
 __global__ void k_zero_acc(CmpAcc* acc, int count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u, 0u, 0u, 0ull, 0ull};
 }
 
 // ---------------------------------------------------------------------------
@@ -921,8 +921,13 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
         const unsigned nfoot = __popc(__ballot_sync(0xffffffffu, r.foot));
         const unsigned nbad = __popc(__ballot_sync(0xffffffffu, r.nonfin));
         const unsigned ncb = __popc(__ballot_sync(0xffffffffu, clean_bad));
+        // screen cells holding a footprint pixel (contamination of a sort-first partition)
+        unsigned long long cells = r.foot ? cell_bit(g.px, g.py, v.W, v.H) : 0ull;
+        cells = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)cells) |
+                ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(cells >> 32)) << 32);
         if (lane == 0) {
             CmpAcc* A = &acc[bk];
+            if (cells) atomicOr(&A->reg_actual, cells);
             if (fx) atomicAdd(&A->sse_fx, fx);
             if (mx > 0.0f) atomicMax(&A->maxabs_bits, __float_as_uint(mx));
             if (nfoot) atomicAdd(&A->footprint, nfoot);
@@ -1032,6 +1037,19 @@ gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st) {
 gs_status launch_finalize(const CmpAcc* acc, int count, gs_result* out, cudaStream_t st) {
     if (count <= 0) return GS_OK;
     k_finalize<<<(count + 255) / 256, 256, 0, st>>>(acc, count, out, nullptr, 1);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+__global__ void k_regions_out(const CmpAcc* acc, int count, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    out[2 * i] = acc[i].reg_actual;
+    out[2 * i + 1] = acc[i].reg_pred;
+}
+
+gs_status launch_regions_out(const CmpAcc* acc, int count, unsigned long long* out, cudaStream_t st) {
+    if (count > 0) k_regions_out<<<(count + 255) / 256, 256, 0, st>>>(acc, count, out);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

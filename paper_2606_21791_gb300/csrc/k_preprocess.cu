@@ -381,8 +381,10 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     const bool ok = f.prim < n && f.word < nwords && f.bit < nbits && !corrected;
     const uint32_t p = ok ? f.prim : 0u;
     unsigned int clamps = 0;
+    bool changed = false;   // does any stored word of the primitive end up different
     for (int w = lane; w < nwords; w += 32) {
-        uint32_t bits = load_bits<FMT>(planes, n, w, p);
+        const uint32_t orig = load_bits<FMT>(planes, n, w, p);
+        uint32_t bits = orig;
         if (ok && w == f.word) bits ^= (1u << f.bit);
         float x = decode<FMT>(bits);
         if ((guard_mode == GS_GUARD_FIELD || guard_mode == GS_GUARD_PRIM) && ((mask >> w) & 1ull)) {
@@ -401,8 +403,10 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
             }
         }
         sv[wib][w] = x;
+        changed |= __float_as_uint(x) != __float_as_uint(decode<FMT>(orig));
     }
     clamps = __reduce_add_sync(0xffffffffu, clamps);
+    changed = ok && __any_sync(0xffffffffu, changed);
     __syncwarp();
     if (lane >= K) return;
     const int k = lane, bk = b * K + k;
@@ -450,6 +454,12 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     z.clamps = (k == 0) ? clamps : 0u;   // clamps reported once per variant, on view 0
     z.clean_nonfinite_replaced = 0u;
     z.pad = 0u;
+    z.reg_actual = 0ull;
+    // contamination prediction: the cells the primitive's tile rects meet, before
+    // and after the upset, when its stored words changed
+    z.reg_pred = changed ? rect_cells(orect, cams[k].W, cams[k].H, kTile) |
+                               rect_cells(make_uint2(nx0 | (ny0 << 16), nx1 | (ny1 << 16)), cams[k].W, cams[k].H, kTile)
+                         : 0ull;
     acc[bk] = z;
 }
 

@@ -59,6 +59,7 @@ SIGNATURES = {
     "gs_clean_image": (_i32, [_vp, _i32, _vp, _vp]),
     "gs_inject_and_render": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_inject_and_render_full": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
+    "gs_inject_and_render_regions": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp]),
     "gs_set_graphs": (_i32, [_vp, _i32]),
     "gs_set_batch": (_i32, [_vp, _i32]),
     "gs_count_work": (_i32, [_vp, _i32]),
@@ -248,6 +249,14 @@ def gs_inject_and_render(scene, dev_flips, B: int, flips_per_variant: int, guard
                          dev_out, stream=None):
     _check(load_library().gs_inject_and_render(scene, _ptr(dev_flips), B, flips_per_variant, guard_mode, word_mask,
                                                _ptr(dev_out), _stream(stream)), "gs_inject_and_render")
+
+
+def gs_inject_and_render_regions(scene, dev_flips, B: int, guard_mode: int, word_mask: int, dev_out,
+                                 dev_regions, stream=None):
+    """dev_regions: device buffer of B*K*2 uint64 ([actual, predicted] cell masks)."""
+    _check(load_library().gs_inject_and_render_regions(scene, _ptr(dev_flips), B, guard_mode, word_mask,
+                                                       _ptr(dev_out), _ptr(dev_regions), _stream(stream)),
+           "gs_inject_and_render_regions")
 
 
 def gs_inject_and_render_full(scene, dev_flips, B: int, flips_per_variant: int, guard_mode: int, word_mask: int,

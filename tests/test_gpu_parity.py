@@ -466,3 +466,38 @@ def test_ecc_campaign_matches_oracle(G, fmt):
         assert (g["footprint"] == o["footprint"]).mean() >= 0.99
     finally:
         G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("guard", [-1, 0, 2])
+def test_contamination_regions_match_oracle(G, guard):
+    """Sort-first contamination masks (Sec. 5): predicted cells bit for bit (they
+    come from the bit-exact tile rects), actual cells equal on >= 99% of the
+    (variant, view) pairs, records equal to the plain campaign call."""
+    torch = _torch()
+    sc = S.make_scene(30000, 3, S.FP32, 74, layout="clusters")
+    cams = S.ring_cameras(2, 320, 240)
+    flips = S.flips_stratified(59 * 32, sc.n, sc.nwords, S.FP32, 75)[::2]
+    mask = S.GUARD_WORDS_DEFAULT
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        out = G.device_bytes(len(flips) * 2 * 24)
+        reg = torch.zeros(len(flips) * 2 * 2, dtype=torch.int64, device="cuda")
+        G.gs_inject_and_render_regions(h, G.to_device(flips), len(flips), guard, mask, out, reg)
+        torch.cuda.synchronize()
+        g = G.from_device(out, G.RESULT_DTYPE).reshape(len(flips), 2)
+        r = reg.cpu().numpy().view(np.uint64).reshape(len(flips), 2, 2)
+        ref = _campaign_gpu(G, h, flips, 2, guard=guard, mask=mask)
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert np.array_equal(g[f], ref[f]), f
+        kw = {}
+        if guard == 0:
+            lo, hi = G.gs_field_box(h, 59)
+            kw = dict(box_lo=lo, box_hi=hi)
+        _, _, _, act, pred = O.campaign(sc.planes, S.FP32, 3, cams, flips, guard_mode=guard, word_mask=mask,
+                                        nthreads=O.max_threads(), regions=True, **kw)
+        assert np.array_equal(r[:, :, 1], pred)
+        assert (r[:, :, 0] == act).mean() >= 0.99
+        assert ((r[:, :, 0] & ~r[:, :, 1]) == 0).all()
+    finally:
+        G.gs_free_scene(h)
