@@ -391,6 +391,8 @@ def main():
 
     if not args.no_guard_stress:
         line["guard"] = guard_stress(args, G, S, dev, pk, pk_kind)
+    if world == 1 and not args.no_serving:
+        line["campaign_analytics"] = campaign_analytics(G, S, dev)
     if not args.no_serving:
         line["serving"] = serving(args, G, S, dev)
         st = line["serving"]["storm"]
@@ -424,6 +426,60 @@ def contamination(G, S, h, scene, K_views, dev, count=256):
         torch.cuda.synchronize()
         r = reg.cpu().numpy().view(np.uint64).reshape(count * K_views, 2)
         res[name] = {str(k): v for k, v in CT.summary(r[:, 0], r[:, 1]).items()}
+    return res
+
+
+def campaign_analytics(G, S, dev):
+    """Table 2 on the 134,826-Gaussian stratified campaign (50,000 upsets, fp32,
+    800x800), with the campaign's own injection rate, and the scaling law of the
+    median / mean single-upset error (MSE) over model sizes 5k-300k (20,000
+    stratified upsets each), guard off and FIELD guard."""
+    import torch
+    from paper_2606_21791_gb300 import analytics as AN
+    res = {}
+    sc, cams, fl = S.batching_workload(S.FP32)
+    h = G.gs_load_scene(sc.planes, sc.n, 3, S.FP32)
+    G.gs_set_views(h, cams)
+    d = G.to_device(fl, dev)
+    out = G.device_bytes(len(fl) * 24, dev)
+    G.gs_inject_and_render(h, d[:8 * 512], 512, 1, G.GS_GUARD_OFF, S.GUARD_WORDS_DEFAULT, out)   # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.gs_inject_and_render(h, d, len(fl), 1, G.GS_GUARD_OFF, S.GUARD_WORDS_DEFAULT, out)
+    e1.record()
+    torch.cuda.synchronize()
+    rec = G.from_device(out, G.RESULT_DTYPE).reshape(len(fl), 1)
+    G.gs_free_scene(h)
+    res["table2"] = {"workload": "134,826 Gaussians (4 clusters, SH 3, fp32), 800x800, 50,000 stratified upsets",
+                     "injections_per_s": len(fl) / (e0.elapsed_time(e1) / 1000.0),
+                     "fields": AN.severity_table(fl, rec, 800 * 800)}
+    sizes = [5_000, 20_000, 80_000, 300_000]
+    med = {"no_guard": [], "field_guard": []}
+    mean = {"no_guard": [], "field_guard": []}
+    for n in sizes:
+        sc = S.make_scene(n, 3, S.FP32, S.SEED_BASE + 120 + n % 97, layout="clusters")
+        cams = S.ring_cameras(1, 800, 800)
+        fl = S.flips_stratified(20_000, sc.n, sc.nwords, S.FP32, S.SEED_BASE + 121)
+        h = G.gs_load_scene(sc.planes, sc.n, 3, S.FP32)
+        G.gs_set_views(h, cams)
+        d = G.to_device(fl, dev)
+        out = G.device_bytes(len(fl) * 24, dev)
+        for name, mode in (("no_guard", G.GS_GUARD_OFF), ("field_guard", G.GS_GUARD_FIELD)):
+            G.gs_inject_and_render(h, d, len(fl), 1, mode, S.GUARD_WORDS_DEFAULT, out)
+            torch.cuda.synchronize()
+            mse = G.from_device(out, G.RESULT_DTYPE)["sse"] / (800 * 800 * 3)
+            med[name].append(float(np.median(mse)))
+            mean[name].append(float(mse.mean()))
+        G.gs_free_scene(h)
+    fits = {}
+    for name in med:
+        a, _, r2 = AN.loglog_fit(sizes, med[name])
+        am, _, r2m = AN.loglog_fit(sizes, mean[name])
+        fits[name] = {"median_mse": med[name], "mean_mse": mean[name], "alpha_median": a, "r2_median": r2,
+                      "alpha_mean": am, "r2_mean": r2m}
+    res["scaling"] = {"sizes": sizes, "upsets_per_size": 20_000, "error": "per-variant MSE (800x800x3)", **fits,
+                      "guard_mean_error_factor_at_largest": mean["no_guard"][-1] / max(mean["field_guard"][-1], 1e-30)}
     return res
 
 

@@ -813,3 +813,46 @@ def test_campaign_actual_contamination_within_prediction():
                                         clean_imgs=clean, nthreads=O.max_threads(), regions=True)
     corr = O.ecc_corrects(S.FP32, (1 << 14) - 1, flips)
     assert corr.any() and (pred_e[corr] == 0).all() and (act_e[corr] == 0).all()
+
+
+# ---------------------------------------------------------------------------
+# campaign analytics (Table 2 Wilson intervals, Sec. 5 scaling-law fit)
+# ---------------------------------------------------------------------------
+from paper_2606_21791_gb300 import analytics as AN
+
+
+@pytest.mark.parametrize("k,n", [(0, 10), (1, 10), (5, 10), (10, 10), (7, 2512), (2782, 100000), (1, 1)])
+def test_wilson_interval_matches_scipy(k, n):
+    st = pytest.importorskip("scipy.stats")
+    ci = st.binomtest(k, n).proportion_ci(confidence_level=0.95, method="wilson")
+    lo, hi = AN.wilson(k, n)
+    assert abs(lo - ci.low) < 1e-12 and abs(hi - ci.high) < 1e-12
+
+
+def test_wilson_closed_forms():
+    n, z = 400, AN.Z95
+    lo, hi = AN.wilson(0, n)
+    assert lo == 0.0 and abs(hi - z * z / (n + z * z)) < 1e-15
+    lo, hi = AN.wilson(n // 2, n)
+    assert abs((lo + hi) / 2 - 0.5) < 1e-15
+
+
+def test_loglog_fit_recovers_power_law():
+    N = np.array([5e3, 2e4, 8e4, 3e5])
+    a, c, r2 = AN.loglog_fit(N, 7.5 * N ** -0.83)
+    assert abs(a + 0.83) < 1e-12 and abs(c - math.log(7.5)) < 1e-10 and abs(r2 - 1.0) < 1e-12
+
+
+def test_severity_table_pooling_and_definition2():
+    # 3 variants per field word group, 2 views, 1000-pixel frames
+    words = np.array([0, 3, 3, 6, 10, 11, 20, 20])
+    fl = S.flips_at(np.zeros(len(words), np.uint32), words, 0)
+    rec = np.zeros((len(words), 2), dtype=[("footprint", "<u4"), ("nonfinite", "<u4")])
+    rec["footprint"][1] = (30, 10)      # log-scale: 2.0% averaged -> catastrophic
+    rec["footprint"][2] = (10, 10)      # log-scale: 1.0%, not above 1% -> not catastrophic
+    rec["nonfinite"][5] = (0, 1)        # DC: non-finite in one view -> catastrophic
+    t = AN.severity_table(fl, rec, 1000)
+    assert t["log-scale"]["n"] == 2 and t["log-scale"]["catastrophe_pct"] == 50.0
+    assert t["log-scale"]["max"] == 2.0 and t["log-scale"]["mean"] == 1.5
+    assert t["color (DC)"]["catastrophe_pct"] == 100.0 and t["color (SH)"]["n"] == 2
+    assert t["mean"]["catastrophe_pct"] == 0.0
