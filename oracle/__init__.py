@@ -65,7 +65,9 @@ def lib():
             L.or_compare.argtypes = [vp, vp, i32, i32, vp]
             L.or_render.argtypes = [vp, i32, u64, i32, vp, i32, i32, vp]
             L.or_campaign.argtypes = [vp, i32, u64, i32, i32, vp, i32, i32, i32, vp, vp, i64, i32, i32,
-                                      u64, vp, vp, i32, vp, vp, i32, vp, vp]
+                                      u64, vp, vp, i32, vp, vp, i32, vp, vp, vp]
+            L.or_ssim.argtypes = [vp, vp, i32, i32]
+            L.or_ssim.restype = C.c_double
             L.or_region_actual.argtypes = [vp, vp, i32, i32]
             L.or_region_actual.restype = u64
             L.or_region_rect.argtypes = [vp, i32, i32, i32, i32]
@@ -186,13 +188,14 @@ def compare(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: int = 1,
              guard_mode: int = -1, word_mask: int = (1 << 14) - 1, box_lo=None, box_hi=None,
-             clean_imgs=None, tile=(16, 16), nthreads: int = 1, regions: bool = False):
+             clean_imgs=None, tile=(16, 16), nthreads: int = 1, regions: bool = False, ssim: bool = False):
     """Per variant: copy, flip, (guard), render each view, compare with clean.
     guard_mode: -1 off, 0 FIELD box, 1 PRIM boxes, 2 ECC emulation (upsets on
     the sign/exponent bits of the words in word_mask are corrected).
     Returns (metrics[nvar, K], clamps[nvar], clean_imgs); with regions=True also
     the contamination masks (actual[nvar, K], predicted[nvar, K]) over the 8x8
-    screen cells."""
+    screen cells; with ssim=True the SSIM of every (variant, view) is appended
+    last (ssim[nvar, K])."""
     p = _c(planes)
     c = _cam(cams)
     K = len(c)
@@ -205,16 +208,27 @@ def campaign(planes, fmt: int, sh_degree: int, cams, flips, flips_per_variant: i
     clamps = np.zeros(nvar, dtype=np.uint64)
     ra = np.zeros(nvar * K, dtype=np.uint64) if regions else None
     rp = np.zeros(nvar * K, dtype=np.uint64) if regions else None
+    ss = np.zeros(nvar * K, dtype=np.float64) if ssim else None
     lo, hi = _c(box_lo), _c(box_hi)
     nbox = 0 if lo is None else (p.shape[0] if guard_mode == 0 else lo.shape[0])
     rc = lib().or_campaign(_p(p), fmt, p.shape[1], p.shape[0], sh_degree, _p(c), K, tile[0], tile[1], _p(flat),
                            _p(f), nvar, flips_per_variant, guard_mode, word_mask, _p(lo), _p(hi), nbox,
-                           _p(out), _p(clamps), nthreads, _p(ra), _p(rp))
+                           _p(out), _p(clamps), nthreads, _p(ra), _p(rp), _p(ss))
     if rc != 0:
         raise ValueError("campaign failed (flip site or box out of range)")
+    res = (out.reshape(nvar, K), clamps, clean_imgs)
     if regions:
-        return out.reshape(nvar, K), clamps, clean_imgs, ra.reshape(nvar, K), rp.reshape(nvar, K)
-    return out.reshape(nvar, K), clamps, clean_imgs
+        res += (ra.reshape(nvar, K), rp.reshape(nvar, K))
+    if ssim:
+        res += (ss.reshape(nvar, K),)
+    return res
+
+
+def ssim(a: np.ndarray, b: np.ndarray) -> float:
+    """SSIM of image a against image b (H x W x 3 float32)."""
+    a = _c(a, np.float32)
+    b = _c(b, np.float32)
+    return float(lib().or_ssim(_p(a), _p(b), a.shape[0], a.shape[1]))
 
 
 def region_actual(a: np.ndarray, b: np.ndarray) -> int:

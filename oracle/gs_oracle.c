@@ -699,6 +699,44 @@ int or_ecc_corrects(int fmt, uint64_t word_mask, const or_flip* f) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* SSIM (Sec. 3 "Metrics and severity", Wang et al. 2004): per channel, local */
+/* Gaussian-weighted means, variances and covariance over an 11x11 window     */
+/* (sigma 1.5, weights normalised to sum 1), SSIM = (2 mx my + C1)(2 sxy + C2) */
+/* / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)), C1 = 0.01^2, C2 = 0.03^2 (data    */
+/* range 1), on images clamped to [0, 1] (NaN as 0, like the other metrics);   */
+/* the mean over the windows that lie inside the frame and over the channels. */
+/* Direct 2-D window sums in double.                                           */
+/* ------------------------------------------------------------------------- */
+double or_ssim(const float* a, const float* b, int H, int W) {
+    const int R = 5;
+    double w1[11], ws = 0.0;
+    for (int i = -R; i <= R; i++) ws += (w1[i + R] = exp(-(double)(i * i) / (2.0 * 1.5 * 1.5)));
+    for (int i = 0; i < 11; i++) w1[i] /= ws;
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    if (H <= 2 * R || W <= 2 * R) return 1.0;
+    double total = 0.0;
+    for (int y = R; y < H - R; y++)
+        for (int x = R; x < W - R; x++)
+            for (int c = 0; c < 3; c++) {
+                double mx = 0, my = 0, sxx = 0, syy = 0, sxy = 0;
+                for (int dy = -R; dy <= R; dy++)
+                    for (int dx = -R; dx <= R; dx++) {
+                        const int64_t q = ((int64_t)(y + dy) * W + (x + dx)) * 3 + c;
+                        const double w = w1[dy + R] * w1[dx + R];
+                        const double u = clamp01(a[q]), v = clamp01(b[q]);
+                        mx += w * u;
+                        my += w * v;
+                        sxx += w * u * u;
+                        syy += w * v * v;
+                        sxy += w * u * v;
+                    }
+                const double vx = sxx - mx * mx, vy = syy - my * my, cxy = sxy - mx * my;
+                total += ((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2));
+            }
+    return total / (3.0 * (double)(H - 2 * R) * (double)(W - 2 * R));
+}
+
+/* ------------------------------------------------------------------------- */
 /* Contamination of a sort-first partition (Sec. 5 "Cross-node contamination */
 /* in distributed rendering"): each node renders the primitives whose        */
 /* footprint overlaps its screen region, so an upset contaminates the regions */
@@ -749,7 +787,7 @@ int or_campaign(const void* clean, int fmt, uint64_t n, int nwords, int sh_degre
                 int tile_w, int tile_h, const float* clean_imgs, const or_flip* flips, int64_t nvar,
                 int flips_per_variant, int guard_mode, uint64_t word_mask, const void* box_lo, const void* box_hi,
                 int nbox_words, or_metrics* out, uint64_t* clamps_out, int nthreads, uint64_t* reg_actual,
-                uint64_t* reg_pred) {
+                uint64_t* reg_pred, double* ssim_out) {
     size_t bytes = (size_t)n * (size_t)nwords * (size_t)or_word_bytes(fmt);
     int64_t px = 0;
     for (int k = 0; k < K; k++) px += (int64_t)cams[k].width * cams[k].height * 3;
@@ -787,6 +825,7 @@ int or_campaign(const void* clean, int fmt, uint64_t n, int nwords, int sh_degre
                 or_compare(img + off, clean_imgs + off, cams[k].height, cams[k].width, &out[v * K + k]);
                 if (reg_actual)
                     reg_actual[v * K + k] = or_region_actual(img + off, clean_imgs + off, cams[k].height, cams[k].width);
+                if (ssim_out) ssim_out[v * K + k] = or_ssim(img + off, clean_imgs + off, cams[k].height, cams[k].width);
                 if (reg_pred) {
                     uint64_t m = 0;
                     for (int f = 0; f < flips_per_variant; f++) {

@@ -856,3 +856,39 @@ def test_severity_table_pooling_and_definition2():
     assert t["log-scale"]["max"] == 2.0 and t["log-scale"]["mean"] == 1.5
     assert t["color (DC)"]["catastrophe_pct"] == 100.0 and t["color (SH)"]["n"] == 2
     assert t["mean"]["catastrophe_pct"] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# SSIM (Sec. 3 "Metrics and severity"; Wang et al. 2004)
+# ---------------------------------------------------------------------------
+def test_ssim_identical_and_constant_images():
+    rng = np.random.default_rng(S.SEED_BASE + 76)
+    a = rng.random((30, 41, 3), dtype=np.float32)
+    assert O.ssim(a, a) == 1.0
+    c1, c2 = 0.25, 0.75
+    x = np.full((20, 20, 3), c1, np.float32)
+    y = np.full((20, 20, 3), c2, np.float32)
+    C1 = 0.01 ** 2
+    want = (2 * c1 * c2 + C1) / (c1 * c1 + c2 * c2 + C1)   # variances and covariance vanish
+    assert abs(O.ssim(x, y) - want) < 1e-12
+
+
+def test_ssim_equals_separable_gaussian_filter_form():
+    nd = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(S.SEED_BASE + 77)
+    a = rng.random((37, 52, 3), dtype=np.float32)
+    b = np.clip(a + rng.normal(0, 0.05, a.shape).astype(np.float32), -0.2, 1.2).astype(np.float32)
+    b[3, 7, 1] = np.nan
+    ca, cb = np.clip(np.nan_to_num(a.astype(np.float64), nan=0.0), 0, 1), np.clip(np.nan_to_num(b.astype(np.float64), nan=0.0), 0, 1)
+    f = lambda z: nd.gaussian_filter(z, sigma=1.5, truncate=5 / 1.5, mode="constant")
+    vals = []
+    for c in range(3):
+        u, v = ca[..., c], cb[..., c]
+        mx, my = f(u), f(v)
+        vx, vy, cxy = f(u * u) - mx * mx, f(v * v) - my * my, f(u * v) - mx * my
+        C1, C2 = 0.01 ** 2, 0.03 ** 2
+        m = ((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2))
+        vals.append(m[5:-5, 5:-5])
+    want = float(np.mean(vals))
+    assert abs(O.ssim(b, a) - want) < 1e-12
+    assert abs(O.ssim(a, b) - O.ssim(b, a)) < 1e-12
