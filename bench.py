@@ -338,6 +338,8 @@ def main():
 
     # sort-first contamination (nodes a scale-sign upset corrupts), guard off / FIELD guard
     contam = contamination(G, S, h, scene, K_views, dev)
+    # SSIM of every (variant, view) from the re-blended pixels
+    ssim_line = ssim_campaign(G, S, h, d_flips, nflips, K_views, dev)
 
     # roofline of the dominant kernel (dirty-tile blend): FP32-pipe bound
     clocks = clk.summary()
@@ -379,6 +381,7 @@ def main():
         "mpix_s_effective": value * K_views * Wd * Hd / 1e6,
         "plain_loop": plain,
         "contamination": contam,
+        "ssim": ssim_line,
         "speedup_vs_plain_loop": value / plain["value"],
         "batch_latency_ms": {"p50": p50, "p99": p99, "what": f"one launch of {B} variants x {K_views} views"},
         "wall_s_timed_region": wall,
@@ -488,6 +491,32 @@ def campaign_analytics(G, S, dev):
     res["scaling"] = {"sizes": sizes, "upsets_per_size": "20,000 on log-scale sign/exponent bits (words 3-5, bits 23-31)",
                       "error": "per-variant MSE (800x800x3)", **fits,
                       "guard_mean_error_factor_at_largest": mean["no_guard"][-1] / max(mean["field_guard"][-1], 1e-30)}
+    return res
+
+
+def ssim_campaign(G, S, h, d_flips, nflips, K_views, dev, count=1024):
+    """The campaign with the per-(variant, view) SSIM on and off (same upsets):
+    injections/s of each, and the SSIM distribution."""
+    import torch
+    count = min(count, nflips)
+    out = G.device_bytes(count * K_views * 24, dev)
+    ss = torch.zeros(count * K_views, dtype=torch.float64, device=dev)
+    d = d_flips[:8 * count]
+    res = {}
+    for name, arg in (("with_ssim", ss), ("without", None)):
+        G.gs_inject_and_render_ex(h, d, count, G.GS_GUARD_OFF, S.GUARD_WORDS_DEFAULT, out, None, arg)   # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            G.gs_inject_and_render_ex(h, d, count, G.GS_GUARD_OFF, S.GUARD_WORDS_DEFAULT, out, None, arg)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_injections_per_s"] = 3 * count / (e0.elapsed_time(e1) / 1000.0)
+    v = ss.cpu().numpy()
+    res.update({"upsets": f"{count} of the benchmark's upsets, {K_views} views each",
+                "mean_ssim": float(v.mean()), "min_ssim": float(v.min()),
+                "frac_below_0.99": float((v < 0.99).mean())})
     return res
 
 

@@ -162,6 +162,16 @@ GS_API gs_status gs_render(gs_scene* scene, const gs_camera* host_cams, int K, f
 /* (e) Comparison of K image pairs (layout as gs_render), one gs_result each
  * (clamps = 0).  dev_out: K records. */
 GS_API gs_status gs_compare(const float* dev_a, const float* dev_b, int H, int W, int K, gs_result* dev_out, void* stream);
+/* SSIM of K image pairs (Sec. 3 "Metrics and severity", Wang et al. 2004):
+ * per channel, Gaussian-weighted local means, variances and covariance over an
+ * 11x11 window (sigma 1.5, normalised), SSIM = (2 mx my + C1)(2 sxy + C2) /
+ * ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)), C1 = 0.01^2, C2 = 0.03^2, on values
+ * clamped to [0, 1] (NaN as 0); dev_out[k] (double) = the mean over the pixels
+ * at least 5 from every edge and over the channels (1 when there are none).
+ * dev_test / dev_clean: K images H*W*3 float32 (layout as gs_render).  Per-pixel
+ * fp32 arithmetic with fixed rounding, summed in fixed point (2^-32). */
+GS_API gs_status gs_ssim(const float* dev_test, const float* dev_clean, int H, int W, int K, double* dev_out,
+                         void* stream);
 
 /* Allocation-free variant of gs_compare (the paper has no counterpart; it is a
  * library convenience).  For callers that must not allocate device memory once
@@ -215,6 +225,18 @@ GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_f
 GS_API gs_status gs_inject_and_render_regions(gs_scene* scene, const gs_flip* dev_flips, int B, int guard_mode,
                                               uint64_t word_mask, gs_result* dev_out, uint64_t* dev_regions,
                                               void* stream);
+/* gs_inject_and_render for single-flip variants with optional extra outputs
+ * (device, caller-owned, each may be NULL): dev_regions as in
+ * gs_inject_and_render_regions; dev_ssim (B*K doubles) the SSIM of every
+ * (variant, view) against its clean frame, as gs_ssim defines it, computed
+ * from the re-blended pixels only (SSIM is exactly 1 wherever a window is
+ * unchanged) and bit-identical to gs_ssim on the full re-rendered frame.  The
+ * SSIM buffers (about 270 MB plus 16 B per (variant, view, tile)) are
+ * allocated on first use; GS_ERR_CAPACITY if a batch has more dirty tiles
+ * than they hold (retry with a smaller gs_set_batch). */
+GS_API gs_status gs_inject_and_render_ex(gs_scene* scene, const gs_flip* dev_flips, int B, int guard_mode,
+                                         uint64_t word_mask, gs_result* dev_out, uint64_t* dev_regions,
+                                         double* dev_ssim, void* stream);
 /* Enable (default) or disable CUDA-graph replay of the batched dirty-tile step. */
 GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
 /* Work counters for measurement: while enabled, the dirty-tile kernels add

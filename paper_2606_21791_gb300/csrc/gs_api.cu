@@ -27,7 +27,9 @@ gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* of
 gs_status launch_zero_acc(CmpAcc* acc, int count, cudaStream_t st);
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
                              void* plan, uint2* cand, uint32_t* groups, uint32_t gcap, CmpAcc* acc,
-                             unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, cudaStream_t st);
+                             unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, const SsimBufs& sb,
+                             cudaStream_t st);
+gs_status launch_ssim_out(const CmpAcc* acc, int count, const void* dev_views, int K, double* out, cudaStream_t st);
 gs_status launch_regions_out(const CmpAcc* acc, int count, unsigned long long* out, cudaStream_t st);
 gs_status launch_finalize_dirty(const CmpAcc* acc, int count, gs_result* out, const unsigned int* clean_nonfin, int K,
                                 cudaStream_t st);
@@ -122,8 +124,11 @@ void destroy_graphs(gs_scene* s) {
     s->graphs.clear();
 }
 
+void free_ssim_buffers(gs_scene* s);
+
 void free_views(gs_scene* s) {
     destroy_graphs(s);
+    free_ssim_buffers(s);
     for (auto& v : s->views) {
         cudaFree(v.recs);
         cudaFree(v.rects);
@@ -152,10 +157,43 @@ void free_views(gs_scene* s) {
     s->dev_clean_recs = nullptr;
 }
 
+void free_ssim_buffers(gs_scene* s) {
+    cudaFree(s->ssim.slot_group);
+    cudaFree(s->ssim.slot_flags);
+    cudaFree(s->ssim.deltas);
+    cudaFree(s->ssim.tile_map);
+    cudaFree(s->ssim.ssim_map);
+    cudaFree(s->ssim.overflow);
+    s->ssim = SsimBufs{};
+}
+
+// SSIM buffers sized for the current batch capacity (zeroed: generation 0 is never current)
+gs_status ensure_ssim_buffers(gs_scene* s) {
+    if (s->ssim.tile_map) return GS_OK;
+    const int K = std::max(s->K, 1);
+    SsimBufs b{};
+    b.slot_cap = (uint32_t)std::min<uint64_t>(s->plan_cap, 1ull << 18);
+    b.delta_cap = (uint32_t)std::min<uint64_t>((kTilePix / 32) * s->plan_cap, 1ull << 19);
+    b.max_tiles = (uint32_t)std::max(s->max_tiles, 1);
+    const size_t maps = (size_t)s->cap_B * K * b.max_tiles;
+    s->ssim = b;   // caps now; pointers below (freed together on failure)
+    GS_TRY(dmalloc((void**)&s->ssim.slot_group, sizeof(uint32_t) * 8 * b.slot_cap));
+    GS_TRY(dmalloc((void**)&s->ssim.slot_flags, sizeof(uint32_t) * b.slot_cap));
+    GS_TRY(dmalloc((void**)&s->ssim.deltas, sizeof(float4) * 32 * (size_t)b.delta_cap));
+    GS_TRY(dmalloc((void**)&s->ssim.tile_map, sizeof(unsigned long long) * maps));
+    GS_TRY(dmalloc((void**)&s->ssim.ssim_map, sizeof(unsigned long long) * maps));
+    GS_TRY(dmalloc((void**)&s->ssim.overflow, sizeof(unsigned int)));
+    GS_CUDA(cudaMemset(s->ssim.tile_map, 0, sizeof(unsigned long long) * maps));
+    GS_CUDA(cudaMemset(s->ssim.ssim_map, 0, sizeof(unsigned long long) * maps));
+    GS_CUDA(cudaMemset(s->ssim.overflow, 0, sizeof(unsigned int)));
+    return GS_OK;
+}
+
 gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     int K = std::max(s->K, 1);
     if (B <= s->cap_B && fpv * B <= s->cap_flips) return GS_OK;
     destroy_graphs(s);
+    free_ssim_buffers(s);
     cudaFree(s->flip_stage);
     cudaFree(s->desc);
     cudaFree(s->item_off);
@@ -177,6 +215,7 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     GS_TRY(dmalloc((void**)&s->acc, sizeof(CmpAcc) * cb * K));
     GS_TRY(dmalloc((void**)&s->res_stage, sizeof(gs_result) * cb * K));
     GS_TRY(dmalloc((void**)&s->queue, sizeof(unsigned int) * 8));
+    GS_CUDA(cudaMemset(s->queue, 0, sizeof(unsigned int) * 8));   // queue[6]: batch generation
     GS_TRY(dmalloc((void**)&s->saved, sizeof(uint32_t) * cf));
     // every (variant, view) can dirty at most every tile of its view
     s->plan_cap = (uint64_t)cb * K * (uint64_t)std::max(s->max_tiles, 1);
@@ -207,25 +246,27 @@ gs_status check_flip_args(gs_scene* s, const gs_flip* flips, int B, int fpv, int
 }
 
 // enqueue one dirty-tile batch (B <= cap_B, flips already in flip_stage)
-gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaStream_t st) {
+gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, bool ssim, cudaStream_t st) {
     int K = s->K;
     GS_TRY(launch_inject_prep(s, s->dev_cams, K, s->flip_stage, B, guard_mode, mask,
                               (const uint2* const*)s->dev_clean_rects, (const BlendRec* const*)s->dev_clean_recs,
                               s->desc, s->item_off, s->acc, s->queue, st));
     // external records: inside a stream capture they become event-record nodes of the graph
     if (s->ev_k0) GS_CUDA(cudaEventRecordWithFlags(s->ev_k0, st, cudaEventRecordExternal));
+    const SsimBufs sb = ssim ? s->ssim : SsimBufs{};
     GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->cand, s->groups,
-                              (uint32_t)((kTilePix / 32) * s->plan_cap), s->acc, s->queue, s->work_ctr, s->ev_kp, st));
+                              (uint32_t)((kTilePix / 32) * s->plan_cap), s->acc, s->queue, s->work_ctr, s->ev_kp, sb,
+                              st));
     if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
     GS_TRY(launch_finalize_dirty(s->acc, B * K, s->res_stage, s->clean_nonfin, K, st));
     return GS_OK;
 }
 
-gs_status run_dirty_batch(gs_scene* s, int B, int guard_mode, uint64_t mask, cudaStream_t st) {
-    if (!s->use_graphs || s->work_ctr) return enqueue_dirty(s, B, guard_mode, mask, st);
+gs_status run_dirty_batch(gs_scene* s, int B, int guard_mode, uint64_t mask, bool ssim, cudaStream_t st) {
+    if (!s->use_graphs || s->work_ctr) return enqueue_dirty(s, B, guard_mode, mask, ssim, st);
     GraphEntry* ge = nullptr;
     for (auto& g : s->graphs)
-        if (g.B == B && g.guard == guard_mode && g.mask == mask) ge = &g;
+        if (g.B == B && g.guard == guard_mode && g.mask == mask && g.ssim == ssim) ge = &g;
     if (!ge) {
         dirty_grid();   // occupancy query outside the capture
         cudaStream_t cs;
@@ -234,12 +275,13 @@ gs_status run_dirty_batch(gs_scene* s, int B, int guard_mode, uint64_t mask, cud
         g.B = B;
         g.guard = guard_mode;
         g.mask = mask;
+        g.ssim = ssim;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             cudaStreamDestroy(cs);
             return cuda_error(e, "cudaStreamBeginCapture");
         }
-        gs_status qs = enqueue_dirty(s, B, guard_mode, mask, cs);
+        gs_status qs = enqueue_dirty(s, B, guard_mode, mask, ssim, cs);
         e = cudaStreamEndCapture(cs, &g.graph);
         cudaStreamDestroy(cs);
         if (qs != GS_OK) {
@@ -357,6 +399,7 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->plan);
     cudaFree(s->cand);
     cudaFree(s->groups);
+    free_ssim_buffers(s);
     cudaFree(s->clean_nonfin);
     cudaFree(s->work_ctr);
     if (s->ev_k0) cudaEventDestroy(s->ev_k0);
@@ -578,7 +621,7 @@ gs_status gs_clean_image(gs_scene* s, int k, float* dev_rgb, void* stream) {
 
 namespace {
 gs_status inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode, uint64_t word_mask,
-                            gs_result* dev_out, uint64_t* dev_regions, void* stream);
+                            gs_result* dev_out, uint64_t* dev_regions, double* dev_ssim, void* stream);
 }
 
 gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int flips_per_variant, int guard_mode,
@@ -587,32 +630,51 @@ gs_status gs_inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int
     if (!dev_out && B > 0) return set_error(GS_ERR_ARG, "dev_out is NULL");
     if (flips_per_variant != 1)
         return gs_inject_and_render_full(s, dev_flips, B, flips_per_variant, guard_mode, word_mask, dev_out, stream);
-    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, nullptr, stream);
+    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, nullptr, nullptr, stream);
 }
 
 gs_status gs_inject_and_render_regions(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode,
                                        uint64_t word_mask, gs_result* dev_out, uint64_t* dev_regions, void* stream) {
     GS_TRY(check_flip_args(s, dev_flips, B, 1, guard_mode, word_mask));
     if ((!dev_out || !dev_regions) && B > 0) return set_error(GS_ERR_ARG, "dev_out or dev_regions is NULL");
-    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, dev_regions, stream);
+    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, dev_regions, nullptr, stream);
+}
+
+gs_status gs_inject_and_render_ex(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode, uint64_t word_mask,
+                                  gs_result* dev_out, uint64_t* dev_regions, double* dev_ssim, void* stream) {
+    GS_TRY(check_flip_args(s, dev_flips, B, 1, guard_mode, word_mask));
+    if (!dev_out && B > 0) return set_error(GS_ERR_ARG, "dev_out is NULL");
+    return inject_and_render(s, dev_flips, B, guard_mode, word_mask, dev_out, dev_regions, dev_ssim, stream);
 }
 
 namespace {
 gs_status inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int guard_mode, uint64_t word_mask,
-                            gs_result* dev_out, uint64_t* dev_regions, void* stream) {
+                            gs_result* dev_out, uint64_t* dev_regions, double* dev_ssim, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
     const int max_chunk = max_batch(K);
     const int chunk = s->batch > 0 ? std::min(s->batch, max_chunk) : max_chunk;
     GS_TRY(ensure_batch_buffers(s, chunk, 1));
+    const bool ssim = dev_ssim != nullptr;
+    if (ssim) GS_TRY(ensure_ssim_buffers(s));
     for (int b0 = 0; b0 < B; b0 += chunk) {
         int nb = std::min(chunk, B - b0);
         GS_CUDA(cudaMemcpyAsync(s->flip_stage, dev_flips + b0, sizeof(gs_flip) * nb, cudaMemcpyDeviceToDevice, st));
-        GS_TRY(run_dirty_batch(s, nb, guard_mode, word_mask, st));
+        GS_TRY(run_dirty_batch(s, nb, guard_mode, word_mask, ssim, st));
         GS_CUDA(cudaMemcpyAsync(dev_out + (size_t)b0 * K, s->res_stage, sizeof(gs_result) * nb * K,
                                 cudaMemcpyDeviceToDevice, st));
         if (dev_regions)
             GS_TRY(launch_regions_out(s->acc, nb * K, (unsigned long long*)dev_regions + (size_t)2 * b0 * K, st));
+        if (ssim) GS_TRY(launch_ssim_out(s->acc, nb * K, s->dev_views, K, dev_ssim + (size_t)b0 * K, st));
+    }
+    if (ssim) {   // a capacity overflow leaves some SSIM values incomplete: report it
+        unsigned int over = 0;
+        GS_CUDA(cudaMemcpyAsync(&over, s->ssim.overflow, sizeof(over), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+        if (over) {
+            GS_CUDA(cudaMemset(s->ssim.overflow, 0, sizeof(unsigned int)));
+            return set_error(GS_ERR_CAPACITY, "SSIM buffers too small for this batch: use a smaller batch");
+        }
     }
     return GS_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -76,6 +77,7 @@ struct CmpAcc {
     unsigned int pad;
     unsigned long long reg_actual;   // dirty engine: 8x8 screen cells holding a footprint pixel
     unsigned long long reg_pred;     // dirty engine: cells met by the changed primitive's tile rects
+    unsigned long long ssim_fx;      // sum over pixels and channels of (1 - SSIM), fixed point 2^-32 (signed)
 };
 
 // Screen cells of the contamination masks: an 8x8 grid, cell of pixel (x, y) =
@@ -96,6 +98,52 @@ __host__ __device__ inline unsigned long long rect_cells(uint2 rect, int W, int 
         for (int cx = cx0; cx <= cx1; cx++) m |= 1ull << (cy * 8 + cx);
     return m;
 }
+
+struct ViewPtrs {
+    const BlendRec* recs;
+    const uint32_t* ids;
+    const uint32_t* dk;      // depth bits of ids[j] (list-aligned)
+    const uint2* ranges;
+    const float* clean;
+    const uint32_t* stop;    // clean stop index of every pixel
+    const uint32_t* tile_stop;   // largest stop index of each tile
+    const unsigned long long* stop_key;   // (depth bits, id) of the list entry at tile_stop; ~0 if none
+    const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
+    const uint32_t* ck_off;      // first checkpoint of each tile
+    const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
+    int W, H, tiles_x, pad;
+};
+
+// One dirty tile that needs re-blending (112 B).  ins is the insertion position
+// in the clean list without the primitive's old entry; cut is the first changed
+// position of the clean list; rec is the corrupted record (when flags bit 1);
+// mask marks the tile's active pixels (natural order, 8 x 32 bits).
+struct __align__(16) PlanItem {
+    BlendRec rec;
+    uint32_t mask[kTilePix / 32];
+    uint32_t bk;      // (variant, view) = variant * K + view
+    uint32_t tile;
+    uint32_t s, e;    // clean list range
+    uint32_t pp, ins, cut;
+    uint32_t flags;   // bit 0: old entry in this tile, bit 1: corrupted entry in this tile
+};
+static_assert(sizeof(PlanItem) == 112 && offsetof(PlanItem, mask) == 48 && offsetof(PlanItem, bk) == 80 &&
+                  offsetof(PlanItem, pp) == 96,
+              "k_plan writes PlanItem as 7 16-byte parts");
+
+// Buffers of the dirty-tile SSIM (all NULL when it is off): per plan slot the
+// delta index of each of its 8x4 blocks (0xffffffff: none), per delta index the
+// new values of the block's 32 pixels, per (variant, view) and tile the plan
+// slot (generation << 32 | slot) and the SSIM claim (generation << 32).
+struct SsimBufs {
+    uint32_t* slot_group;              // [slot_cap * 8]
+    uint32_t* slot_flags;              // [slot_cap] changed pixels: bit 4 any, 0-3 within 5 of the left/right/top/bottom edge
+    float4* deltas;                    // [delta_cap * 32]
+    unsigned long long* tile_map;      // [B*K * max_tiles]
+    unsigned long long* ssim_map;      // [B*K * max_tiles]
+    unsigned int* overflow;            // set when a capacity is exceeded
+    uint32_t slot_cap, delta_cap, max_tiles, pad;
+};
 
 // Dirty-tile work descriptor of one (variant, view).
 struct DirtyDesc {
@@ -157,6 +205,7 @@ struct GraphEntry {
     int B = 0;
     int guard = -2;
     uint64_t mask = 0;
+    bool ssim = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -201,6 +250,7 @@ struct gs_scene {
     void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
     uint2* cand = nullptr;                  // candidate tiles of the plan's first pass [plan_cap]
     uint32_t* groups = nullptr;             // 8x4 pixel blocks to re-blend, (item << 3) | block [8 * plan_cap]
+    gs::SsimBufs ssim{};                    // dirty-tile SSIM buffers (allocated on first use, else NULL)
     uint64_t plan_cap = 0;
     unsigned int* clean_nonfin = nullptr;   // [K] non-finite pixels of each clean view
     uint32_t* saved = nullptr;

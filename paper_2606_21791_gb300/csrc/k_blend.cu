@@ -409,26 +409,13 @@ __global__ void k_finalize(const CmpAcc* acc, int count, gs_result* out, const u
 
 __global__ void k_zero_acc(CmpAcc* acc, int count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u, 0u, 0u, 0ull, 0ull};
+    if (i < count) acc[i] = CmpAcc{0ull, 0u, 0u, 0u, 0u, 0u, 0u, 0ull, 0ull, 0ull};
 }
 
 // ---------------------------------------------------------------------------
 // dirty-tile persistent kernel
 // ---------------------------------------------------------------------------
-struct ViewPtrs {
-    const BlendRec* recs;
-    const uint32_t* ids;
-    const uint32_t* dk;      // depth bits of ids[j] (list-aligned)
-    const uint2* ranges;
-    const float* clean;
-    const uint32_t* stop;    // clean stop index of every pixel
-    const uint32_t* tile_stop;   // largest stop index of each tile
-    const unsigned long long* stop_key;   // (depth bits, id) of the list entry at tile_stop; ~0 if none
-    const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
-    const uint32_t* ck_off;      // first checkpoint of each tile
-    const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
-    int W, H, tiles_x, pad;
-};
+
 
 // First index in [lo, hi) whose (depth bits, id) is not below (dkey, p); the
 // lists are sorted by (depth, id).  Called by a whole warp: each round probes 31
@@ -459,22 +446,7 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
     return lo + __popc(__ballot_sync(0xffffffffu, less));
 }
 
-// One dirty tile that needs re-blending (112 B).  ins is the insertion position
-// in the clean list without the primitive's old entry; cut is the first changed
-// position of the clean list; rec is the corrupted record (when flags bit 1);
-// mask marks the tile's active pixels (natural order, 8 x 32 bits).
-struct __align__(16) PlanItem {
-    BlendRec rec;
-    uint32_t mask[kBT / 32];
-    uint32_t bk;      // (variant, view) = variant * K + view
-    uint32_t tile;
-    uint32_t s, e;    // clean list range
-    uint32_t pp, ins, cut;
-    uint32_t flags;   // bit 0: old entry in this tile, bit 1: corrupted entry in this tile
-};
-static_assert(sizeof(PlanItem) == 112 && offsetof(PlanItem, mask) == 48 && offsetof(PlanItem, bk) == 80 &&
-                  offsetof(PlanItem, pp) == 96,
-              "k_plan writes PlanItem as 7 16-byte parts");
+
 
 // A pixel of a dirty tile keeps its clean value, bit for bit, when its clean
 // blend stopped before the first changed list position, or when its blend skips
@@ -656,7 +628,8 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
                                                       const DirtyDesc* __restrict__ desc, int K,
                                                       const uint2* __restrict__ cand, PlanItem* __restrict__ plan,
                                                       uint32_t* __restrict__ groups, uint32_t gcap,
-                                                      unsigned int* __restrict__ counts, unsigned long long* work) {
+                                                      unsigned int* __restrict__ counts, unsigned long long* work,
+                                                      SsimBufs sb) {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -736,6 +709,17 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
             const uint32_t gi = gbase + __popc(gm & ((1u << lane) - 1u));
             groups[heavy ? gi : gcap - 1u - gi] = (slot << 3) | (uint32_t)lane;
         }
+        if (sb.tile_map) {   // dirty-tile SSIM: tile -> slot of this batch, no block delta yet
+            if (slot < sb.slot_cap) {
+                if (lane < kTilePix / 32) sb.slot_group[(size_t)slot * 8 + lane] = 0xffffffffu;
+                if (lane == 0) sb.slot_flags[slot] = 0u;
+                if (lane == 0)
+                    sb.tile_map[(size_t)ibk * sb.max_tiles + (size_t)tile] =
+                        ((unsigned long long)counts[6] << 32) | slot;
+            } else if (lane == 0) {
+                atomicOr(sb.overflow, 1u);
+            }
+        }
         uint4* dst = reinterpret_cast<uint4*>(&plan[slot]);
         if (lane < 3) {
             dst[lane] = reinterpret_cast<const uint4*>(&d.rec)[lane];
@@ -802,7 +786,7 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
                                                               const unsigned int* __restrict__ counts,
                                                               CmpAcc* __restrict__ acc,
                                                               unsigned int* __restrict__ queue,
-                                                              unsigned long long* work) {
+                                                              unsigned long long* work, SsimBufs sb) {
     __shared__ WarpRing rings[kDirtyWarps];
     const int lane = threadIdx.x & 31;
     WarpRing& R = rings[threadIdx.x >> 5];
@@ -904,6 +888,28 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
         // its clean value (Delta = 0), and the clean image's non-finite pixels are
         // counted once per view at finalize
         const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
+        if (sb.deltas) {   // dirty-tile SSIM: keep the block's new values (delta index = work-queue index)
+            const uint32_t slot = code >> 3;
+            if (gi < sb.delta_cap && slot < sb.slot_cap) {
+                if (active) sb.deltas[(size_t)gi * 32 + lane] = make_float4(v0, v1, v2, 0.0f);
+                if (lane == 0) sb.slot_group[(size_t)slot * 8 + w] = gi;
+                // where the changed pixels are: which neighbouring tiles their SSIM windows reach
+                bool ch = false;
+                if (active) {
+                    const float* c = v.clean + ((size_t)g.py * v.W + g.px) * 3;
+                    ch = __float_as_uint(v0) != __float_as_uint(c[0]) || __float_as_uint(v1) != __float_as_uint(c[1]) ||
+                         __float_as_uint(v2) != __float_as_uint(c[2]);
+                }
+                const int lx = g.px % kTile, ly = g.py % kTile;
+                const unsigned f = ch ? (16u | (lx < 5 ? 1u : 0u) | (lx > kTile - 6 ? 2u : 0u) | (ly < 5 ? 4u : 0u) |
+                                         (ly > kTile - 6 ? 8u : 0u))
+                                      : 0u;
+                const unsigned fo = __reduce_or_sync(0xffffffffu, f);
+                if (lane == 0 && fo) atomicOr(&sb.slot_flags[slot], fo);
+            } else if (lane == 0) {
+                atomicOr(sb.overflow, 1u);
+            }
+        }
         PixCmp r{0ull, 0.0f, false, false};
         bool clean_bad = false;
         if (active) {
@@ -1079,28 +1085,34 @@ size_t plan_item_size() { return sizeof(PlanItem); }
 // queue[0]: blend work queue, queue[1]: plan items, queue[2]: candidate tiles,
 // queue[3] / queue[4]: heavy / light groups (all zeroed by the injector); cand
 // holds as many entries as plan, groups gcap = 8 per plan entry.
+gs_status launch_dirty_ssim(const void* dev_views, int K, const void* plan, const unsigned int* queue,
+                            const SsimBufs& sb, CmpAcc* acc, cudaStream_t st);
+
 gs_status launch_dirty_blend(const void* dev_views, const DirtyDesc* desc, const uint32_t* item_off, int BK, int K,
                              void* plan, uint2* cand, uint32_t* groups, uint32_t gcap, CmpAcc* acc,
-                             unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, cudaStream_t st) {
+                             unsigned int* queue, unsigned long long* work, cudaEvent_t ev_mid, const SsimBufs& sb,
+                             cudaStream_t st) {
     const ViewPtrs* views = (const ViewPtrs*)dev_views;
     PlanItem* pl = (PlanItem*)plan;
     const int plan_blocks = num_sms() * 8;
     if (work) {
         k_plan_filter<true><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, cand, queue, work);
-        k_plan_exact<true><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, groups, gcap, queue, work);
+        k_plan_exact<true><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, groups, gcap, queue, work, sb);
     } else {
         k_plan_filter<false><<<plan_blocks, 256, 0, st>>>(views, desc, item_off, BK, K, cand, queue, nullptr);
-        k_plan_exact<false><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, groups, gcap, queue, nullptr);
+        k_plan_exact<false><<<plan_blocks, 256, 0, st>>>(views, desc, K, cand, pl, groups, gcap, queue, nullptr, sb);
     }
     if (ev_mid) {
         cudaError_t e = cudaEventRecordWithFlags(ev_mid, st, cudaEventRecordExternal);
         if (e != cudaSuccess) return set_error(GS_ERR_CUDA, cudaGetErrorString(e));
     }
     if (work)
-        k_dirty<true><<<dirty_grid(), kDirtyWarps * 32, 0, st>>>(views, K, pl, groups, gcap, queue, acc, queue, work);
+        k_dirty<true><<<dirty_grid(), kDirtyWarps * 32, 0, st>>>(views, K, pl, groups, gcap, queue, acc, queue, work,
+                                                                sb);
     else
         k_dirty<false><<<dirty_grid(), kDirtyWarps * 32, 0, st>>>(views, K, pl, groups, gcap, queue, acc, queue,
-                                                                 nullptr);
+                                                                 nullptr, sb);
+    if (sb.tile_map) GS_TRY(launch_dirty_ssim(dev_views, K, plan, queue, sb, acc, st));
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

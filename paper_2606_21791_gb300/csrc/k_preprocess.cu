@@ -455,6 +455,7 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     z.clean_nonfinite_replaced = 0u;
     z.pad = 0u;
     z.reg_actual = 0ull;
+    z.ssim_fx = 0ull;
     // contamination prediction: the cells the primitive's tile rects meet, before
     // and after the upset, when its stored words changed
     z.reg_pred = changed ? rect_cells(orect, cams[k].W, cams[k].H, kTile) |
@@ -495,6 +496,7 @@ __global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, in
         queue[2] = 0u;
         queue[3] = 0u;
         queue[4] = 0u;
+        queue[6] += 1u;   // batch generation (tags of the dirty-tile SSIM maps)
     }
 }
 

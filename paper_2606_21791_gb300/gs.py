@@ -60,6 +60,8 @@ SIGNATURES = {
     "gs_inject_and_render": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_inject_and_render_full": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_inject_and_render_regions": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp]),
+    "gs_inject_and_render_ex": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp]),
+    "gs_ssim": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "gs_set_graphs": (_i32, [_vp, _i32]),
     "gs_set_batch": (_i32, [_vp, _i32]),
     "gs_count_work": (_i32, [_vp, _i32]),
@@ -257,6 +259,19 @@ def gs_inject_and_render_regions(scene, dev_flips, B: int, guard_mode: int, word
     _check(load_library().gs_inject_and_render_regions(scene, _ptr(dev_flips), B, guard_mode, word_mask,
                                                        _ptr(dev_out), _ptr(dev_regions), _stream(stream)),
            "gs_inject_and_render_regions")
+
+
+def gs_inject_and_render_ex(scene, dev_flips, B: int, guard_mode: int, word_mask: int, dev_out, dev_regions=None,
+                            dev_ssim=None, stream=None):
+    """Single-flip campaign with optional region masks (B*K*2 uint64) and SSIM (B*K float64)."""
+    _check(load_library().gs_inject_and_render_ex(scene, _ptr(dev_flips), B, guard_mode, word_mask, _ptr(dev_out),
+                                                  _ptr(dev_regions), _ptr(dev_ssim), _stream(stream)),
+           "gs_inject_and_render_ex")
+
+
+def gs_ssim(dev_test, dev_clean, H: int, W: int, K: int, dev_out, stream=None):
+    """SSIM of K image pairs into dev_out (K float64, device)."""
+    _check(load_library().gs_ssim(_ptr(dev_test), _ptr(dev_clean), H, W, K, _ptr(dev_out), _stream(stream)), "gs_ssim")
 
 
 def gs_inject_and_render_full(scene, dev_flips, B: int, flips_per_variant: int, guard_mode: int, word_mask: int,

@@ -501,3 +501,68 @@ def test_contamination_regions_match_oracle(G, guard):
         assert ((r[:, :, 0] & ~r[:, :, 1]) == 0).all()
     finally:
         G.gs_free_scene(h)
+
+
+def test_ssim_image_pairs_match_oracle(G):
+    torch = _torch()
+    rng = np.random.default_rng(S.SEED_BASE + 78)
+    H, W = 67, 91                     # ragged: partial tiles on both edges
+    a = rng.random((2, H, W, 3), dtype=np.float32)
+    b = a.copy()
+    b[0] += rng.normal(0, 0.05, b[0].shape).astype(np.float32)
+    b[1, 10:30, 20:50] = 0.0
+    b[1, 5, 5, 0] = np.nan
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    G.gs_ssim(db, da, H, W, 2, out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()
+    o = np.array([O.ssim(b[k], a[k]) for k in range(2)])
+    assert np.abs(g - o).max() < 5e-5, (g, o)
+    G.gs_ssim(da, da, H, W, 2, out)
+    torch.cuda.synchronize()
+    assert (out.cpu().numpy() == 1.0).all()
+
+
+def test_dirty_tile_ssim_equals_full_frame_ssim(G):
+    """The campaign's SSIM, from re-blended pixels only, equals gs_ssim of the
+    full re-rendered frame bit for bit, and the oracle's SSIM within 5e-5."""
+    torch = _torch()
+    sc = S.make_scene(30000, 3, S.FP32, 79, layout="clusters")
+    cams = S.ring_cameras(2, 320, 240)
+    flips = S.flips_stratified(59 * 32, sc.n, sc.nwords, S.FP32, 80)[::4]
+    B, K, H, W = len(flips), 2, 240, 320
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        d = G.to_device(flips)
+        out = G.device_bytes(B * K * 24)
+        ss = torch.zeros(B * K, dtype=torch.float64, device="cuda")
+        G.gs_inject_and_render_ex(h, d, B, -1, S.GUARD_WORDS_DEFAULT, out, None, ss)
+        torch.cuda.synchronize()
+        g = G.from_device(out, G.RESULT_DTYPE).reshape(B, K)
+        ssim = ss.cpu().numpy().reshape(B, K)
+        ref = _campaign_gpu(G, h, flips, K)
+        for f in ("sse", "maxabs", "footprint", "nonfinite"):
+            assert np.array_equal(g[f], ref[f]), f
+        changed = np.nonzero(g["sse"].sum(axis=1) > 0)[0]
+        assert len(changed) > 4
+        sample = np.concatenate([changed[:: max(1, len(changed) // 12)], np.nonzero(g["sse"].sum(axis=1) == 0)[0][:2]])
+        clean = torch.empty(K * H * W * 3, dtype=torch.float32, device="cuda")
+        for k in range(K):
+            G.gs_clean_image(h, k, clean[k * H * W * 3:(k + 1) * H * W * 3])
+        img = torch.empty_like(clean)
+        one = torch.zeros(K, dtype=torch.float64, device="cuda")
+        for i in sample:
+            fi = G.to_device(flips[i:i + 1])
+            G.gs_apply_flips(h, fi, 1)
+            G.gs_render(h, cams, img)
+            G.gs_apply_flips(h, fi, 1)   # XOR back
+            G.gs_ssim(img, clean, H, W, K, one)
+            torch.cuda.synchronize()
+            assert np.array_equal(one.cpu().numpy(), ssim[i]), (i, one.cpu().numpy(), ssim[i])
+        assert np.array_equal(_read(G, h, sc), sc.planes)
+        _, _, _, o = O.campaign(sc.planes, S.FP32, 3, cams, flips[sample], nthreads=O.max_threads(), ssim=True)
+        assert np.abs(o - ssim[sample]).max() < 5e-5
+    finally:
+        G.gs_free_scene(h)
