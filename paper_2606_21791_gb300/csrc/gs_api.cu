@@ -231,7 +231,7 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
 
 // Variants per dirty-tile launch: the injector's scan covers at most 1024
 // (variant, view) pairs in one block.
-int max_batch(int K) { return std::max(1, std::min(kMaxBatch, 1024 / K)); }
+int max_batch(int K) { return std::max(1, std::min(kMaxBatch, kMaxPairs / K)); }
 
 gs_status check_flip_args(gs_scene* s, const gs_flip* flips, int B, int fpv, int guard_mode, uint64_t mask) {
     if (!s || (!flips && B > 0) || B < 0 || fpv < 1) return set_error(GS_ERR_ARG, "bad campaign arguments");
@@ -789,7 +789,7 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
     const int max_chunk = max_batch(K);
-    const int cands[6] = {8, 16, 32, 64, 128, 256};
+    const int cands[8] = {8, 16, 32, 64, 128, 256, 512, 1024};
     gs_result* out = nullptr;
     GS_CUDA(cudaMallocAsync((void**)&out, sizeof(gs_result) * (size_t)count * K, st));
     cudaEvent_t e0, e1;

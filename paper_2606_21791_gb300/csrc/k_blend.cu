@@ -561,7 +561,7 @@ __global__ __launch_bounds__(256) void k_plan_filter(const ViewPtrs* __restrict_
                                                     uint2* __restrict__ cand, unsigned int* __restrict__ counts,
                                                     unsigned long long* work) {
     const int lane = threadIdx.x & 31;
-    __shared__ uint32_t s_off[1025];   // item_off[0, BK], BK <= 1024
+    __shared__ uint32_t s_off[kMaxPairs + 1];   // item_off[0, BK], BK <= kMaxPairs
     for (int i = threadIdx.x; i <= BK; i += blockDim.x) s_off[i] = item_off[i];
     __syncthreads();
     const uint32_t total = s_off[BK];

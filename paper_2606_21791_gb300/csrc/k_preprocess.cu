@@ -464,13 +464,22 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     acc[bk] = z;
 }
 
-// Exclusive scan of the dirty-tile counts of the B*K (variant, view) pairs
-// (single block of 1024 threads); resets the work-queue counters.
+// Exclusive scan of the dirty-tile counts of the B*K <= kMaxPairs (variant,
+// view) pairs (single block of 1024 threads, kPairsPerThread consecutive pairs
+// each); resets the work-queue counters.
+constexpr int kPairsPerThread = kMaxPairs / 1024;
 __global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, int total, uint32_t* item_off,
                                                      unsigned int* queue) {
     __shared__ uint32_t wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const uint32_t items = tid < total ? n_items[tid] : 0u;
+    uint32_t a[kPairsPerThread];
+    uint32_t items = 0;
+#pragma unroll
+    for (int j = 0; j < kPairsPerThread; j++) {
+        const int p = tid * kPairsPerThread + j;
+        a[j] = p < total ? n_items[p] : 0u;
+        items += a[j];
+    }
     uint32_t x = items;
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -487,9 +496,14 @@ __global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, in
         wsum[lane] = s;
     }
     __syncthreads();
-    const uint32_t incl = x + (wid > 0 ? wsum[wid - 1] : 0u);
-    if (tid < total) item_off[tid] = incl - items;
-    if (tid == total - 1) item_off[total] = incl;
+    uint32_t run = x - items + (wid > 0 ? wsum[wid - 1] : 0u);   // exclusive offset of this thread's first pair
+#pragma unroll
+    for (int j = 0; j < kPairsPerThread; j++) {
+        const int p = tid * kPairsPerThread + j;
+        if (p < total) item_off[p] = run;
+        run += a[j];
+        if (p == total - 1) item_off[total] = run;
+    }
     if (tid == 0) {
         queue[0] = 0u;
         queue[1] = 0u;
@@ -537,7 +551,7 @@ gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K
                              int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects,
                              const BlendRec* const* dev_clean_recs, DirtyDesc* desc, uint32_t* item_off, CmpAcc* acc,
                              unsigned int* queue, cudaStream_t st) {
-    if (B * K > 1024 || K > 32) return set_error(GS_ERR_ARG, "B * K must be <= 1024 and K <= 32");
+    if (B * K > kMaxPairs || K > 32) return set_error(GS_ERR_ARG, "B * K must be <= 4096 and K <= 32");
     // the per-(variant, view) item counts go to the tail of item_off, past the B*K+1 offsets
     uint32_t* n_items = item_off + (B * K + 1);
     const int blocks = (B + kPrepWarps - 1) / kPrepWarps;

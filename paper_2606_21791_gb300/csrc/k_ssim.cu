@@ -186,7 +186,9 @@ __global__ __launch_bounds__(kTilePix) void k_dirty_ssim(const ViewPtrs* __restr
             }
         }
         __syncthreads();
-        if (!claim) continue;   // block-uniform
+        const int claimed = claim;
+        __syncthreads();   // every thread has read the flag before thread 0 rewrites it
+        if (!claimed) continue;   // block-uniform
         // the 3x3 tiles around (tx, ty): delta index and active mask of each 8x4 block
         // (0xffffffff / 0: no delta), resolved once for the staging below
         __shared__ uint32_t nb_gi[9][8], nb_mask[9][8];
