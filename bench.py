@@ -245,7 +245,7 @@ def main():
     # each rank takes its own slice of the upset list (independent units, no collective)
     d_flips = G.to_device(flips, dev)
     nflips = len(flips)
-    B, us_per = G.gs_autotune(h, d_flips, 4096, G.GS_GUARD_OFF, mask)
+    B, us_per = G.gs_autotune(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
     log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned batch B={B} ({us_per:.1f} us/variant)")
 
     out = G.device_bytes(B * K_views * 24, dev)

@@ -258,10 +258,10 @@ GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
  * (host array of 2 floats).  GS_ERR_STATE while timing is off. */
 GS_API gs_status gs_time_kernels(gs_scene* scene, int enable);
 GS_API gs_status gs_read_kernel_ms(gs_scene* scene, float* ms);
-/* Variants per dirty-tile launch (0 = largest allowed, min(1024, 4096 / K)). */
+/* Variants per dirty-tile launch (0 = largest allowed, min(2048, 8192 / K)). */
 GS_API gs_status gs_set_batch(gs_scene* scene, int batch);
 /* Autotuner: times the campaign over dev_flips[0, count) at batch sizes
- * 8, 16, 32, 64, 128, 256, 512, 1024 (those <= min(1024, 4096 / K)), keeps the fastest for this scene and
+ * 8, 16, 32, 64, 128, 256, 512, 1024, 2048 (those <= min(2048, 8192 / K)), keeps the fastest for this scene and
  * returns it (and its time per variant in microseconds, may be NULL).
  * Synchronises the stream. */
 GS_API gs_status gs_autotune(gs_scene* scene, const gs_flip* dev_flips, int count, int guard_mode, uint64_t word_mask,

@@ -789,7 +789,7 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
     cudaStream_t st = (cudaStream_t)stream;
     const int K = s->K;
     const int max_chunk = max_batch(K);
-    const int cands[8] = {8, 16, 32, 64, 128, 256, 512, 1024};
+    const int cands[9] = {8, 16, 32, 64, 128, 256, 512, 1024, 2048};
     gs_result* out = nullptr;
     GS_CUDA(cudaMallocAsync((void**)&out, sizeof(gs_result) * (size_t)count * K, st));
     cudaEvent_t e0, e1;

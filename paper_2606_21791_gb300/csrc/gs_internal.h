@@ -17,8 +17,8 @@ namespace gs {
 constexpr int kTile = 16;             // render tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;
 constexpr int kMaxWords = 59;
-constexpr int kMaxPairs = 4096;       // (variant, view) pairs per dirty-tile launch (one scan block)
-constexpr int kMaxBatch = 1024;       // variants per dirty-tile launch (also <= kMaxPairs / views)
+constexpr int kMaxPairs = 8192;       // (variant, view) pairs per dirty-tile launch (one scan block)
+constexpr int kMaxBatch = 2048;       // variants per dirty-tile launch (also <= kMaxPairs / views)
 // first bit of the sign and exponent bits a sign+exponent code protects
 __host__ __device__ inline int ecc_first_bit(int fmt) { return fmt == GS_FP32 ? 23 : (fmt == GS_FP16 ? 10 : 7); }
 constexpr int kSseFracBits = 39;      // fixed-point scale of per-pixel squared errors (3 * 2^39 * 5.1e6 px < 2^64)

@@ -551,7 +551,7 @@ gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K
                              int guard_mode, uint64_t mask, const uint2* const* dev_clean_rects,
                              const BlendRec* const* dev_clean_recs, DirtyDesc* desc, uint32_t* item_off, CmpAcc* acc,
                              unsigned int* queue, cudaStream_t st) {
-    if (B * K > kMaxPairs || K > 32) return set_error(GS_ERR_ARG, "B * K must be <= 4096 and K <= 32");
+    if (B * K > kMaxPairs || K > 32) return set_error(GS_ERR_ARG, "B * K must be <= 8192 and K <= 32");
     // the per-(variant, view) item counts go to the tail of item_off, past the B*K+1 offsets
     uint32_t* n_items = item_off + (B * K + 1);
     const int blocks = (B + kPrepWarps - 1) / kPrepWarps;

@@ -1,7 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times, on sampled outputs the oracle computes one by one.
 
-* 2,000,000 Gaussians, 4 views 1600x1040, batch 1024 (the largest batch the
+* 2,000,000 Gaussians, 4 views 1600x1040, batch 2048 (the largest batch the
   benchmark's autotuner picks from): the clean frame of view 0 against the
   oracle's render; a sample of the step's variants against the oracle campaign
   in view 0; the sampled variants' records against full re-renders (bit for bit).
@@ -53,7 +53,7 @@ def test_scale_workload_step_matches_oracle(G):
     h = G.gs_load_scene(sc.planes, sc.n, 3, S.FP32)
     try:
         G.gs_set_views(h, cams)
-        G.gs_set_batch(h, 1024)
+        G.gs_set_batch(h, 2048)
         # clean frame of view 0
         W, H = int(cams[0]["width"]), int(cams[0]["height"])
         clean_gpu = torch.empty(W * H * 3, dtype=torch.float32, device="cuda")
@@ -62,11 +62,11 @@ def test_scale_workload_step_matches_oracle(G):
         clean_or = O.render(sc.planes, S.FP32, 3, cams[0])
         ok = (np.abs(clean_gpu.astype(np.float64) - clean_or) <= PIX_TOL).all(axis=2).mean()
         assert ok >= 0.999, ok
-        # one step: 1024 variants x 4 views in one launch
-        step = flips[:1024]
+        # one step: 2048 variants x 4 views in one launch
+        step = flips[:2048]
         g = _records(G, h, step, 4)
         # sample: 16 variants, view 0, against the oracle
-        sample = np.arange(0, 1024, 64)
+        sample = np.arange(0, 2048, 128)
         o, _, _ = O.campaign(sc.planes, S.FP32, 3, cams[0:1], step[sample], clean_imgs=[clean_or],
                              nthreads=O.max_threads())
         npx = W * H * 3
