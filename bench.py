@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--only-guard", action="store_true", help="run only the guard measurement (profiling)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency measurement")
     ap.add_argument("--no-analytics", action="store_true", help="skip the Table 2 / scaling-law campaigns")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="variants per launch (default: the library's autotuner picks); for small profiling cases")
     ap.add_argument("--gaussians", type=int, default=2_000_000,
                     help="scene size (the 2M default is the benchmark; smaller only for profiling captures)")
     return ap.parse_args()
@@ -245,8 +247,13 @@ def main():
     # each rank takes its own slice of the upset list (independent units, no collective)
     d_flips = G.to_device(flips, dev)
     nflips = len(flips)
-    B, us_per = G.gs_autotune(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
-    log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned batch B={B} ({us_per:.1f} us/variant)")
+    if args.batch > 0:
+        G.gs_set_batch(h, args.batch)
+        B = args.batch
+        log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; batch B={B} (set)")
+    else:
+        B, us_per = G.gs_autotune(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
+        log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned batch B={B} ({us_per:.1f} us/variant)")
 
     out = G.device_bytes(B * K_views * 24, dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
