@@ -37,10 +37,12 @@ size_t plan_item_size();
 size_t view_ptrs_size();
 gs_status launch_stop_keys(const uint2* ranges, const uint32_t* tile_stop, const uint32_t* dk, const uint32_t* ids,
                            int ntiles, unsigned long long* out, cudaStream_t st);
-void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop,
-                    const unsigned long long* stop_key, const float4* ck,
-                    const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H);
+void fill_view_ptrs(void* host_dst, const ViewState& vs);
+gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int ntiles, int tiles_x,
+                        uint32_t* counts, const uint32_t* off, uint32_t* pos, cudaStream_t st);
+gs_status launch_exclusive_scan(const uint32_t* in, uint64_t n, uint32_t* out, unsigned long long* scratch,
+                                unsigned long long* total, cudaStream_t st);
+uint64_t scan_scratch_len(uint64_t n);
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
                                   const uint32_t* ck_cnt, unsigned int* clean_nonfin, cudaStream_t st);
@@ -139,6 +141,8 @@ void free_views(gs_scene* s) {
         cudaFree(v.stop);
         cudaFree(v.tile_stop);
         cudaFree(v.stop_key);
+        cudaFree(v.bl_off);
+        cudaFree(v.bl_pos);
         cudaFree(v.ck);
         cudaFree(v.ck_off);
         cudaFree(v.ck_cnt);
@@ -584,8 +588,32 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
         }
         GS_TRY(launch_stop_keys(v.ranges, v.tile_stop, v.dk, v.ids, ntiles, v.stop_key, st));
         v.npairs = np;
-        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v.recs, v.ids, v.dk, v.ranges, v.clean, v.stop,
-                       v.tile_stop, v.stop_key, v.ck, v.ck_off, v.ck_cnt, v.cam.W, v.cam.H);
+        // per (tile, 8x4 block) sublists of the clean lists
+        {
+            const uint64_t nb = (uint64_t)ntiles * 8;
+            uint32_t* counts = nullptr;
+            unsigned long long* scratch = nullptr;
+            GS_TRY(dmalloc((void**)&v.bl_off, sizeof(uint32_t) * (nb + 1)));
+            GS_TRY(dmalloc((void**)&counts, sizeof(uint32_t) * nb));
+            GS_TRY(dmalloc((void**)&scratch, sizeof(unsigned long long) * (scan_scratch_len(nb) + 3)));
+            unsigned long long* total = scratch + scan_scratch_len(nb);
+            gs_status bs = launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, counts, nullptr, nullptr, st);
+            if (bs == GS_OK) bs = launch_exclusive_scan(counts, nb, v.bl_off, scratch, total, st);
+            unsigned long long tot = 0;
+            if (bs == GS_OK && cudaMemcpyAsync(&tot, total, sizeof(tot), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                bs = set_error(GS_ERR_CUDA, "sublist total");
+            if (bs == GS_OK && cudaStreamSynchronize(st) != cudaSuccess) bs = set_error(GS_ERR_CUDA, "sublist sync");
+            cudaFree(counts);
+            cudaFree(scratch);
+            GS_TRY(bs);
+            if (tot >= 0xffffffffull) return set_error(GS_ERR_CAPACITY, "block sublists exceed 2^32 entries");
+            const uint32_t tot32 = (uint32_t)tot;
+            GS_CUDA(cudaMemcpyAsync(v.bl_off + nb, &tot32, sizeof(tot32), cudaMemcpyHostToDevice, st));
+            GS_TRY(dmalloc((void**)&v.bl_pos, sizeof(uint32_t) * std::max<uint64_t>(tot, 1)));
+            GS_TRY(launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, nullptr, v.bl_off, v.bl_pos, st));
+            GS_CUDA(cudaStreamSynchronize(st));
+        }
+        fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v);
         crects[k] = v.rects;
         crecs[k] = v.recs;
         max_pairs = std::max(max_pairs, np);

@@ -109,6 +109,8 @@ struct ViewPtrs {
     const uint32_t* stop;    // clean stop index of every pixel
     const uint32_t* tile_stop;   // largest stop index of each tile
     const unsigned long long* stop_key;   // (depth bits, id) of the list entry at tile_stop; ~0 if none
+    const uint32_t* bl_off;      // per (tile, 8x4 block): start of its sublist in bl_pos (ntiles * 8 + 1)
+    const uint32_t* bl_pos;      // positions (in the tile's list) of the entries whose box meets the block
     const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
     const uint32_t* ck_off;      // first checkpoint of each tile
     const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
@@ -173,6 +175,8 @@ struct ViewState {
     uint32_t* stop = nullptr;        // [H*W] list index that stopped each clean pixel
     uint32_t* tile_stop = nullptr;   // [ntiles] largest stop index in each tile
     unsigned long long* stop_key = nullptr;   // [ntiles] (depth bits << 32 | id) of the entry at tile_stop (~0: none)
+    uint32_t* bl_off = nullptr;      // [ntiles * 8 + 1] start of each (tile, 8x4 block) sublist in bl_pos
+    uint32_t* bl_pos = nullptr;      // list positions whose box meets the block, ascending per sublist
     float4* ck = nullptr;            // clean-blend checkpoints [total][256 pixels]
     uint32_t* ck_off = nullptr;      // [ntiles]
     uint32_t* ck_cnt = nullptr;      // [ntiles]

@@ -762,6 +762,26 @@ struct WarpRing {
     float4 q[kWarpRing][3][32];   // [chunk slot][16-byte part of the record][entry]
 };
 
+// First index in [lo, hi) of the ascending array a whose value is not below key
+// (whole warp: each round probes 31 splitters and keeps 1/32 of the interval).
+__device__ __forceinline__ uint32_t warp_lower_bound_u32(const uint32_t* __restrict__ a, uint32_t lo, uint32_t hi,
+                                                         uint32_t key) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const uint32_t len = hi - lo;
+        bool less = false;
+        if (lane < 31) less = a[lo + (uint32_t)(((uint64_t)len * (uint32_t)(lane + 1)) >> 5)] < key;
+        const int c = __popc(__ballot_sync(0xffffffffu, less));
+        const uint32_t nlo = c == 0 ? lo : lo + (uint32_t)(((uint64_t)len * (uint32_t)c) >> 5) + 1;
+        const uint32_t nhi = c == 31 ? hi : lo + (uint32_t)(((uint64_t)len * (uint32_t)(c + 1)) >> 5);
+        lo = nlo;
+        hi = nhi;
+    }
+    const uint32_t pos = lo + (uint32_t)lane;
+    const bool less = pos < hi && a[pos] < key;
+    return lo + __popc(__ballot_sync(0xffffffffu, less));
+}
+
 // Entry m of the merged list: the inserted record (returns true) or the clean
 // list entry ci (relative to the tile's range).
 __device__ __forceinline__ bool merged_entry(uint32_t m, bool has_old, bool has_new, uint32_t pp, uint32_t ins,
@@ -832,14 +852,37 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
             p.c1 = st.z;
             p.c2 = st.w;
         }
-        const uint32_t nch = L > start ? (L - start + 31u) / 32u : 0u;
+        // This block's sublist of the clean list (the entries whose box meets the
+        // block, positions ascending) from `start`, without the old entry and with the
+        // corrupted record at its place: every entry outside the sublist fails the
+        // cull below anyway.
+        const uint32_t boff = v.bl_off[(size_t)tile * 8 + w];
+        const uint32_t blen = v.bl_off[(size_t)tile * 8 + w + 1] - boff;
+        const uint32_t* B = v.bl_pos + boff;
+        const uint32_t k0 = warp_lower_bound_u32(B, 0, blen, start);
+        bool has_kpp = false;
+        uint32_t kpp = 0, lins = 0;
+        if (has_old) {
+            kpp = warp_lower_bound_u32(B, 0, blen, pp);
+            has_kpp = kpp < blen && B[kpp] == pp;
+        }
+        if (has_new) {
+            // clean-list position before which the corrupted record goes (ins counts
+            // the list without the old entry; at ins == pp both readings coincide)
+            const uint32_t ins_c = (has_old && ins >= pp) ? ins + 1u : ins;
+            const uint32_t tins = warp_lower_bound_u32(B, 0, blen, ins_c);
+            lins = tins - k0 - ((has_kpp && kpp < tins) ? 1u : 0u);
+        }
+        const uint32_t Lb = (blen - k0) - (has_kpp ? 1u : 0u) + (has_new ? 1u : 0u);
+        const uint32_t nch = (Lb + 31u) / 32u;
+        (void)L;
         // source of this lane's entry in chunk c (NULL past the end)
         auto src_of = [&](uint32_t c) -> const BlendRec* {
-            const uint32_t m = start + c * 32u + (uint32_t)lane;
-            if (c >= nch || m >= L) return nullptr;
+            const uint32_t m = c * 32u + (uint32_t)lane;
+            if (c >= nch || m >= Lb) return nullptr;
             uint32_t ci = 0;
-            if (merged_entry(m, has_old, has_new, pp, ins, ci)) return &it->rec;
-            return v.recs + v.ids[s0 + ci];
+            if (merged_entry(m, has_kpp, has_new, kpp - k0, lins, ci)) return &it->rec;
+            return v.recs + v.ids[s0 + B[k0 + ci]];
         };
         auto issue = [&](uint32_t c, const BlendRec* src) {
             if (src) {
@@ -865,8 +908,8 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
             cp_async_wait_group<kWarpRing - 1>();   // this lane's copies of chunk c have landed
             __syncwarp();                            // and every other lane's
             const int slot = (int)(c % (uint32_t)kWarpRing);
-            const uint32_t base = start + c * 32u;
-            const int cnt = (int)min(32u, L - base);
+            const uint32_t base = c * 32u;
+            const int cnt = (int)min(32u, Lb - base);
             staged += (uint32_t)cnt;
             bool pass = false;
             if (lane < cnt) {
@@ -1152,27 +1195,85 @@ gs_status launch_stop_keys(const uint2* ranges, const uint32_t* tile_stop, const
     return GS_OK;
 }
 
-void fill_view_ptrs(void* host_dst, const BlendRec* recs, const uint32_t* ids, const uint32_t* dk, const uint2* ranges,
-                    const float* clean, const uint32_t* stop, const uint32_t* tile_stop,
-                    const unsigned long long* stop_key, const float4* ck,
-                    const uint32_t* ck_off, const uint32_t* ck_cnt, int W, int H) {
+void fill_view_ptrs(void* host_dst, const ViewState& vs) {
     ViewPtrs v;
-    v.recs = recs;
-    v.ids = ids;
-    v.dk = dk;
-    v.ranges = ranges;
-    v.clean = clean;
-    v.stop = stop;
-    v.tile_stop = tile_stop;
-    v.stop_key = stop_key;
-    v.ck = ck;
-    v.ck_off = ck_off;
-    v.ck_cnt = ck_cnt;
-    v.W = W;
-    v.H = H;
-    v.tiles_x = (W + kTile - 1) / kTile;
+    v.recs = vs.recs;
+    v.ids = vs.ids;
+    v.dk = vs.dk;
+    v.ranges = vs.ranges;
+    v.clean = vs.clean;
+    v.stop = vs.stop;
+    v.tile_stop = vs.tile_stop;
+    v.stop_key = vs.stop_key;
+    v.bl_off = vs.bl_off;
+    v.bl_pos = vs.bl_pos;
+    v.ck = vs.ck;
+    v.ck_off = vs.ck_off;
+    v.ck_cnt = vs.ck_cnt;
+    v.W = vs.cam.W;
+    v.H = vs.cam.H;
+    v.tiles_x = (vs.cam.W + kTile - 1) / kTile;
     v.pad = 0;
     memcpy(host_dst, &v, sizeof(v));
+}
+
+// ---------------------------------------------------------------------------
+// Per (tile, 8x4 block) sublists of the clean tile lists: the positions of the
+// entries whose box [mx - ex, mx + ex] x [my - ey, my + ey] meets the block's
+// pixel-centre box (the same comparisons as the dirty-tile cull, on a box that
+// contains every active-pixel box of the block, so an entry left out would be
+// culled there anyway).  One warp per tile; positions ascend in each sublist.
+// ---------------------------------------------------------------------------
+template <bool FILL>
+__global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
+                         const uint2* __restrict__ ranges, int ntiles, int tiles_x, uint32_t* __restrict__ counts,
+                         const uint32_t* __restrict__ off, uint32_t* __restrict__ pos) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = warp; t < ntiles; t += nwarps) {
+        const uint2 rg = ranges[t];
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        uint32_t base[8];
+#pragma unroll
+        for (int w = 0; w < 8; w++) base[w] = FILL ? off[(size_t)t * 8 + w] : 0u;
+        for (uint32_t j0 = 0; j0 < rg.y - rg.x; j0 += 32) {
+            const uint32_t j = j0 + (uint32_t)lane;
+            unsigned m8 = 0u;
+            if (j < rg.y - rg.x) {
+                const float4* r = reinterpret_cast<const float4*>(recs + ids[rg.x + j]);
+                const float4 a = __ldg(r), b = __ldg(r + 1);   // (mx, my, ca, cb), (cc, opac, ex, ey)
+#pragma unroll
+                for (int w = 0; w < 8; w++) {
+                    const float wx0 = (float)(tx * kTile + (w & 1) * 8) + 0.5f, wx1 = wx0 + 7.0f;
+                    const float wy0 = (float)(ty * kTile + (w >> 1) * 4) + 0.5f, wy1 = wy0 + 3.0f;
+                    const bool pass = !(a.x + b.z < wx0 || a.x - b.z > wx1 || a.y + b.w < wy0 || a.y - b.w > wy1);
+                    m8 |= pass ? (1u << w) : 0u;
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                const unsigned bw = __ballot_sync(0xffffffffu, (m8 >> w) & 1u);
+                if (FILL && ((m8 >> w) & 1u)) pos[base[w] + __popc(bw & ((1u << lane) - 1u))] = j;
+                base[w] += (uint32_t)__popc(bw);
+            }
+        }
+        if (!FILL && lane < 8) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) c = lane == w ? base[w] : c;
+            counts[(size_t)t * 8 + lane] = c;
+        }
+    }
+}
+
+gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int ntiles, int tiles_x,
+                        uint32_t* counts, const uint32_t* off, uint32_t* pos, cudaStream_t st) {
+    if (ntiles <= 0) return GS_OK;
+    const int blocks = std::max(1, std::min((ntiles + 7) / 8, num_sms() * 16));
+    if (pos) k_blists<true><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, nullptr, off, pos);
+    else k_blists<false><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, counts, nullptr, nullptr);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
 }
 
 gs_status launch_records_to_blend(const gs_record* in, uint64_t n, BlendRec* out, cudaStream_t st) {

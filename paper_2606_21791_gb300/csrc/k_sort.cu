@@ -538,6 +538,19 @@ gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, 
     return GS_OK;
 }
 
+// exclusive scan of n u32 values into out (n entries); total[0..2] (device) gets
+// the sum; scratch: div_up(n, kScanTile) + 1 u64
+gs_status launch_exclusive_scan(const uint32_t* in, uint64_t n, uint32_t* out, unsigned long long* scratch,
+                                unsigned long long* total, cudaStream_t st) {
+    const int nparts = (int)std::max<uint64_t>(div_up(n, kScanTile), 1);
+    k_scan_partials<<<nparts, kScanBlockT, 0, st>>>(in, n, scratch);
+    k_scan_partials_top<<<1, kScanT, 0, st>>>(scratch, nparts, total, ~0ull);
+    k_scan_apply<<<nparts, kScanBlockT, 0, st>>>(in, n, scratch, out);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+uint64_t scan_scratch_len(uint64_t n) { return std::max<uint64_t>(div_up(n, kScanTile), 1) + 1; }
+
 gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* offsets,
                                    const unsigned long long* total, cudaStream_t st) {
     k_ranges_to_offsets<<<(ntiles + 255) / 256, 256, 0, st>>>(ranges, ntiles, offsets);
