@@ -39,7 +39,7 @@ gs_status launch_stop_keys(const uint2* ranges, const uint32_t* tile_stop, const
                            int ntiles, unsigned long long* out, cudaStream_t st);
 void fill_view_ptrs(void* host_dst, const ViewState& vs);
 gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int ntiles, int tiles_x,
-                        uint32_t* counts, const uint32_t* off, uint32_t* pos, cudaStream_t st);
+                        uint32_t* counts, const uint32_t* off, uint32_t* pos, BlendRec* brec, cudaStream_t st);
 gs_status launch_exclusive_scan(const uint32_t* in, uint64_t n, uint32_t* out, unsigned long long* scratch,
                                 unsigned long long* total, cudaStream_t st);
 uint64_t scan_scratch_len(uint64_t n);
@@ -143,6 +143,7 @@ void free_views(gs_scene* s) {
         cudaFree(v.stop_key);
         cudaFree(v.bl_off);
         cudaFree(v.bl_pos);
+        cudaFree(v.bl_rec);
         cudaFree(v.ck);
         cudaFree(v.ck_off);
         cudaFree(v.ck_cnt);
@@ -597,7 +598,8 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
             GS_TRY(dmalloc((void**)&counts, sizeof(uint32_t) * nb));
             GS_TRY(dmalloc((void**)&scratch, sizeof(unsigned long long) * (scan_scratch_len(nb) + 3)));
             unsigned long long* total = scratch + scan_scratch_len(nb);
-            gs_status bs = launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, counts, nullptr, nullptr, st);
+            gs_status bs =
+                launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, counts, nullptr, nullptr, nullptr, st);
             if (bs == GS_OK) bs = launch_exclusive_scan(counts, nb, v.bl_off, scratch, total, st);
             unsigned long long tot = 0;
             if (bs == GS_OK && cudaMemcpyAsync(&tot, total, sizeof(tot), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -610,7 +612,9 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
             const uint32_t tot32 = (uint32_t)tot;
             GS_CUDA(cudaMemcpyAsync(v.bl_off + nb, &tot32, sizeof(tot32), cudaMemcpyHostToDevice, st));
             GS_TRY(dmalloc((void**)&v.bl_pos, sizeof(uint32_t) * std::max<uint64_t>(tot, 1)));
-            GS_TRY(launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, nullptr, v.bl_off, v.bl_pos, st));
+            GS_TRY(dmalloc((void**)&v.bl_rec, sizeof(BlendRec) * std::max<uint64_t>(tot, 1)));
+            GS_TRY(launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, nullptr, v.bl_off, v.bl_pos, v.bl_rec,
+                                 st));
             GS_CUDA(cudaStreamSynchronize(st));
         }
         fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v);

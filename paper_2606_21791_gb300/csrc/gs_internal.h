@@ -111,6 +111,7 @@ struct ViewPtrs {
     const unsigned long long* stop_key;   // (depth bits, id) of the list entry at tile_stop; ~0 if none
     const uint32_t* bl_off;      // per (tile, 8x4 block): start of its sublist in bl_pos (ntiles * 8 + 1)
     const uint32_t* bl_pos;      // positions (in the tile's list) of the entries whose box meets the block
+    const BlendRec* bl_rec;      // their records, same order
     const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
     const uint32_t* ck_off;      // first checkpoint of each tile
     const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
@@ -177,6 +178,7 @@ struct ViewState {
     unsigned long long* stop_key = nullptr;   // [ntiles] (depth bits << 32 | id) of the entry at tile_stop (~0: none)
     uint32_t* bl_off = nullptr;      // [ntiles * 8 + 1] start of each (tile, 8x4 block) sublist in bl_pos
     uint32_t* bl_pos = nullptr;      // list positions whose box meets the block, ascending per sublist
+    BlendRec* bl_rec = nullptr;      // the records of those entries, in the same order (streamed by the blend)
     float4* ck = nullptr;            // clean-blend checkpoints [total][256 pixels]
     uint32_t* ck_off = nullptr;      // [ntiles]
     uint32_t* ck_cnt = nullptr;      // [ntiles]

@@ -882,7 +882,7 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
             if (c >= nch || m >= Lb) return nullptr;
             uint32_t ci = 0;
             if (merged_entry(m, has_kpp, has_new, kpp - k0, lins, ci)) return &it->rec;
-            return v.recs + v.ids[s0 + B[k0 + ci]];
+            return v.bl_rec + boff + k0 + ci;   // the sublist's records are stored in order
         };
         auto issue = [&](uint32_t c, const BlendRec* src) {
             if (src) {
@@ -1207,6 +1207,7 @@ void fill_view_ptrs(void* host_dst, const ViewState& vs) {
     v.stop_key = vs.stop_key;
     v.bl_off = vs.bl_off;
     v.bl_pos = vs.bl_pos;
+    v.bl_rec = vs.bl_rec;
     v.ck = vs.ck;
     v.ck_off = vs.ck_off;
     v.ck_cnt = vs.ck_cnt;
@@ -1227,7 +1228,7 @@ void fill_view_ptrs(void* host_dst, const ViewState& vs) {
 template <bool FILL>
 __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
                          const uint2* __restrict__ ranges, int ntiles, int tiles_x, uint32_t* __restrict__ counts,
-                         const uint32_t* __restrict__ off, uint32_t* __restrict__ pos) {
+                         const uint32_t* __restrict__ off, uint32_t* __restrict__ pos, BlendRec* __restrict__ brec) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int t = warp; t < ntiles; t += nwarps) {
@@ -1239,8 +1240,10 @@ __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __re
         for (uint32_t j0 = 0; j0 < rg.y - rg.x; j0 += 32) {
             const uint32_t j = j0 + (uint32_t)lane;
             unsigned m8 = 0u;
+            uint32_t id = 0;
             if (j < rg.y - rg.x) {
-                const float4* r = reinterpret_cast<const float4*>(recs + ids[rg.x + j]);
+                id = ids[rg.x + j];
+                const float4* r = reinterpret_cast<const float4*>(recs + id);
                 const float4 a = __ldg(r), b = __ldg(r + 1);   // (mx, my, ca, cb), (cc, opac, ex, ey)
 #pragma unroll
                 for (int w = 0; w < 8; w++) {
@@ -1253,7 +1256,11 @@ __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __re
 #pragma unroll
             for (int w = 0; w < 8; w++) {
                 const unsigned bw = __ballot_sync(0xffffffffu, (m8 >> w) & 1u);
-                if (FILL && ((m8 >> w) & 1u)) pos[base[w] + __popc(bw & ((1u << lane) - 1u))] = j;
+                if (FILL && ((m8 >> w) & 1u)) {
+                    const uint32_t q = base[w] + __popc(bw & ((1u << lane) - 1u));
+                    pos[q] = j;
+                    brec[q] = recs[id];
+                }
                 base[w] += (uint32_t)__popc(bw);
             }
         }
@@ -1267,11 +1274,11 @@ __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __re
 }
 
 gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int ntiles, int tiles_x,
-                        uint32_t* counts, const uint32_t* off, uint32_t* pos, cudaStream_t st) {
+                        uint32_t* counts, const uint32_t* off, uint32_t* pos, BlendRec* brec, cudaStream_t st) {
     if (ntiles <= 0) return GS_OK;
     const int blocks = std::max(1, std::min((ntiles + 7) / 8, num_sms() * 16));
-    if (pos) k_blists<true><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, nullptr, off, pos);
-    else k_blists<false><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, counts, nullptr, nullptr);
+    if (pos) k_blists<true><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, nullptr, off, pos, brec);
+    else k_blists<false><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, counts, nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
