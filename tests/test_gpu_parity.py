@@ -566,3 +566,47 @@ def test_dirty_tile_ssim_equals_full_frame_ssim(G):
         assert np.abs(o - ssim[sample]).max() < 5e-5
     finally:
         G.gs_free_scene(h)
+
+
+def test_campaign_edge_cases(G):
+    """Empty batch; ragged views (not multiples of the tile) and an odd view count;
+    a batch split over launches (2049 variants with the 2048 cap); invalid upsets
+    (site, word or bit out of range) give the clean record; an ECC word index
+    beyond 64 is not a protected word."""
+    torch = _torch()
+    sc = S.make_scene(8000, 3, S.FP32, 81, layout="clusters")
+    cams = S.ring_cameras(3, 250, 130)
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        K = 3
+        out = G.device_bytes(24)
+        G.gs_inject_and_render(h, G.to_device(S.flips_at(np.array([0], np.uint32), 0, 0)), 0, 1, -1,
+                               S.GUARD_WORDS_DEFAULT, out)   # B = 0: nothing to do
+        torch.cuda.synchronize()
+        flips = S.flips_stratified(2049, sc.n, sc.nwords, S.FP32, 82)
+        G.gs_set_batch(h, 2048)
+        a = _campaign_gpu(G, h, flips, K)
+        G.gs_set_batch(h, 64)
+        b = _campaign_gpu(G, h, flips, K)
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert np.array_equal(a[f], b[f]), f
+        sample = np.arange(0, 2049, 97)
+        o, _, _ = O.campaign(sc.planes, S.FP32, 3, cams, flips[sample], nthreads=O.max_threads())
+        npx = 250 * 130 * 3
+        dp = np.abs(np.array([_psnr(x, npx) for x in a[sample]["sse"].ravel()]) -
+                    np.array([_psnr(x, npx) for x in o["sse"].ravel()]))
+        assert dp.max() <= PSNR_TOL
+        full = _campaign_gpu(G, h, flips[sample], K, full=True)
+        for f in ("sse", "maxabs", "footprint", "nonfinite"):
+            assert np.array_equal(full[f], a[sample][f]), f
+        bad = np.concatenate([S.flips_at(np.array([sc.n], np.uint32), 3, 31), S.flips_at(np.array([5], np.uint32), 59, 0),
+                              S.flips_at(np.array([5], np.uint32), 3, 32)])
+        r = _campaign_gpu(G, h, bad, K)
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert (r[f] == 0).all(), f
+        far = S.flips_at(np.array([5], np.uint32), 70, 0)   # word 70 >= 64: invalid, not protected
+        r = _campaign_gpu(G, h, far, K, guard=2, mask=(1 << 59) - 1)
+        assert (r["sse"] == 0).all()
+    finally:
+        G.gs_free_scene(h)
