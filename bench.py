@@ -347,6 +347,8 @@ def main():
     contam = contamination(G, S, h, scene, K_views, dev)
     # SSIM of every (variant, view) from the re-blended pixels
     ssim_line = ssim_campaign(G, S, h, d_flips, nflips, K_views, dev)
+    # stage split of the full render (preprocess / binning + radix sort / blend)
+    stages = render_stages(G, S, h, cams, flush, dev, pk, pk_kind)
 
     # roofline of the dominant kernel (dirty-tile blend): FP32-pipe bound
     clocks = clk.summary()
@@ -386,7 +388,9 @@ def main():
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,
         "mpix_s_effective": value * K_views * Wd * Hd / 1e6,
+        "mpix_s_blended": work["blocks_blended"] * 32 * world / t_total / 1e6,
         "plain_loop": plain,
+        "render_stages": stages,
         "contamination": contam,
         "ssim": ssim_line,
         "speedup_vs_plain_loop": value / plain["value"],
@@ -525,6 +529,59 @@ def ssim_campaign(G, S, h, d_flips, nflips, K_views, dev, count=1024):
                 "mean_ssim": float(v.mean()), "min_ssim": float(v.min()),
                 "frac_below_0.99": float((v < 0.99).mean())})
     return res
+
+
+def render_stages(G, S, h, cams, flush, dev, pk, pk_kind, reps=10):
+    """Stage split of one full render of view 0 (the pipeline the plain loop runs
+    per variant): CUDA events inside gs_render bracket the preprocess, the
+    binning with its radix sorts and the blend; medians over `reps` renders, L2
+    flushed before each.  Algorithmic bytes: the preprocess reads every word of
+    every primitive and writes its 48-B blend record, 8-B tile rect and 8-B
+    depth-sort pair; the tile lists are 8-B (tile, primitive) pairs written once
+    and read once.  The radix passes move 20 B per element (the histogram reads
+    the 4-B key, the scatter reads and writes key and value), the tile count and
+    emit read 20 B per primitive and write 8 B per pair, the range pass reads 4 B
+    per pair."""
+    import torch
+    cam = cams[:1]
+    W, H = int(cam[0]["width"]), int(cam[0]["height"])
+    img = torch.empty(H * W * 3, dtype=torch.float32, device=dev)
+    G.gs_time_kernels(h, True)
+    rows = []
+    for i in range(3 + reps):
+        flush.zero_()
+        if i == 3:
+            torch.cuda.nvtx.range_push("render_stages")
+        G.gs_render(h, cam, img)
+        if i >= 3:
+            rows.append(G.gs_read_render_ms(h))
+    torch.cuda.nvtx.range_pop()
+    G.gs_time_kernels(h, False)
+    pre_ms, sort_ms, blend_ms = (sorted(r[0][j] for r in rows)[len(rows) // 2] for j in range(3))
+    n, pairs, passes_depth, passes_pairs = rows[-1][1]
+    _, _, fmt, nwords = G.gs_scene_info(h)
+    wbytes = 4 if fmt == S.FP32 else 2
+    pre_bytes = n * (nwords * wbytes + 64)
+    sort_alg = pairs * 16
+    sort_moved = 20 * (n * passes_depth + pairs * passes_pairs) + 20 * n + 12 * pairs
+    hbm = pk.get("hbm_gbs")
+    gbs = lambda b, ms: b / (ms * 1e-3) / 1e9
+    frame = pre_ms + sort_ms + blend_ms
+    return {
+        "what": f"full render of one {W}x{H} view of the benchmark scene, stage medians of {reps} (CUDA events)",
+        "frame_ms": frame,
+        "preprocess": {"ms": pre_ms, "share": pre_ms / frame, "bytes": pre_bytes,
+                       "gbs": gbs(pre_bytes, pre_ms), "frac_of_hbm_peak": gbs(pre_bytes, pre_ms) / hbm,
+                       "bytes_per_primitive": nwords * wbytes + 64},
+        "bin_sort": {"ms": sort_ms, "share": sort_ms / frame, "primitives": n, "pairs": pairs,
+                     "radix_passes": {"depth_keys": passes_depth, "pair_tile_keys": passes_pairs},
+                     "algorithmic_bytes": sort_alg, "gbs_algorithmic": gbs(sort_alg, sort_ms),
+                     "bytes_moved_by_passes": sort_moved, "gbs_passes": gbs(sort_moved, sort_ms),
+                     "frac_of_hbm_peak_passes": gbs(sort_moved, sort_ms) / hbm},
+        "blend": {"ms": blend_ms, "share": blend_ms / frame, "mpix_s": W * H / (blend_ms * 1e-3) / 1e6,
+                  "pairs_per_us": pairs / (blend_ms * 1e3)},
+        "peak": {"hbm_gbs": hbm, "source": pk_kind},
+    }
 
 
 def _pct(xs, q):

@@ -258,6 +258,17 @@ GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
  * (host array of 2 floats).  GS_ERR_STATE while timing is off. */
 GS_API gs_status gs_time_kernels(gs_scene* scene, int enable);
 GS_API gs_status gs_read_kernel_ms(gs_scene* scene, float* ms);
+/* Stage times of the full render (the 3DGS forward pass of Sec. 3: preprocess,
+ * tile binning with the radix sort, front-to-back blend) while kernel timing is
+ * on: CUDA events bracket the stages of every view of gs_render.
+ * gs_read_render_ms waits for the last view of the last gs_render call and
+ * writes, into host arrays, ms[0] = preprocess, ms[1] = depth sort + tile
+ * binning + pair sort + tile ranges, ms[2] = blend (3 floats), and counts[0] =
+ * primitives, counts[1] = (tile, primitive) pairs of that view, counts[2] =
+ * radix passes over the 32-bit depth keys, counts[3] = radix passes over the
+ * pairs' tile keys (4 uint64).  GS_ERR_STATE while timing is off or before the
+ * first gs_render after it was switched on. */
+GS_API gs_status gs_read_render_ms(gs_scene* scene, float* ms, uint64_t* counts);
 /* Variants per dirty-tile launch (0 = largest allowed, min(2048, 8192 / K)). */
 GS_API gs_status gs_set_batch(gs_scene* scene, int batch);
 /* Autotuner: times the campaign over dev_flips[0, count) at batch sizes

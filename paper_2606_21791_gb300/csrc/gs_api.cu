@@ -92,19 +92,25 @@ bool valid_camera(const gs_camera& c) {
 
 // Full render pipeline of one view on scratch `w`: preprocess, depth sort,
 // pair emission, tile sort, ranges.  Leaves records in w.recs, lists in *ids.
-gs_status render_lists(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, cudaStream_t st) {
+// ev (optional, 3 events): recorded before the preprocess, after it and after the tile lists.
+gs_status render_lists(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, cudaStream_t st,
+                       cudaEvent_t* ev = nullptr) {
+    if (ev) GS_CUDA(cudaEventRecord(ev[0], st));
     GS_TRY(launch_preprocess(s, cam, w.recs, w.rects, w.dkey[0], w.dval[0], nullptr, st));
-    return build_tile_lists(w, s->n, cam.tiles_x, cam.tiles_y, ids, st);
+    if (ev) GS_CUDA(cudaEventRecord(ev[1], st));
+    GS_TRY(build_tile_lists(w, s->n, cam.tiles_x, cam.tiles_y, ids, st));
+    if (ev) GS_CUDA(cudaEventRecord(ev[2], st));
+    return GS_OK;
 }
 
 // Like render_lists but grows the pair capacity until the lists fit (host sync).
 gs_status render_lists_sized(gs_scene* s, RenderWork& w, const DevCamera& cam, uint32_t** ids, uint64_t* npairs,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaEvent_t* ev = nullptr) {
     int ntiles = cam.tiles_x * cam.tiles_y;
     uint64_t cap = std::max<uint64_t>(w.cap_pairs, std::max<uint64_t>(s->n * 2, 1024));
     for (int attempt = 0; attempt < 4; attempt++) {
         GS_TRY(alloc_render_work(w, s->n, cap, ntiles));
-        GS_TRY(render_lists(s, w, cam, ids, st));
+        GS_TRY(render_lists(s, w, cam, ids, st, ev));
         GS_CUDA(cudaMemcpyAsync(w.host_total, w.total, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         GS_CUDA(cudaStreamSynchronize(st));
         if (!w.host_total[1]) {
@@ -410,6 +416,8 @@ gs_status gs_free_scene(gs_scene* s) {
     if (s->ev_k0) cudaEventDestroy(s->ev_k0);
     if (s->ev_kp) cudaEventDestroy(s->ev_kp);
     if (s->ev_k1) cudaEventDestroy(s->ev_k1);
+    for (auto& e : s->ev_r)
+        if (e) cudaEventDestroy(e);
     delete s;
     return GS_OK;
 }
@@ -493,16 +501,21 @@ gs_status gs_guard(gs_scene* s, int mode, uint64_t word_mask, uint64_t* dev_clam
 gs_status gs_render(gs_scene* s, const gs_camera* host_cams, int K, float* dev_rgb, void* stream) {
     if (!s || !host_cams || !dev_rgb || K < 1) return set_error(GS_ERR_ARG, "bad gs_render arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t* ev = s->ev_r[0] ? s->ev_r : nullptr;
+    s->render_timed = false;
     size_t off = 0;
     for (int k = 0; k < K; k++) {
         if (!valid_camera(host_cams[k])) return set_error(GS_ERR_ARG, "invalid camera");
         DevCamera cam = make_dev_camera(host_cams[k]);
         uint32_t* ids = nullptr;
         uint64_t np = 0;
-        GS_TRY(render_lists_sized(s, s->work, cam, &ids, &np, st));
+        GS_TRY(render_lists_sized(s, s->work, cam, &ids, &np, st, ev));
         GS_TRY(launch_blend_image(s->work.recs, ids, s->work.ranges, cam.W, cam.H, dev_rgb + off, st));
+        if (ev) GS_CUDA(cudaEventRecord(ev[3], st));
+        s->render_pairs = np;
         off += (size_t)cam.W * cam.H * 3;
     }
+    s->render_timed = ev != nullptr;
     return GS_OK;
 }
 
@@ -888,13 +901,19 @@ gs_status gs_time_kernels(gs_scene* s, int enable) {
         GS_CUDA(cudaEventCreate(&s->ev_k0));
         GS_CUDA(cudaEventCreate(&s->ev_kp));
         GS_CUDA(cudaEventCreate(&s->ev_k1));
+        for (auto& e : s->ev_r) GS_CUDA(cudaEventCreate(&e));
     }
     if (!enable && s->ev_k0) {
         cudaEventDestroy(s->ev_k0);
         cudaEventDestroy(s->ev_kp);
         cudaEventDestroy(s->ev_k1);
         s->ev_k0 = s->ev_kp = s->ev_k1 = nullptr;
+        for (auto& e : s->ev_r) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
     }
+    s->render_timed = false;
     return GS_OK;
 }
 
@@ -904,6 +923,19 @@ gs_status gs_read_kernel_ms(gs_scene* s, float* ms) {
     GS_CUDA(cudaEventSynchronize(s->ev_k1));
     GS_CUDA(cudaEventElapsedTime(&ms[0], s->ev_k0, s->ev_kp));
     GS_CUDA(cudaEventElapsedTime(&ms[1], s->ev_kp, s->ev_k1));
+    return GS_OK;
+}
+
+gs_status gs_read_render_ms(gs_scene* s, float* ms, uint64_t* counts) {
+    if (!s || !ms || !counts) return set_error(GS_ERR_ARG, "NULL argument");
+    if (!s->ev_r[0]) return set_error(GS_ERR_STATE, "kernel timing is off");
+    if (!s->render_timed) return set_error(GS_ERR_STATE, "no gs_render since kernel timing was switched on");
+    GS_CUDA(cudaEventSynchronize(s->ev_r[3]));
+    for (int i = 0; i < 3; i++) GS_CUDA(cudaEventElapsedTime(&ms[i], s->ev_r[i], s->ev_r[i + 1]));
+    counts[0] = s->n;
+    counts[1] = s->render_pairs;
+    counts[2] = (uint64_t)s->work.passes[0];
+    counts[3] = (uint64_t)s->work.passes[1];
     return GS_OK;
 }
 

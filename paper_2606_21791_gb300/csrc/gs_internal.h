@@ -206,6 +206,7 @@ struct RenderWork {
     uint2* ranges = nullptr;
     unsigned long long* total = nullptr;        // [0] pair count, [1] overflow flag
     unsigned long long* host_total = nullptr;   // pinned mirror
+    int passes[2] = {0, 0};                     // radix passes of the last build: depth keys, pair tile keys
 };
 
 struct GraphEntry {
@@ -267,6 +268,10 @@ struct gs_scene {
     cudaEvent_t ev_k0 = nullptr;            // timing on: before the plan kernel of the last batch,
     cudaEvent_t ev_kp = nullptr;            // between the plan and the blend kernel,
     cudaEvent_t ev_k1 = nullptr;            // after the blend kernel
+    cudaEvent_t ev_r[4] = {};               // timing on, gs_render: before preprocess, after it, after the tile
+                                            // lists, after the blend (last view of the last call)
+    bool render_timed = false;              // ev_r holds a complete record
+    uint64_t render_pairs = 0;              // tile pairs of that view
     std::vector<gs::GraphEntry> graphs;
 };
 

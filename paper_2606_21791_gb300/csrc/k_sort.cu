@@ -531,6 +531,8 @@ gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, 
     while ((1 << tbits) < ntiles) tbits++;
     int pcur = 0;
     GS_TRY(radix_sort(w.pkey, w.pval, w.total, w.cap_pairs, tbits, w.hist, w.hpart, pcur, st));
+    w.passes[0] = 4;                  // 32-bit depth keys, 8 bits a pass
+    w.passes[1] = (tbits + 7) / 8;
     GS_CUDA(cudaMemsetAsync(w.ranges, 0, sizeof(uint2) * ntiles, st));
     k_ranges<<<num_sms() * 8, 256, 0, st>>>(w.pkey[pcur], w.total, w.cap_pairs, w.ranges);
     GS_CUDA(cudaGetLastError());

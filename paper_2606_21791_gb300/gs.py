@@ -67,6 +67,7 @@ SIGNATURES = {
     "gs_count_work": (_i32, [_vp, _i32]),
     "gs_time_kernels": (_i32, [_vp, _i32]),
     "gs_read_kernel_ms": (_i32, [_vp, _vp]),
+    "gs_read_render_ms": (_i32, [_vp, _vp, _vp]),
     "gs_read_work": (_i32, [_vp, _vp]),
     "gs_autotune": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp]),
     "gs_preprocess": (_i32, [_vp, _vp, _vp, _vp]),
@@ -307,6 +308,16 @@ def gs_read_kernel_ms(scene):
     ms = (C.c_float * 2)()
     _check(load_library().gs_read_kernel_ms(scene, ms), "gs_read_kernel_ms")
     return float(ms[0]), float(ms[1])
+
+
+def gs_read_render_ms(scene):
+    """Stage times of the last view of the last gs_render (kernel timing on):
+    ((preprocess ms, binning + sort ms, blend ms),
+     (primitives, tile pairs, depth-key radix passes, pair radix passes))."""
+    ms = (C.c_float * 3)()
+    counts = (C.c_uint64 * 4)()
+    _check(load_library().gs_read_render_ms(scene, ms, counts), "gs_read_render_ms")
+    return tuple(float(x) for x in ms), tuple(int(x) for x in counts)
 
 
 def gs_set_batch(scene, batch: int):

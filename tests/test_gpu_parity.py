@@ -223,6 +223,40 @@ def test_bin_tiles_bit_exact(G, case):
     assert e.value.status == G.GS_ERR_CAPACITY
 
 
+def test_render_stage_times(G):
+    """Stage timing of the full render: the counts it reports are the oracle's
+    (pairs of the last view's tile lists; 4 depth-key passes and ceil(tile bits
+    / 8) pair passes of the 8-bit radix sort), the times are positive, and the
+    image is the same with timing on."""
+    sc = S.make_scene(30000, 3, S.FP32, 62, layout="clusters")
+    cams = S.ring_cameras(2, 480, 304)
+    h = _load(G, sc)
+    try:
+        plain = _render_gpu(G, h, cams)
+        with pytest.raises(G.GsError) as e:
+            G.gs_read_render_ms(h)
+        assert e.value.status == G.GS_ERR_STATE
+        G.gs_time_kernels(h, True)
+        with pytest.raises(G.GsError) as e:
+            G.gs_read_render_ms(h)
+        assert e.value.status == G.GS_ERR_STATE
+        timed = _render_gpu(G, h, cams)
+        ms, counts = G.gs_read_render_ms(h)
+        for a, b in zip(plain, timed):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+        cam = cams[-1]
+        W, H = int(cam["width"]), int(cam["height"])
+        _, ids_o = O.bin_tiles(O.preprocess(sc.planes, S.FP32, 3, cam), W, H)
+        ntiles = -(-W // 16) * -(-H // 16)
+        assert counts == (sc.n, len(ids_o), 4, -(-int(math.ceil(math.log2(ntiles))) // 8))
+        assert all(t > 0 for t in ms)
+        G.gs_time_kernels(h, False)
+        with pytest.raises(G.GsError):
+            G.gs_read_render_ms(h)
+    finally:
+        G.gs_free_scene(h)
+
+
 # ---------------------------------------------------------------------------
 # (d) blend from the same records and lists; (e) compare from the same images
 # ---------------------------------------------------------------------------
