@@ -241,10 +241,19 @@ __global__ __launch_bounds__(kScanBlockT) void k_scan_apply(const uint32_t* in, 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t base = (uint64_t)blockIdx.x * kScanTile;
     if (threadIdx.x == 0) carry = (uint32_t)part[blockIdx.x];
+    // all loads first (kScanItems in flight per thread): the barriers of the
+    // rounds below would otherwise expose one load latency per round
+    uint32_t vv[kScanItems];
+#pragma unroll
+    for (int r = 0; r < kScanItems; r++) {
+        const uint64_t i = base + (uint64_t)r * kScanBlockT + threadIdx.x;
+        vv[r] = i < n ? in[i] : 0u;
+    }
     __syncthreads();
+#pragma unroll
     for (int r = 0; r < kScanItems; r++) {
         uint64_t i = base + (uint64_t)r * kScanBlockT + threadIdx.x;
-        uint32_t v = i < n ? in[i] : 0u;
+        uint32_t v = vv[r];
         uint32_t x = v;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
