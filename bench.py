@@ -4,12 +4,14 @@ Default workload (one GPU): 2,000,000 Gaussians (4 clusters, SH degree 3, fp32
 storage), four 1600x1040 views on a ring, 20,000 single-bit upsets with 70% on
 bits 24-31 of log-scale and opacity.  A step is one launch of the batched
 dirty-tile engine over B variants (B picked by the library's autotuner from
-{8,16,32,64}), replayed as a CUDA graph: inject + guard-ready preprocess of the
-flipped primitives, dirty-tile re-blend fused with the comparison against the
-clean frames, finalisation of the per-(variant, view) records.  Reported beside
-it: the plain one-variant-per-launch full-render loop on the same flips, the
-end-to-end rate through host buffers, the support-guard clamp bandwidth on a
-66,000,000-Gaussian scene, and the CPU oracle on a bounded sample.
+{8, 16, ..., 2048}), replayed as a CUDA graph: inject + guard-ready preprocess
+of the flipped primitives, the two plan kernels, dirty-tile re-blend fused with
+the comparison against the clean frames, finalisation of the per-(variant,
+view) records.  Reported beside it: the plain one-variant-per-launch
+full-render loop on the same flips and the stage split of a full render, the
+end-to-end rate through host buffers, contamination and SSIM campaigns, the
+support-guard clamp bandwidth on a 66,000,000-Gaussian scene, Table 2 and the
+scaling law, the serving loop, and the CPU oracle on bounded samples.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -140,10 +142,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (rank 0, N = 1)
 # ---------------------------------------------------------------------------
-def cpu_baseline(scene, cams, flips, crop=None, variants=None):
+def cpu_baseline(scene, cams, flips, crop=None, variants=None, keep=None):
     """Times the oracle as it stands on the host cores: `variants` upsets (one per
     core), each rendered in view 0 (optionally a centred crop of it) and compared
-    with the clean view; extrapolated to injections/s over all views."""
+    with the clean view; extrapolated to injections/s over all views.  `keep`
+    (a dict) receives the clean view and its render time."""
     import oracle as O
     from paper_2606_21791_gb300 import synth as S
     cores = O.max_threads()
@@ -159,6 +162,8 @@ def cpu_baseline(scene, cams, flips, crop=None, variants=None):
     t0 = time.perf_counter()
     clean = [O.render(scene.planes, scene.fmt, scene.sh_degree, cam[0])]
     t_clean = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(cam=cam, clean=clean, t_clean=t_clean)
     t0 = time.perf_counter()
     O.campaign(scene.planes, scene.fmt, scene.sh_degree, cam, flips[:nvar], clean_imgs=clean, nthreads=cores)
     t = time.perf_counter() - t0
@@ -168,6 +173,63 @@ def cpu_baseline(scene, cams, flips, crop=None, variants=None):
             "sample": f"{nvar} upsets x 1 of {len(cams)} views ({cam['width'][0]}x{cam['height'][0]} px), "
                       f"{t:.1f} s on {cores} threads (OpenMP over upsets); extrapolated linearly in pixels "
                       f"to all views; clean render {t_clean:.1f} s untimed"}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_timing(scene3, cams3, flips3, c3_all, c3_view0):
+    """Per-injection cost of the oracle, as it stands, single-threaded and with
+    OpenMP over upsets on all host cores, on the three campaign workloads: the
+    5,000-Gaussian 256x256 one (bounded samples of its 200 upsets), the
+    134,826-Gaussian 800x800 stratified one (samples of 100 upsets) and the
+    benchmark's (one upset single-threaded in view 0, extrapolated to 4 views;
+    the all-cores figure is `cpu_baseline`, whose clean view 0 `c3_view0` holds).
+    Clean frames are rendered first and timed on their own.  Context for the
+    GPU numbers, never a target."""
+    import oracle as O
+    from paper_2606_21791_gb300 import synth as S
+    cores = O.max_threads()
+
+    def clean_of(sc, cams):
+        t0 = time.perf_counter()
+        imgs = [O.render(sc.planes, sc.fmt, sc.sh_degree, c) for c in cams]
+        return imgs, time.perf_counter() - t0
+
+    def per_inj(sc, cams, fl, clean, nthreads):
+        t0 = time.perf_counter()
+        O.campaign(sc.planes, sc.fmt, sc.sh_degree, cams, fl, clean_imgs=clean, nthreads=nthreads)
+        return (time.perf_counter() - t0) / len(fl)
+
+    out = {"cores": cores, "cpu": cpu_model(), "unit": "s per injection (all views of the workload)"}
+    sc, cams, fl = S.tiny_workload()
+    clean, tc = clean_of(sc, cams)
+    out["c1"] = {"workload": "5,000 Gaussians (SH 0, fp32), 256x256, 1 view", "clean_frame_s": tc,
+                 "single_thread": per_inj(sc, cams, fl[:20], clean, 1), "all_cores": per_inj(sc, cams, fl, clean, cores),
+                 "sample": "20 of the 200 upsets single-threaded, all 200 on all cores"}
+    sc, cams, fl = S.batching_workload(S.FP32)
+    clean, tc = clean_of(sc, cams)
+    nall = max(cores, 16)
+    out["c2"] = {"workload": "134,826 Gaussians (4 clusters, SH 3, fp32), 800x800, 1 view", "clean_frame_s": tc,
+                 "single_thread": per_inj(sc, cams, fl[:2], clean, 1),
+                 "all_cores": per_inj(sc, cams, fl[:nall], clean, cores),
+                 "sample": f"2 of 100 upsets single-threaded, {nall} on all cores"}
+    cam0, clean, tc = c3_view0["cam"], c3_view0["clean"], c3_view0["t_clean"]
+    single = per_inj(scene3, cam0, flips3[:1], clean, 1) * len(cams3)
+    out["c3"] = {"workload": "2M Gaussians (4 clusters, SH 3, fp32), 4 views 1600x1040",
+                 "clean_frame_s": tc, "single_thread": single, "all_cores": 1.0 / c3_all,
+                 "sample": "1 upset in view 0 single-threaded, extrapolated to 4 views; all cores: cpu_baseline",
+                 "campaign_of_20000_single_thread_days": single * 20000 / 86400.0}
+    return out
 
 
 def run_reference(args):
@@ -415,7 +477,12 @@ def main():
                                         "storm_guard_off": st["guard_off"]["p99_ms"],
                                         "poisson_80pct": line["serving"]["poisson"][1]["p99_ms"]}
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(scene, cams, flips)
+        view0 = {}
+        line["cpu_baseline"] = cpu_baseline(scene, cams, flips, keep=view0)
+        try:
+            line["oracle_timing"] = oracle_timing(scene, cams, flips, line["cpu_baseline"]["value"], view0)
+        except Exception as e:   # context only: report the failure, keep the measured line
+            line["oracle_timing"] = {"error": repr(e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
