@@ -149,6 +149,14 @@ GS_API gs_status gs_apply_flips(gs_scene* scene, const gs_flip* dev_flips, int64
 GS_API gs_status gs_field_box(gs_scene* scene, uint32_t* host_lo, uint32_t* host_hi);
 GS_API gs_status gs_set_prim_box(gs_scene* scene, const void* lo, const void* hi, int src_on_device, int nbox_words);
 GS_API gs_status gs_guard(gs_scene* scene, int mode, uint64_t word_mask, uint64_t* dev_clamps, void* stream);
+/* gs_guard with the optional bitmap of clamped words: dev_bitmap (device,
+ * caller-owned, nwords * ceil(n / 32) uint32) is overwritten so that bit
+ * (i % 32) of dev_bitmap[w * ceil(n / 32) + i / 32] is set iff the guard clamps
+ * word w of primitive i (rows of unguarded words and the bits past n are 0).
+ * The decisions are those of the clamp, taken by one extra read pass over the
+ * guarded planes before it; popcount(bitmap) equals the clamps added. */
+GS_API gs_status gs_guard_bitmap(gs_scene* scene, int mode, uint64_t word_mask, uint64_t* dev_clamps,
+                                 uint32_t* dev_bitmap, void* stream);
 
 /* ---------------------------------------------------------------------------
  * (b)-(d) Forward render of the scene as it is now (3DGS forward pass: EWA

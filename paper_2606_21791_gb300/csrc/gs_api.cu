@@ -498,6 +498,16 @@ gs_status gs_guard(gs_scene* s, int mode, uint64_t word_mask, uint64_t* dev_clam
     return launch_guard(s, mode, word_mask, (unsigned long long*)dev_clamps, (cudaStream_t)stream);
 }
 
+gs_status gs_guard_bitmap(gs_scene* s, int mode, uint64_t word_mask, uint64_t* dev_clamps, uint32_t* dev_bitmap,
+                          void* stream) {
+    if (!s) return set_error(GS_ERR_ARG, "scene is NULL");
+    if (mode != GS_GUARD_FIELD && mode != GS_GUARD_PRIM) return set_error(GS_ERR_ARG, "mode must be FIELD or PRIM");
+    if (!dev_bitmap && s->n > 0) return set_error(GS_ERR_ARG, "dev_bitmap is NULL");
+    const cudaStream_t st = (cudaStream_t)stream;
+    GS_TRY(launch_guard_mark(s, mode, word_mask, dev_bitmap, st));   // the decisions, on the words before the clamp
+    return launch_guard(s, mode, word_mask, (unsigned long long*)dev_clamps, st);
+}
+
 gs_status gs_render(gs_scene* s, const gs_camera* host_cams, int K, float* dev_rgb, void* stream) {
     if (!s || !host_cams || !dev_rgb || K < 1) return set_error(GS_ERR_ARG, "bad gs_render arguments");
     cudaStream_t st = (cudaStream_t)stream;

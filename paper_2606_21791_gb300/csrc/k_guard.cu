@@ -229,6 +229,44 @@ __global__ __launch_bounds__(kGuardThreads) void k_guard(void* __restrict__ plan
     }
 }
 
+// Clamped-word bitmap, an optional output of the guard: bit (i % 32) of
+// bitmap[w * words32 + i / 32] is set when the guard clamps word w of primitive
+// i -- the decision of k_guard (value outside [lo, hi], NaN included), taken
+// on the words before the clamp, so this runs before k_guard.  One thread per
+// (primitive, guarded plane); a warp covers 32 consecutive primitives, so lane
+// 0 writes each bitmap word whole.  The loop bound is uniform in a block.
+template <int FMT, bool PRIM>
+__global__ __launch_bounds__(kGuardThreads) void k_guard_mark(const void* __restrict__ planes,
+                                                              const void* __restrict__ plo,
+                                                              const void* __restrict__ phi, uint64_t n, GuardParams gp,
+                                                              uint32_t* __restrict__ bitmap, uint64_t words32) {
+    using W = typename std::conditional<FMT == GS_FP32, uint32_t, uint16_t>::type;
+    const int p = blockIdx.y;
+    const int w = gp.word[p];
+    const W* base = (const W*)planes + (uint64_t)w * n;
+    const W* lbase = PRIM ? (const W*)plo + (uint64_t)w * n : nullptr;
+    const W* hbase = PRIM ? (const W*)phi + (uint64_t)w * n : nullptr;
+    auto value = [](uint32_t b) -> float {
+        if (FMT == GS_FP32) return __uint_as_float(b);
+        if (FMT == GS_FP16) return __half2float(__ushort_as_half((unsigned short)b));
+        return __uint_as_float(b << 16);
+    };
+    const uint64_t span = words32 * 32u;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * kGuardThreads; i0 < span; i0 += (uint64_t)gridDim.x * kGuardThreads) {
+        const uint64_t i = i0 + threadIdx.x;
+        bool hit = false;
+        if (i < n) {
+            const float x = value((uint32_t)base[i]);
+            const float lo = PRIM ? value((uint32_t)lbase[i]) : gp.lo[p];
+            const float hi = PRIM ? value((uint32_t)hbase[i]) : gp.hi[p];
+            hit = !(x >= lo && x <= hi);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const uint64_t word = i >> 5;   // lane 0: i is a multiple of 32
+        if ((threadIdx.x & 31) == 0 && word < words32) bitmap[(uint64_t)w * words32 + word] = m;
+    }
+}
+
 }  // namespace
 
 int num_sms() {
@@ -301,8 +339,8 @@ float host_word_value(uint32_t bits, int fmt) {
     return __half2float(__half(r));
 }
 
-gs_status launch_guard(gs_scene* s, int mode, uint64_t mask, unsigned long long* dev_clamps, cudaStream_t st) {
-    GuardParams gp;
+// the guarded planes of `mask` and their FIELD boxes
+static gs_status guard_params(const gs_scene* s, int mode, uint64_t mask, GuardParams& gp) {
     memset(&gp, 0, sizeof(gp));
     for (int w = 0; w < s->nwords; w++) {
         if (!((mask >> w) & 1ull)) continue;
@@ -315,6 +353,39 @@ gs_status launch_guard(gs_scene* s, int mode, uint64_t mask, unsigned long long*
         gp.lo[p] = host_word_value(s->box_lo[w], s->fmt);
         gp.hi[p] = host_word_value(s->box_hi[w], s->fmt);
     }
+    if (mode == GS_GUARD_PRIM && gp.nplanes > 0 && s->n > 0 && (!s->pbox_lo || !s->pbox_hi))
+        return set_error(GS_ERR_STATE, "gs_guard: no per-primitive box set");
+    return GS_OK;
+}
+
+gs_status launch_guard_mark(gs_scene* s, int mode, uint64_t mask, uint32_t* bitmap, cudaStream_t st) {
+    GuardParams gp;
+    GS_TRY(guard_params(s, mode, mask, gp));
+    const uint64_t words32 = div_up(s->n, 32);
+    if (words32 == 0) return GS_OK;
+    GS_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)s->nwords * (size_t)words32, st));
+    if (gp.nplanes == 0) return GS_OK;
+    const uint64_t want = (uint64_t)num_sms() * 16 / (uint64_t)gp.nplanes + 1;
+    const uint64_t bx = std::max<uint64_t>(1, std::min<uint64_t>(div_up(words32 * 32, kGuardThreads), want));
+    dim3 grid((unsigned)bx, gp.nplanes);
+    const bool prim = mode == GS_GUARD_PRIM;
+#define GS_MARK_LAUNCH(F, P) \
+    k_guard_mark<F, P><<<grid, kGuardThreads, 0, st>>>(s->planes, s->pbox_lo, s->pbox_hi, s->n, gp, bitmap, words32)
+    if (s->fmt == GS_FP32) {
+        if (prim) GS_MARK_LAUNCH(GS_FP32, true); else GS_MARK_LAUNCH(GS_FP32, false);
+    } else if (s->fmt == GS_FP16) {
+        if (prim) GS_MARK_LAUNCH(GS_FP16, true); else GS_MARK_LAUNCH(GS_FP16, false);
+    } else {
+        if (prim) GS_MARK_LAUNCH(GS_BF16, true); else GS_MARK_LAUNCH(GS_BF16, false);
+    }
+#undef GS_MARK_LAUNCH
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status launch_guard(gs_scene* s, int mode, uint64_t mask, unsigned long long* dev_clamps, cudaStream_t st) {
+    GuardParams gp;
+    GS_TRY(guard_params(s, mode, mask, gp));
     if (gp.nplanes == 0 || s->n == 0) return GS_OK;
     // enough blocks for ~2 waves of 8 resident blocks per SM, spread over the planes
     uint64_t vec_per_plane = div_up(s->n, s->fmt == GS_FP32 ? 4 : 8);
@@ -323,7 +394,6 @@ gs_status launch_guard(gs_scene* s, int mode, uint64_t mask, unsigned long long*
     if (bx < 1) bx = 1;
     dim3 grid((unsigned)bx, gp.nplanes);
     bool prim = mode == GS_GUARD_PRIM;
-    if (prim && (!s->pbox_lo || !s->pbox_hi)) return set_error(GS_ERR_STATE, "gs_guard: no per-primitive box set");
 #define GS_GUARD_LAUNCH(F, P) \
     k_guard<F, P><<<grid, kGuardThreads, 0, st>>>(s->planes, s->pbox_lo, s->pbox_hi, s->n, gp, dev_clamps)
     if (s->fmt == GS_FP32) {

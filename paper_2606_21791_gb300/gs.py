@@ -52,6 +52,7 @@ SIGNATURES = {
     "gs_field_box": (_i32, [_vp, _vp, _vp]),
     "gs_set_prim_box": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "gs_guard": (_i32, [_vp, _i32, _u64, _vp, _vp]),
+    "gs_guard_bitmap": (_i32, [_vp, _i32, _u64, _vp, _vp, _vp]),
     "gs_render": (_i32, [_vp, _vp, _i32, _vp, _vp]),
     "gs_compare": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "gs_compare_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
@@ -222,6 +223,12 @@ def gs_set_prim_box(scene, lo, hi, nbox_words: int):
 
 def gs_guard(scene, mode: int, word_mask: int, dev_clamps=None, stream=None):
     _check(load_library().gs_guard(scene, mode, word_mask, _ptr(dev_clamps), _stream(stream)), "gs_guard")
+
+
+def gs_guard_bitmap(scene, mode: int, word_mask: int, dev_bitmap, dev_clamps=None, stream=None):
+    """gs_guard plus the bitmap of clamped words (device uint32[nwords * ceil(n / 32)])."""
+    _check(load_library().gs_guard_bitmap(scene, mode, word_mask, _ptr(dev_clamps), _ptr(dev_bitmap),
+                                          _stream(stream)), "gs_guard_bitmap")
 
 
 def gs_render(scene, cams, dev_rgb, stream=None):

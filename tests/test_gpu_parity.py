@@ -148,6 +148,50 @@ def test_guard_bit_exact(G, fmt, mode, mask):
         G.gs_free_scene(h)
 
 
+@pytest.mark.parametrize("fmt", [S.FP32, S.FP16, S.BF16])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_guard_bitmap(G, fmt, mode):
+    """The guard's optional bitmap of clamped words is exactly the set of words
+    the oracle's guard changes (a clamp always changes the word: the endpoint
+    differs from an out-of-box or NaN value), with zero rows for the unguarded
+    words and zero bits past n; its popcount is the clamp count, and the
+    guarded model is the oracle's."""
+    torch = _torch()
+    n = 20_011   # not a multiple of 32
+    clean = S.make_scene(n, 3, fmt, 63, layout="clusters")
+    mask = S.GUARD_WORDS_DEFAULT
+    if mode == 0:
+        lo, hi = O.field_box(clean.planes, fmt)
+    else:
+        lo, hi = S.prim_boxes(clean, 14, 64)
+    rng = np.random.default_rng(65)
+    fl = S.flips_at(rng.integers(0, n, size=3000), 0, 0)
+    fl["word"] = rng.integers(0, 59, size=3000)
+    fl["bit"] = rng.integers(0, S.FORMAT_BITS[fmt], size=3000)
+    bad = O.apply_flips(clean.planes, fmt, fl)
+    ref, nref = O.guard(bad, fmt, mask, mode, lo, hi)
+    words32 = -(-n // 32)
+    changed = np.zeros((clean.nwords, words32 * 32), dtype=bool)
+    changed[:, :n] = ref != bad
+    expect = np.packbits(changed, axis=1, bitorder="little").view("<u4")
+    h = _load(G, clean)
+    try:
+        if mode == 1:
+            G.gs_set_prim_box(h, lo, hi, 14)
+        G.gs_apply_flips(h, G.to_device(fl), len(fl))
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        bm = torch.full((clean.nwords * words32,), -1, dtype=torch.int32, device="cuda")   # overwritten whole
+        G.gs_guard_bitmap(h, mode, mask, bm, cnt)
+        torch.cuda.synchronize()
+        got = bm.cpu().numpy().view(np.uint32).reshape(clean.nwords, words32)
+        assert nref > 0 and int(cnt.item()) == nref
+        assert np.array_equal(got, expect)
+        assert int(np.unpackbits(got.view(np.uint8)).sum()) == nref
+        assert np.array_equal(_read(G, h, clean), ref)
+    finally:
+        G.gs_free_scene(h)
+
+
 # ---------------------------------------------------------------------------
 # (b) preprocess
 # ---------------------------------------------------------------------------
