@@ -60,3 +60,47 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "gs_oracle" not in text, f
+
+
+def test_invalid_arguments_are_refused_before_the_device(lib):
+    """Every call checks its arguments before it touches the device: a NULL
+    scene or server, a NULL required buffer or an out-of-range size returns
+    GS_ERR_ARG with a message, and never aborts (runs without a GPU)."""
+    from paper_2606_21791_gb300 import gs
+    calls = {
+        "gs_scene_info": (None, None, None, None, None),
+        "gs_apply_flips": (None, None, 1, None),
+        "gs_field_box": (None, None, None),
+        "gs_set_prim_box": (None, None, None, 0, 0),
+        "gs_guard": (None, 0, 1, None, None),
+        "gs_guard_bitmap": (None, 0, 1, None, None, None),
+        "gs_render": (None, None, 1, None, None),
+        "gs_compare": (None, None, 1, 1, 1, None, None),
+        "gs_compare_noalloc": (None, None, 1, 1, 1, None, None),
+        "gs_ssim": (None, None, 1, 1, 1, None, None),
+        "gs_set_views": (None, None, 1, None),
+        "gs_inject_and_render": (None, None, 1, 1, -1, 1, None, None),
+        "gs_inject_and_render_full": (None, None, 1, 1, -1, 1, None, None),
+        "gs_inject_and_render_regions": (None, None, 1, -1, 1, None, None, None),
+        "gs_inject_and_render_ex": (None, None, 1, -1, 1, None, None, None, None),
+        "gs_set_graphs": (None, 1),
+        "gs_count_work": (None, 1),
+        "gs_read_work": (None, None),
+        "gs_time_kernels": (None, 1),
+        "gs_read_kernel_ms": (None, None),
+        "gs_read_render_ms": (None, None, None),
+        "gs_set_batch": (None, 0),
+        "gs_autotune": (None, None, 0, -1, 1, None, None, None),
+        "gs_preprocess": (None, None, None, None),
+        "gs_bin_tiles": (None, None, 5, 1, 1, None, None, 1, None, None),
+        "gs_blend_lists": (None, 0, None, None, 1, 1, None, None),
+        "gs_server_create": (0, 0, None),
+        "gs_server_submit": (None, None, 0.0, None),
+        "gs_server_wait": (None, 0, 0, None),
+        "gs_server_cancel": (None, 0),
+        "gs_server_stats": (None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == gs.GS_ERR_ARG, name
+        assert lib.gs_last_error(), name
+    assert lib.gs_server_destroy(None) == gs.GS_OK      # NULL is a no-op, like free
