@@ -179,15 +179,14 @@ void free_ssim_buffers(gs_scene* s) {
 }
 
 // SSIM buffers sized for the current batch capacity (zeroed: generation 0 is never current)
-gs_status ensure_ssim_buffers(gs_scene* s) {
-    if (s->ssim.tile_map) return GS_OK;
+static gs_status alloc_ssim_buffers(gs_scene* s) {
     const int K = std::max(s->K, 1);
     SsimBufs b{};
     b.slot_cap = (uint32_t)std::min<uint64_t>(s->plan_cap, 1ull << 18);
     b.delta_cap = (uint32_t)std::min<uint64_t>((kTilePix / 32) * s->plan_cap, 1ull << 19);
     b.max_tiles = (uint32_t)std::max(s->max_tiles, 1);
     const size_t maps = (size_t)s->cap_B * K * b.max_tiles;
-    s->ssim = b;   // caps now; pointers below (freed together on failure)
+    s->ssim = b;   // caps now; pointers below
     GS_TRY(dmalloc((void**)&s->ssim.slot_group, sizeof(uint32_t) * 8 * b.slot_cap));
     GS_TRY(dmalloc((void**)&s->ssim.slot_flags, sizeof(uint32_t) * b.slot_cap));
     GS_TRY(dmalloc((void**)&s->ssim.deltas, sizeof(float4) * 32 * (size_t)b.delta_cap));
@@ -198,6 +197,14 @@ gs_status ensure_ssim_buffers(gs_scene* s) {
     GS_CUDA(cudaMemset(s->ssim.ssim_map, 0, sizeof(unsigned long long) * maps));
     GS_CUDA(cudaMemset(s->ssim.overflow, 0, sizeof(unsigned int)));
     return GS_OK;
+}
+
+// All or nothing: a set tile_map means every SSIM buffer is allocated and zeroed.
+gs_status ensure_ssim_buffers(gs_scene* s) {
+    if (s->ssim.tile_map) return GS_OK;
+    const gs_status rs = alloc_ssim_buffers(s);
+    if (rs != GS_OK) free_ssim_buffers(s);
+    return rs;
 }
 
 gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
@@ -215,11 +222,23 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     cudaFree(s->plan);
     cudaFree(s->cand);
     cudaFree(s->groups);
+    s->flip_stage = nullptr;
+    s->desc = nullptr;
+    s->item_off = nullptr;
+    s->acc = nullptr;
+    s->res_stage = nullptr;
+    s->queue = nullptr;
+    s->saved = nullptr;
     s->plan = nullptr;
     s->cand = nullptr;
     s->groups = nullptr;
-    int cb = std::max(B, s->cap_B);
-    int cf = std::max(fpv * B, s->cap_flips);
+    const int cb = std::max(B, s->cap_B);
+    const int cf = std::max(fpv * B, s->cap_flips);
+    // no capacity until every buffer below is allocated: a failure part way (out
+    // of memory) leaves nothing that a later call could take for usable
+    s->cap_B = 0;
+    s->cap_flips = 0;
+    s->plan_cap = 0;
     GS_TRY(dmalloc((void**)&s->flip_stage, sizeof(gs_flip) * cf));
     GS_TRY(dmalloc((void**)&s->desc, sizeof(DirtyDesc) * cb * K));
     GS_TRY(dmalloc((void**)&s->item_off, sizeof(uint32_t) * (2 * cb * K + 1)));   // offsets + per-pair counts
@@ -542,11 +561,8 @@ gs_status gs_compare(const float* dev_a, const float* dev_b, int H, int W, int K
     return rs;
 }
 
-gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* stream) {
-    if (!s || !host_cams || K < 1 || K > 16) return set_error(GS_ERR_ARG, "bad gs_set_views arguments (1 <= K <= 16)");
-    cudaStream_t st = (cudaStream_t)stream;
-    for (int k = 0; k < K; k++)
-        if (!valid_camera(host_cams[k])) return set_error(GS_ERR_ARG, "invalid camera");
+// The clean per-view state of gs_set_views, for validated arguments.
+static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cudaStream_t st) {
     free_views(s);
     s->views.resize(K);
     s->K = K;
@@ -664,6 +680,17 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
     GS_TRY(ensure_batch_buffers(s, 64, 1));
     GS_CUDA(cudaStreamSynchronize(st));
     return GS_OK;
+}
+
+gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* stream) {
+    if (!s || !host_cams || K < 1 || K > 16) return set_error(GS_ERR_ARG, "bad gs_set_views arguments (1 <= K <= 16)");
+    for (int k = 0; k < K; k++)
+        if (!valid_camera(host_cams[k])) return set_error(GS_ERR_ARG, "invalid camera");
+    const gs_status rs = build_views(s, host_cams, K, (cudaStream_t)stream);
+    // a failure part way (out of memory, a capacity limit) leaves no half-built
+    // views behind: campaign calls then report GS_ERR_STATE instead of reading them
+    if (rs != GS_OK) free_views(s);
+    return rs;
 }
 
 gs_status gs_clean_image(gs_scene* s, int k, float* dev_rgb, void* stream) {
