@@ -66,6 +66,12 @@ gs_status cuda_error(cudaError_t e, const char* what) {
     return set_error(GS_ERR_CUDA, m);
 }
 
+// the camera sizes and focal lengths the kernels accept (tile coordinates fit 16 bits)
+bool valid_camera(const gs_camera& c) {
+    return c.width > 0 && c.height > 0 && c.width <= 65535 * kTile && c.height <= 65535 * kTile && c.fx > 0 &&
+           c.fy > 0 && std::isfinite(c.fx) && std::isfinite(c.fy);
+}
+
 namespace {
 
 __global__ void k_move_clamps(unsigned long long* ctr, CmpAcc* acc) {
@@ -83,11 +89,6 @@ gs_status dmalloc(void** p, size_t bytes) {
         return set_error(GS_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
     return GS_OK;
-}
-
-bool valid_camera(const gs_camera& c) {
-    return c.width > 0 && c.height > 0 && c.width <= 65535 * kTile && c.height <= 65535 * kTile && c.fx > 0 &&
-           c.fy > 0 && std::isfinite(c.fx) && std::isfinite(c.fy);
 }
 
 // Full render pipeline of one view on scratch `w`: preprocess, depth sort,

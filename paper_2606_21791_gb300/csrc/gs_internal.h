@@ -290,6 +290,9 @@ gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, const gs_flip*
 // k_preprocess.cu
 DevCamera make_dev_camera(const gs_camera& c);
 
+// gs_api.cu: the camera sizes and focal lengths the kernels accept
+bool valid_camera(const gs_camera& c);
+
 // k_sort.cu
 gs_status alloc_render_work(RenderWork& w, uint64_t n, uint64_t cap_pairs, int ntiles);
 void free_render_work(RenderWork& w);

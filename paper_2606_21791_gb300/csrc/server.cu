@@ -90,7 +90,7 @@ struct gs_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Req*> queue;
     std::map<uint64_t, Req*> all;
-    std::vector<SceneEntry> scenes;
+    std::deque<SceneEntry> scenes;   // stable references: a scene may be added while workers hold one
     std::vector<Slot> slots;
     uint64_t next_ticket = 1;
     uint64_t scratch_total = 0;
@@ -124,10 +124,10 @@ uint64_t resident_total(gs_server* sv) {
     return r;
 }
 
-// run one request on a slot's stream; returns its status
-gs_status execute(gs_server* sv, Slot& sl, Req* q) {
+// run one request on a slot's stream (scene s, taken under the server lock);
+// returns its status
+gs_status execute(gs_scene* s, Slot& sl, Req* q) {
     const gs_request& r = q->r;
-    gs_scene* s = sv->scenes[r.scene].s;
     cudaStream_t st = sl.stream;
     if (r.kind == GS_REQ_CAMPAIGN) {
         GS_TRY(gs_inject_and_render(s, r.dev_flips, r.nflips, 1, r.guard_mode, r.word_mask, r.dev_results, st));
@@ -205,9 +205,10 @@ void worker(gs_server* sv, int slot_id) {
         pick->status = -2;
         pick->slot = slot_id;
         pick->t_start = now_ms(sv->t0);
+        gs_scene* scene = e.s;
         lk.unlock();
 
-        gs_status rs = execute(sv, sl, pick);
+        gs_status rs = execute(scene, sl, pick);
         std::string msg = rs == GS_OK ? std::string() : std::string(gs_last_error());
 
         lk.lock();
@@ -273,7 +274,7 @@ gs_status gs_server_submit(gs_server* sv, const gs_request* r, double arrival_ms
         return set_error(GS_ERR_ARG, "campaign request needs flips and result buffers");
     if (r->kind != GS_REQ_CAMPAIGN) {
         const gs_camera& c = r->cam;
-        if (c.width <= 0 || c.height <= 0 || !(c.fx > 0) || !(c.fy > 0)) return set_error(GS_ERR_ARG, "invalid camera");
+        if (!valid_camera(c)) return set_error(GS_ERR_ARG, "invalid camera");
         if (r->kind == GS_REQ_STORM && r->nflips > 0 && !r->dev_flips) return set_error(GS_ERR_ARG, "storm flips NULL");
     }
     Req* q = new Req();
