@@ -875,9 +875,14 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
     const int cands[9] = {8, 16, 32, 64, 128, 256, 512, 1024, 2048};
     gs_result* out = nullptr;
     GS_CUDA(cudaMallocAsync((void**)&out, sizeof(gs_result) * (size_t)count * K, st));
-    cudaEvent_t e0, e1;
-    GS_CUDA(cudaEventCreate(&e0));
-    GS_CUDA(cudaEventCreate(&e1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        cudaFreeAsync(out, st);
+        return set_error(GS_ERR_CUDA, "gs_autotune: event creation failed");
+    }
+    const int prev_batch = s->batch;
     int best = max_chunk;
     float best_t = 1e30f;
     gs_status rs = GS_OK;
@@ -904,7 +909,10 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(out, st);
-    if (rs != GS_OK) return rs;
+    if (rs != GS_OK) {
+        s->batch = prev_batch;   // a failed tuning run leaves the setting as it was
+        return rs;
+    }
     s->batch = best;
     *best_batch = best;
     if (best_us_per_variant) *best_us_per_variant = best_t;
