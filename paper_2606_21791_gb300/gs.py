@@ -102,7 +102,7 @@ class GsError(RuntimeError):
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
-    """Load libgs.so (built by build.py); raises if it is absent."""
+    """Load libgs.so (built by buildlib.build()); raises if it is absent."""
     global _lib
     with _lock:
         if _lib is None:

@@ -104,3 +104,15 @@ def test_invalid_arguments_are_refused_before_the_device(lib):
         assert getattr(lib, name)(*args) == gs.GS_ERR_ARG, name
         assert lib.gs_last_error(), name
     assert lib.gs_server_destroy(None) == gs.GS_OK      # NULL is a no-op, like free
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: without libgs.so the binding raises (in a fresh process,
+    since a loaded library is cached)."""
+    import subprocess
+    import sys
+    code = ("from paper_2606_21791_gb300 import gs\n"
+            f"gs.load_library({str(tmp_path / 'libgs.so')!r})\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode != 0
+    assert "no CPU fallback" in r.stderr
