@@ -40,7 +40,7 @@ WORKLOAD = ("2M Gaussians (4 clusters, SH degree 3, fp32), 4 ring views 1600x104
 FLOP_PER_EVAL = 20          # FP32 ops per pixel-primitive evaluation of the blend (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_k_dirty_2M_4views_batch2048.txt")
 
 
 def log(*a):
