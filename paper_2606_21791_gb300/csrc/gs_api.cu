@@ -776,7 +776,7 @@ gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B
     for (int b = 0; b < B; b++) {
         const gs_flip* f = dev_flips + (size_t)b * fpv;
         GS_TRY(launch_zero_acc(s->acc, K, st));
-        GS_TRY(launch_save_sites(s->planes, s->fmt, s->n, f, fpv, s->saved, st));
+        GS_TRY(launch_save_sites(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->saved, st));
         GS_TRY(launch_apply_flips(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->dev_err,
                                   guard_mode == GS_GUARD_ECC ? word_mask : 0ull, st));
         if (guard_mode == GS_GUARD_FIELD || guard_mode == GS_GUARD_PRIM) {
@@ -791,7 +791,7 @@ gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B
             GS_TRY(launch_blend_compare(s->work.recs, ids, s->work.ranges, v.cam.W, v.cam.H, v.clean, s->acc + k,
                                         s->work_ctr, st));
         }
-        GS_TRY(launch_restore_sites(s->planes, s->fmt, s->n, f, fpv, s->saved, st));
+        GS_TRY(launch_restore_sites(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->saved, st));
         GS_TRY(launch_finalize(s->acc, K, dev_out + (size_t)b * K, st));
     }
     return GS_OK;

@@ -282,9 +282,9 @@ int num_sms();
 gs_status launch_field_box(const void* planes, int fmt, uint64_t n, int nwords, uint32_t* dev_keys, cudaStream_t st);
 gs_status launch_guard(gs_scene* s, int mode, uint64_t mask, unsigned long long* dev_clamps, cudaStream_t st);
 gs_status launch_guard_mark(gs_scene* s, int mode, uint64_t mask, uint32_t* bitmap, cudaStream_t st);
-gs_status launch_save_sites(const void* planes, int fmt, uint64_t n, const gs_flip* flips, int count, uint32_t* saved,
-                            cudaStream_t st);
-gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, const gs_flip* flips, int count,
+gs_status launch_save_sites(const void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int count,
+                            uint32_t* saved, cudaStream_t st);
+gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int count,
                                const uint32_t* saved, cudaStream_t st);
 
 // k_preprocess.cu

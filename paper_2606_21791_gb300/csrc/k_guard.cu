@@ -43,19 +43,30 @@ __global__ void k_apply_flips(void* planes, int fmt, uint64_t n, int nwords, con
     }
 }
 
-__global__ void k_save_sites(const void* planes, int fmt, uint64_t n, const gs_flip* flips, int count, uint32_t* saved) {
+// The plain loop saves each site's word before applying the flips and writes it
+// back afterwards.  A site that k_apply_flips rejects (primitive, word or bit out
+// of range) is neither read nor written here: its index may lie outside the
+// planes.
+__device__ __forceinline__ bool site_valid(const gs_flip& f, int fmt, uint64_t n, int nwords) {
+    return f.prim < n && f.word < nwords && f.bit < (fmt == GS_FP32 ? 32 : 16);
+}
+
+__global__ void k_save_sites(const void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int count,
+                             uint32_t* saved) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
     gs_flip f = flips[j];
+    if (!site_valid(f, fmt, n, nwords)) return;
     uint64_t idx = (uint64_t)f.word * n + f.prim;
     saved[j] = fmt == GS_FP32 ? ((const uint32_t*)planes)[idx] : ((const uint16_t*)planes)[idx];
 }
 
-__global__ void k_restore_sites(void* planes, int fmt, uint64_t n, const gs_flip* flips, int count,
+__global__ void k_restore_sites(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int count,
                                 const uint32_t* saved) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
     gs_flip f = flips[j];
+    if (!site_valid(f, fmt, n, nwords)) return;
     uint64_t idx = (uint64_t)f.word * n + f.prim;
     if (fmt == GS_FP32)
         ((uint32_t*)planes)[idx] = saved[j];
@@ -289,18 +300,18 @@ gs_status launch_apply_flips(void* planes, int fmt, uint64_t n, int nwords, cons
     return GS_OK;
 }
 
-gs_status launch_save_sites(const void* planes, int fmt, uint64_t n, const gs_flip* flips, int count, uint32_t* saved,
-                            cudaStream_t st) {
+gs_status launch_save_sites(const void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int count,
+                            uint32_t* saved, cudaStream_t st) {
     if (count <= 0) return GS_OK;
-    k_save_sites<<<(count + 255) / 256, 256, 0, st>>>(planes, fmt, n, flips, count, saved);
+    k_save_sites<<<(count + 255) / 256, 256, 0, st>>>(planes, fmt, n, nwords, flips, count, saved);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
-gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, const gs_flip* flips, int count,
+gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, int nwords, const gs_flip* flips, int count,
                                const uint32_t* saved, cudaStream_t st) {
     if (count <= 0) return GS_OK;
-    k_restore_sites<<<(count + 255) / 256, 256, 0, st>>>(planes, fmt, n, flips, count, saved);
+    k_restore_sites<<<(count + 255) / 256, 256, 0, st>>>(planes, fmt, n, nwords, flips, count, saved);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
