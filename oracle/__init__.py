@@ -64,6 +64,7 @@ def lib():
             L.or_blend_brute.argtypes = [vp, u64, i32, i32, i32, i32, vp]
             L.or_compare.argtypes = [vp, vp, i32, i32, vp]
             L.or_render.argtypes = [vp, i32, u64, i32, vp, i32, i32, vp]
+            L.or_render_margins.argtypes = [vp, i32, u64, i32, vp, i32, i32, vp, vp]
             L.or_campaign.argtypes = [vp, i32, u64, i32, i32, vp, i32, i32, i32, vp, vp, i64, i32, i32,
                                       u64, vp, vp, i32, vp, vp, i32, vp, vp, vp]
             L.or_ssim.argtypes = [vp, vp, i32, i32]
@@ -175,6 +176,22 @@ def render(planes, fmt: int, sh_degree: int, cam, tile=(16, 16)) -> np.ndarray:
     rc = lib().or_render(_p(p), fmt, p.shape[1], sh_degree, _p(c), tile[0], tile[1], _p(img))
     assert rc == 0
     return img
+
+
+def render_margins(planes, fmt: int, sh_degree: int, cam, tile=(16, 16)):
+    """The render of ``render`` and, per pixel, how close its blend decisions came
+    to their thresholds: margins[..., 0] = min |alpha - 1/255| / (1/255) over the
+    entries walked, margins[..., 1] = min |T' - 1e-4| / 1e-4 (inf where no entry
+    was tested).  Used to attribute footprint differences between two renderers
+    whose exponentials round differently."""
+    c = _cam(cam)
+    p = _c(planes)
+    H, W = int(c[0]["height"]), int(c[0]["width"])
+    img = np.zeros((H, W, 3), dtype=np.float32)
+    mg = np.zeros((H, W, 2), dtype=np.float32)
+    rc = lib().or_render_margins(_p(p), fmt, p.shape[1], sh_degree, _p(c), tile[0], tile[1], _p(img), _p(mg))
+    assert rc == 0
+    return img, mg
 
 
 def compare(a: np.ndarray, b: np.ndarray) -> np.ndarray:

@@ -551,7 +551,17 @@ int64_t or_bin(const or_rec* recs, uint64_t n, int tiles_x, int tiles_y, uint32_
 /* (d) front-to-back alpha blending over white (Sec. 3 "Metrics and severity" */
 /* composites over white; the cutoffs are 1/255 on alpha and 1e-4 on T).       */
 /* ------------------------------------------------------------------------- */
-static void blend_pixel(const or_rec* recs, const uint32_t* list, size_t len, float pxc, float pyc, float* out3) {
+/* margin (may be NULL): how close the pixel's discrete decisions came to their
+ * thresholds, as relative distances over the entries walked up to the stop:
+ * margin[0] = min |alpha - 1/255| / (1/255) over entries with power <= 0 (the
+ * skip test), margin[1] = min |T' - 1e-4| / 1e-4 over entries that pass it (the
+ * stop test).  A renderer whose exponential rounds differently can take another
+ * decision only where one of these is small.  Diagnostic only: the pixel's
+ * value does not depend on it. */
+static void blend_pixel(const or_rec* recs, const uint32_t* list, size_t len, float pxc, float pyc, float* out3,
+                        float* margin) {
+    const double a_thr = (double)(1.0f / 255.0f), t_thr = (double)1e-4f;
+    double ma = INFINITY, mt = INFINITY;
     float T = 1.0f;
     float C[3] = {0.0f, 0.0f, 0.0f};
     for (size_t k = 0; k < len; k++) {
@@ -561,9 +571,17 @@ static void blend_pixel(const or_rec* recs, const uint32_t* list, size_t len, fl
         float power = -0.5f * (g->ca * dx * dx + g->cc * dy * dy) - g->cb * dx * dy;
         if (power > 0.0f) continue;
         float alpha = g->opac * expf(power);
+        if (margin) {
+            double m = fabs((double)alpha - a_thr) / a_thr;
+            if (m < ma) ma = m;
+        }
         if (alpha < 1.0f / 255.0f) continue;
         if (alpha > 0.99f) alpha = 0.99f;
         float Tn = T * (1.0f - alpha);
+        if (margin) {
+            double m = fabs((double)Tn - t_thr) / t_thr;
+            if (m < mt) mt = m;
+        }
         if (Tn < 1e-4f) break;
         C[0] = C[0] + g->r * alpha * T;
         C[1] = C[1] + g->g * alpha * T;
@@ -573,18 +591,30 @@ static void blend_pixel(const or_rec* recs, const uint32_t* list, size_t len, fl
     out3[0] = C[0] + T * 1.0f;
     out3[1] = C[1] + T * 1.0f;
     out3[2] = C[2] + T * 1.0f;
+    if (margin) {
+        margin[0] = (float)ma;
+        margin[1] = (float)mt;
+    }
 }
 
-/* tiled blend of the per-tile sorted lists; img is H*W*3, row-major */
-int or_blend(const or_rec* recs, const uint32_t* offsets, const uint32_t* ids, int W, int H, int tile_w,
-             int tile_h, float* img) {
+/* tiled blend of the per-tile sorted lists; img is H*W*3, row-major; margins
+ * (H*W*2, may be NULL) as in blend_pixel */
+static void blend_tiles(const or_rec* recs, const uint32_t* offsets, const uint32_t* ids, int W, int H, int tile_w,
+                        int tile_h, float* img, float* margins) {
     int tiles_x = (W + tile_w - 1) / tile_w;
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) {
             int64_t tile = (int64_t)(y / tile_h) * tiles_x + (x / tile_w);
             uint32_t a = offsets[tile], b = offsets[tile + 1];
-            blend_pixel(recs, ids + a, b - a, (float)x + 0.5f, (float)y + 0.5f, &img[((int64_t)y * W + x) * 3]);
+            int64_t p = (int64_t)y * W + x;
+            blend_pixel(recs, ids + a, b - a, (float)x + 0.5f, (float)y + 0.5f, &img[p * 3],
+                        margins ? &margins[p * 2] : NULL);
         }
+}
+
+int or_blend(const or_rec* recs, const uint32_t* offsets, const uint32_t* ids, int W, int H, int tile_w,
+             int tile_h, float* img) {
+    blend_tiles(recs, offsets, ids, W, H, tile_w, tile_h, img, NULL);
     return 0;
 }
 
@@ -608,7 +638,7 @@ int or_blend_brute(const or_rec* recs, uint64_t n, int W, int H, int tile_w, int
             }
             qsort(cand, m, sizeof(depth_id), cmp_depth_id);
             for (size_t k = 0; k < m; k++) list[k] = cand[k].id;
-            blend_pixel(recs, list, m, (float)x + 0.5f, (float)y + 0.5f, &img[((int64_t)y * W + x) * 3]);
+            blend_pixel(recs, list, m, (float)x + 0.5f, (float)y + 0.5f, &img[((int64_t)y * W + x) * 3], NULL);
         }
     free(cand);
     free(list);
@@ -657,8 +687,9 @@ int or_compare(const float* a, const float* b, int H, int W, or_metrics* out) {
 /* ------------------------------------------------------------------------- */
 /* whole forward render of one view                                           */
 /* ------------------------------------------------------------------------- */
-int or_render(const void* planes, int fmt, uint64_t n, int sh_degree, const or_camera* cam, int tile_w, int tile_h,
-              float* img) {
+/* margins: H*W*2 decision margins of every pixel (as in blend_pixel), or NULL */
+int or_render_margins(const void* planes, int fmt, uint64_t n, int sh_degree, const or_camera* cam, int tile_w,
+                      int tile_h, float* img, float* margins) {
     int W = cam->width, H = cam->height;
     int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
     int64_t ntiles = (int64_t)tiles_x * tiles_y;
@@ -671,11 +702,16 @@ int or_render(const void* planes, int fmt, uint64_t n, int sh_degree, const or_c
     uint32_t* ids = (uint32_t*)malloc(sizeof(uint32_t) * (total ? total : 1));
     int64_t got = or_bin(recs, n, tiles_x, tiles_y, offsets, ids, total);
     int rc = (got < 0) ? -1 : 0;
-    if (rc == 0) or_blend(recs, offsets, ids, W, H, tile_w, tile_h, img);
+    if (rc == 0) blend_tiles(recs, offsets, ids, W, H, tile_w, tile_h, img, margins);
     free(ids);
     free(offsets);
     free(recs);
     return rc;
+}
+
+int or_render(const void* planes, int fmt, uint64_t n, int sh_degree, const or_camera* cam, int tile_w, int tile_h,
+              float* img) {
+    return or_render_margins(planes, fmt, n, sh_degree, cam, tile_w, tile_h, img, NULL);
 }
 
 /* ------------------------------------------------------------------------- */

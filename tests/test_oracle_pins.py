@@ -599,6 +599,64 @@ def test_transmittance_cutoff_stops_pixel():
     np.testing.assert_allclose(img[H // 2, W // 2], C + T, atol=2e-6)
 
 
+def test_decision_margins_closed_form():
+    """The blend's decision margins, per pixel, from the closed form of one
+    isotropic primitive on the optical axis: alpha margin = |alpha - 1/255| /
+    (1/255) and, where alpha passes the cut-off, T' margin = |1 - alpha - 1e-4| /
+    1e-4; inf where no entry was tested (outside the tile rect or power > 0 never
+    happens on the centre).  The image equals the plain render."""
+    W = H = 64
+    d = 15.0
+    tile = (16, 16)
+    log_s, logit = -1.6, 1.0
+    cam = S.look_at_camera((0, 0, d), width=W, height=H)
+    v = _one_primitive(log_scale=(log_s,) * 3, logit=logit)
+    planes = _planes_from_values(v)
+    img, mg = O.render_margins(planes, S.FP32, 0, cam, tile)
+    assert np.array_equal(img, O.render(planes, S.FP32, 0, cam, tile))
+    f = float(cam["fx"])
+    var = (f * math.exp(log_s) / d) ** 2 + 0.3
+    r = math.ceil(3 * math.sqrt(var + math.sqrt(0.1)))
+    rect = _rect(W / 2, H / 2, r, W, H, tile)
+    ys, xs = np.mgrid[0:H, 0:W]
+    q = ((xs + 0.5 - W / 2) ** 2 + (ys + 0.5 - H / 2) ** 2) / var
+    alpha = _sigmoid(logit) * np.exp(-0.5 * q)
+    tx, ty = xs // tile[0], ys // tile[1]
+    inrect = (tx >= rect[0]) & (tx < rect[2]) & (ty >= rect[1]) & (ty < rect[3])
+    thr = float(np.float32(1 / 255))
+    exp_a = np.abs(alpha - thr) / thr
+    assert np.isinf(mg[..., 0][~inrect]).all() and np.isinf(mg[..., 1][~inrect]).all()
+    np.testing.assert_allclose(mg[..., 0][inrect], exp_a[inrect], rtol=2e-5, atol=1e-6)
+    passed = inrect & (alpha >= thr) & (np.abs(alpha - thr) > 1e-6)
+    tthr = float(np.float32(1e-4))
+    exp_t = np.abs(1 - np.minimum(alpha, 0.99) - tthr) / tthr
+    np.testing.assert_allclose(mg[..., 1][passed], exp_t[passed], rtol=2e-5)
+    assert np.isinf(mg[..., 1][inrect & (alpha < thr * (1 - 1e-6))]).all()
+
+
+def test_decision_margins_near_the_transmittance_stop():
+    """Two opaque primitives stacked on the axis: at the centre pixel the second
+    one's T' = (1 - a1)(1 - a2) is the closest decision to the 1e-4 stop."""
+    W = H = 32
+    d = 15.0
+    cam = S.look_at_camera((0, 0, d), width=W, height=H)
+    v = np.zeros((14, 2))
+    v[6] = 1.0
+    v[3:6] = 0.5
+    v[10] = 4.5
+    v[2] = (0.0, -1.0)
+    img, mg = O.render_margins(_planes_from_values(v), S.FP32, 0, cam)
+    f = float(cam["fx"])
+    T = 1.0
+    best = math.inf
+    for z in (0.0, -1.0):
+        var = (f * math.exp(0.5) / (d - z)) ** 2 + 0.3
+        a = min(0.99, _sigmoid(4.5) * math.exp(-0.5 * 0.5 / var))
+        T = T * (1 - a)
+        best = min(best, abs(T - 1e-4) / 1e-4)
+    assert abs(mg[H // 2, W // 2, 1] - best) <= 1e-3 * best
+
+
 def test_footprint_threshold_is_strict():
     """Definition 1 counts changes of MORE than one 8-bit level: a change of exactly
     1/255 (in fp32) is not in the footprint."""
