@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+import footprint_attribution as FA
 import oracle as O
 from paper_2606_21791_gb300 import synth as S
 
@@ -401,7 +402,9 @@ def test_campaign_tiny_matches_oracle(G):
         op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
         assert np.abs(gp - op).max() <= PSNR_TOL
         assert np.array_equal(g["nonfinite"] > 0, o["nonfinite"] > 0)
-        assert (g["footprint"] == o["footprint"]).mean() >= 0.99
+        att = FA.attribute(G, h, sc, cams, flips, g["footprint"], o["footprint"])
+        print("footprint attribution, 5,000 Gaussians:", att)
+        assert att["unexplained"] == 0, att
     finally:
         G.gs_free_scene(h)
 
@@ -450,7 +453,10 @@ def test_campaign_batching_guard_matches_oracle(G):
         gp = np.array([_psnr(x, npx) for x in g["sse"].ravel()])
         op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
         assert np.abs(gp - op).max() <= PSNR_TOL
-        assert (g["footprint"] == o["footprint"]).mean() >= 0.99
+        att = FA.attribute(G, h, sc, cams, flips, g["footprint"], o["footprint"], guard=1,
+                           mask=S.GUARD_WORDS_DEFAULT, box_lo=lo, box_hi=hi)
+        print("footprint attribution, 20,000 Gaussians fp16 PRIM guard:", att)
+        assert att["unexplained"] == 0, att
     finally:
         G.gs_free_scene(h)
 
@@ -541,7 +547,10 @@ def test_ecc_campaign_matches_oracle(G, fmt):
         op = np.array([_psnr(x, npx) for x in o["sse"].ravel()])
         assert np.abs(gp - op).max() <= PSNR_TOL
         assert np.array_equal(g["nonfinite"] > 0, o["nonfinite"] > 0)
-        assert (g["footprint"] == o["footprint"]).mean() >= 0.99
+        assert (o[corr]["footprint"] == 0).all()
+        att = FA.attribute(G, h, sc, cams, flips[~corr], g[~corr]["footprint"], o[~corr]["footprint"])
+        print(f"footprint attribution, ECC fmt {fmt}:", att)
+        assert att["unexplained"] == 0, att
     finally:
         G.gs_free_scene(h)
 
@@ -683,6 +692,23 @@ def test_campaign_edge_cases(G):
         r = _campaign_gpu(G, h, bad, K)
         for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
             assert (r[f] == 0).all(), f
+        # The plain loop saves, applies and restores the sites: an invalid site is
+        # skipped by all three (the scene stays clean, the error flag is raised),
+        # one variant at a time and as part of a multi-upset variant.
+        G.gs_scene_errors(h)   # clear
+        before = _read(G, h, sc)
+        for guard in (-1, 1):
+            r = _campaign_gpu(G, h, bad, K, guard=guard, full=True)
+            for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+                assert (r[f] == 0).all(), (guard, f)
+        assert G.gs_scene_errors(h) & 1
+        mixed = np.concatenate([bad, S.flips_at(np.array([7], np.uint32), 10, 30)])   # 3 invalid + 1 valid
+        r = _campaign_gpu(G, h, mixed, K, fpv=4, full=True)
+        one = _campaign_gpu(G, h, mixed[3:], K, full=True)
+        for f in ("sse", "maxabs", "footprint", "nonfinite"):
+            assert np.array_equal(r[f], one[f]), f
+        assert G.gs_scene_errors(h) & 1
+        assert np.array_equal(_read(G, h, sc).view(np.uint32), before.view(np.uint32))
         far = S.flips_at(np.array([5], np.uint32), 70, 0)   # word 70 >= 64: invalid, not protected
         r = _campaign_gpu(G, h, far, K, guard=2, mask=(1 << 59) - 1)
         assert (r["sse"] == 0).all()
