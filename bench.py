@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 METRIC = "injections/s and Mpix/s vs plain loop on 1 GB300; p99 frame latency; guard GB/s"
 UNIT = "injections/s"
 WORKLOAD = ("2M Gaussians (4 clusters, SH degree 3, fp32), 4 ring views 1600x1040, 20k upsets "
-            "(70% on bits 24-31 of log-scale/opacity); batched dirty-tile engine, CUDA graphs, guard off")
+            "(70% on bits 24-31 of log-scale/opacity), guard off")
+ENGINE = "batched dirty-tile engine (inject, plan, re-blend + compare, finalise), replayed as a CUDA graph"
 FLOP_PER_EVAL = 20          # FP32 ops per pixel-primitive evaluation of the blend (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -142,37 +143,42 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (rank 0, N = 1)
 # ---------------------------------------------------------------------------
-def cpu_baseline(scene, cams, flips, crop=None, variants=None, keep=None):
-    """Times the oracle as it stands on the host cores: `variants` upsets (one per
-    core), each rendered in view 0 (optionally a centred crop of it) and compared
-    with the clean view; extrapolated to injections/s over all views.  `keep`
-    (a dict) receives the clean view and its render time."""
+def workload_config(n, cams, nflips, world=1):
+    """The `config` of both arms: the workload only (no engine settings)."""
+    W, H = int(cams[0]["width"]), int(cams[0]["height"])
+    name = WORKLOAD if n == 2_000_000 else f"profiling case: {n} Gaussians, otherwise " + WORKLOAD
+    return {"workload": name, "gaussians": n, "sh_degree": 3, "storage": "fp32", "resolution": f"{W}x{H}",
+            "views": len(cams), "upsets": nflips, "guard": "off",
+            "l2": "GPU steps: a 256 MB buffer is written between timed steps (outside the step events)",
+            "parallelism": f"replicas x{world}, upset list sharded"}
+
+
+def clean_views(scene, cams):
+    """Clean renders of every view by the oracle, one thread per view (its C calls
+    release the GIL); returns (images, seconds)."""
+    import concurrent.futures as cf
     import oracle as O
-    from paper_2606_21791_gb300 import synth as S
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=len(cams)) as ex:
+        imgs = list(ex.map(lambda c: O.render(scene.planes, scene.fmt, scene.sh_degree, c), list(cams)))
+    return imgs, time.perf_counter() - t0
+
+
+def cpu_baseline(scene, cams, flips, clean, t_clean):
+    """Times the oracle as it stands on the host cores on the benchmark workload
+    itself: one upset per core, each rendered in every view at full resolution
+    and compared with the clean views (OpenMP over upsets).  Nothing is
+    extrapolated: value = upsets / seconds."""
+    import oracle as O
     cores = O.max_threads()
-    nvar = variants or cores
-    cam = np.array(cams[0:1], copy=True)
-    full_px = int(cams[0]["width"]) * int(cams[0]["height"])
-    if crop:
-        w, h = crop
-        cam["cx"] -= (int(cam["width"][0]) - w) / 2.0
-        cam["cy"] -= (int(cam["height"][0]) - h) / 2.0
-        cam["width"], cam["height"] = w, h
-    px = int(cam["width"][0]) * int(cam["height"][0])
+    nvar = cores
     t0 = time.perf_counter()
-    clean = [O.render(scene.planes, scene.fmt, scene.sh_degree, cam[0])]
-    t_clean = time.perf_counter() - t0
-    if keep is not None:
-        keep.update(cam=cam, clean=clean, t_clean=t_clean)
-    t0 = time.perf_counter()
-    O.campaign(scene.planes, scene.fmt, scene.sh_degree, cam, flips[:nvar], clean_imgs=clean, nthreads=cores)
+    O.campaign(scene.planes, scene.fmt, scene.sh_degree, cams, flips[:nvar], clean_imgs=clean, nthreads=cores)
     t = time.perf_counter() - t0
-    frac = px / (full_px * len(cams))
-    value = nvar * frac / t
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nvar} upsets x 1 of {len(cams)} views ({cam['width'][0]}x{cam['height'][0]} px), "
-                      f"{t:.1f} s on {cores} threads (OpenMP over upsets); extrapolated linearly in pixels "
-                      f"to all views; clean render {t_clean:.1f} s untimed"}
+    W, H = int(cams[0]["width"]), int(cams[0]["height"])
+    return {"value": nvar / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nvar} upsets x all {len(cams)} views at {W}x{H}, {t:.1f} s on {cores} threads (OpenMP over "
+                      f"upsets), not extrapolated; clean views rendered untimed ({t_clean:.1f} s)"}
 
 
 def cpu_model() -> str:
@@ -187,13 +193,13 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def oracle_timing(scene3, cams3, flips3, c3_all, c3_view0):
+def oracle_timing(scene3, cams3, flips3, c3_all, clean3, t_clean3):
     """Per-injection cost of the oracle, as it stands, single-threaded and with
     OpenMP over upsets on all host cores, on the three campaign workloads: the
     5,000-Gaussian 256x256 one (bounded samples of its 200 upsets), the
     134,826-Gaussian 800x800 stratified one (samples of 100 upsets) and the
     benchmark's (one upset single-threaded in view 0, extrapolated to 4 views;
-    the all-cores figure is `cpu_baseline`, whose clean view 0 `c3_view0` holds).
+    the all-cores figure is `cpu_baseline`; `clean3` are its clean views).
     Clean frames are rendered first and timed on their own.  Context for the
     GPU numbers, never a target."""
     import oracle as O
@@ -223,51 +229,52 @@ def oracle_timing(scene3, cams3, flips3, c3_all, c3_view0):
                  "single_thread": per_inj(sc, cams, fl[:2], clean, 1),
                  "all_cores": per_inj(sc, cams, fl[:nall], clean, cores),
                  "sample": f"2 of 100 upsets single-threaded, {nall} on all cores"}
-    cam0, clean, tc = c3_view0["cam"], c3_view0["clean"], c3_view0["t_clean"]
-    single = per_inj(scene3, cam0, flips3[:1], clean, 1) * len(cams3)
+    single = per_inj(scene3, cams3[0:1], flips3[:1], clean3[0:1], 1) * len(cams3)
     out["c3"] = {"workload": "2M Gaussians (4 clusters, SH 3, fp32), 4 views 1600x1040",
-                 "clean_frame_s": tc, "single_thread": single, "all_cores": 1.0 / c3_all,
+                 "clean_frames_s": t_clean3, "single_thread": single, "all_cores": 1.0 / c3_all,
                  "sample": "1 upset in view 0 single-threaded, extrapolated to 4 views; all cores: cpu_baseline",
                  "campaign_of_20000_single_thread_days": single * 20000 / 86400.0}
     return out
 
 
 def run_reference(args):
+    """The oracle, as it stands, on the host cores (there is no other
+    implementation of this path to install).  A step is one upset per core,
+    rendered at full resolution in one view and compared with it; the view
+    rotates over the four ring views from step to step, so K steps cover
+    K * cores (upset, view) pairs = K * cores / 4 injections.  Only rank 0 runs."""
     rank, local, world = dist_info()
     if rank != 0:
         return
     from paper_2606_21791_gb300 import synth as S
     import oracle as O
     O.build()
-    scene, cams, flips = S.scale_workload()
+    scene, cams, flips = S.scale_workload(n=args.gaussians)
     cores = O.max_threads()
-    crop = (400, 260)
-    K, W = args.steps, args.warmup
+    K, Wu = args.steps, args.warmup
+    nv = len(cams)
+    clean, t_clean = clean_views(scene, cams)
     times = []
-    for i in range(W + K):
+    for i in range(Wu + K):
         sl = flips[(i * cores) % (len(flips) - cores):][:cores]
+        k = i % nv
         t0 = time.perf_counter()
-        cam = np.array(cams[0:1], copy=True)
-        cam["cx"] -= (int(cam["width"][0]) - crop[0]) / 2.0
-        cam["cy"] -= (int(cam["height"][0]) - crop[1]) / 2.0
-        cam["width"], cam["height"] = crop
-        if i == 0:
-            clean = [O.render(scene.planes, scene.fmt, scene.sh_degree, cam[0])]
-            t0 = time.perf_counter()
-        O.campaign(scene.planes, scene.fmt, scene.sh_degree, cam, sl, clean_imgs=clean, nthreads=cores)
-        if i >= W:
+        O.campaign(scene.planes, scene.fmt, scene.sh_degree, cams[k:k + 1], sl, clean_imgs=clean[k:k + 1],
+                   nthreads=cores)
+        if i >= Wu:
             times.append(time.perf_counter() - t0)
-    frac = crop[0] * crop[1] / (1600 * 1040 * len(cams))
     total = sum(times)
-    value = K * cores * frac / total
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": W,
+    value = K * cores / nv / total
+    W, H = int(cams[0]["width"]), int(cams[0]["height"])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": Wu,
             "ms_per_step": 1000 * total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD if scene.n == 2_000_000 else f"profiling case: {scene.n} Gaussians, otherwise "
-                                                                      + WORKLOAD, "gaussians": scene.n, "views": len(cams), "resolution": "1600x1040"},
+            "config": workload_config(scene.n, cams, len(flips), args.gpus),
+            "engine": "CPU oracle (plain C, fp32 render math, OpenMP over upsets)",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per step {cores} upsets x view 0 crop {crop[0]}x{crop[1]} (OpenMP over "
-                                       f"upsets), extrapolated linearly in pixels to 4 full views"},
+                             "sample": f"per step {cores} upsets x 1 full {W}x{H} view, the view rotating over the "
+                                       f"{nv} ring views; value = steps x {cores} / {nv} / seconds (not "
+                                       f"extrapolated in pixels); clean views rendered untimed ({t_clean:.1f} s)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -384,9 +391,33 @@ def main():
         host_out.copy_(out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_t, e2e_units = R.aggregate(time.perf_counter() - e0, B * args.steps, dev)
+    # the last step's records of every rank on rank 0, in list order (untimed): the
+    # ranks' slices of one step are consecutive, rank by rank
+    last = host_out.numpy().view(G.RESULT_DTYPE).reshape(B, K_views)
+    gathered = R.gather_records(rank * B + np.arange(B), last, world * B, dev)
     e2e = {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": B * 8,
            "d2h_bytes_per_step": B * K_views * 24,
            "how": "per step: pinned host flips -> device, gs_inject_and_render, records -> pinned host, sync"}
+
+    # the same workload at batches of 8-64 variants per launch (graph replay each)
+    small_b = {}
+    nsb = min(2048, nflips)
+    for b in (8, 16, 32, 64):
+        G.gs_set_batch(h, b)
+        G.gs_inject_and_render(h, d_flips[:8 * b], b, 1, G.GS_GUARD_OFF, mask, out)   # capture
+        torch.cuda.synchronize()
+        sb0, sb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sbo = G.device_bytes(nsb * K_views * 24, dev)
+        flush.zero_()
+        sb0.record(stream)
+        G.gs_inject_and_render(h, d_flips[:8 * nsb], nsb, 1, G.GS_GUARD_OFF, mask, sbo)
+        sb1.record(stream)
+        torch.cuda.synchronize()
+        small_b[str(b)] = nsb / (sb0.elapsed_time(sb1) / 1000.0)
+    best_small = max(small_b, key=small_b.get)
+    small_batches = {"injections_s": small_b, "best_batch": int(best_small), "best_injections_s": small_b[best_small],
+                     "sample": f"the first {nsb} upsets per batch size, one call each (launches of B variants)"}
+    G.gs_set_batch(h, B)
 
     # plain loop: one variant per launch, full preprocess + sort + blend + compare, no graphs
     nplain = 16
@@ -432,6 +463,7 @@ def main():
                                     "blocks_blended": work["blocks_blended"] / args.steps,
                                     "warp_steps": work["warp_steps"] / args.steps,
                                     "warp_steps_blending": work["warp_steps_blending"] / args.steps,
+                                    "warp_cycle_share": phase_shares(work),
                                     "plan_drops": {k: work[k] / args.steps for k in
                                                    ("dropped_stop_key", "dropped_tile_reach", "dropped_no_reach",
                                                     "dropped_pixel_stop")}},
@@ -442,13 +474,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if scene.n == 2_000_000 else f"profiling case: {scene.n} Gaussians, otherwise "
-                                                                      + WORKLOAD, "gaussians": scene.n, "sh_degree": 3, "storage": "fp32",
-                   "resolution": f"{Wd}x{Hd}", "views": K_views, "batch": B, "upsets": nflips,
-                   "l2": "256 MB buffer written between timed steps (outside the step events)",
-                   "parallelism": f"replicas x{world}, upset list sharded"},
+        "config": workload_config(scene.n, cams, nflips, world),
+        "engine": {"name": ENGINE, "batch": B, "batch_from": "set" if args.batch > 0 else "autotuner"},
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        # per step: injector, item scan, two plan kernels, dirty-tile blend, finalise
+        "gpu_launches": 6 * args.steps,
+        "records_gathered_on_rank0": None if gathered is None else int(gathered.shape[0]),
         "mpix_s_effective": value * K_views * Wd * Hd / 1e6,
         "mpix_s_blended": work["blocks_blended"] * 32 * world / t_total / 1e6,
         "plain_loop": plain,
@@ -456,6 +487,7 @@ def main():
         "contamination": contam,
         "ssim": ssim_line,
         "speedup_vs_plain_loop": value / plain["value"],
+        "batches_8_to_64": small_batches,
         "batch_latency_ms": {"p50": p50, "p99": p99, "what": f"one launch of {B} variants x {K_views} views"},
         "wall_s_timed_region": wall,
         "roofline": roofline,
@@ -470,23 +502,54 @@ def main():
         line["guard"] = guard_stress(args, G, S, dev, pk, pk_kind)
     if world == 1 and not args.no_analytics:
         line["campaign_analytics"] = campaign_analytics(G, S, dev)
+        line["formats_134k"] = batching_formats(G, S, dev)
     if not args.no_serving:
         line["serving"] = serving(args, G, S, dev)
         st = line["serving"]["storm"]
-        line["p99_frame_latency_ms"] = {"storm_guard_on": st["guard_on"]["p99_ms"],
+        line["p99_frame_latency_ms"] = {"storm_field_guard": st["guard_field"]["p99_ms"],
+                                        "storm_prim_guard": st["guard_prim"]["p99_ms"],
                                         "storm_guard_off": st["guard_off"]["p99_ms"],
-                                        "poisson_80pct": line["serving"]["poisson"][1]["p99_ms"]}
+                                        "poisson_80pct": line["serving"]["poisson"][1]["p99_ms"],
+                                        "poisson_80pct_budget_bound": line["serving"]["budget_bound"]["p99_ms"]}
     if rank == 0 and world == 1 and not args.no_cpu:
-        view0 = {}
-        line["cpu_baseline"] = cpu_baseline(scene, cams, flips, keep=view0)
+        clean3, t_clean3 = clean_views(scene, cams)
+        line["cpu_baseline"] = cpu_baseline(scene, cams, flips, clean3, t_clean3)
         try:
-            line["oracle_timing"] = oracle_timing(scene, cams, flips, line["cpu_baseline"]["value"], view0)
+            line["oracle_timing"] = oracle_timing(scene, cams, flips, line["cpu_baseline"]["value"], clean3, t_clean3)
         except Exception as e:   # context only: report the failure, keep the measured line
             line["oracle_timing"] = {"error": repr(e)}
+    line["summary"] = summary(line)   # last, so a cut-off tail of the line still holds it
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def phase_shares(work):
+    """Shares of the dirty-tile blend's warp cycles (measurement build) spent
+    setting up a block, walking its entries and comparing."""
+    keys = ("cycles_setup", "cycles_walk", "cycles_compare")
+    tot = sum(work.get(k, 0) for k in keys)
+    return {k.split("_", 1)[1]: (work[k] / tot if tot else None) for k in keys}
+
+
+def summary(line):
+    """The secondary targets of the line in one small object."""
+    def get(*path):
+        d = line
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    return {"injections_s": line["value"], "e2e_injections_s": get("e2e", "value"),
+            "plain_loop_injections_s": get("plain_loop", "value"),
+            "speedup_vs_plain_loop": line.get("speedup_vs_plain_loop"),
+            "k_dirty_roofline_frac": get("roofline", "frac"),
+            "guard_field_frac_of_hbm": get("guard", "field", "frac"),
+            "guard_prim_frac_of_hbm": get("guard", "prim", "frac"),
+            "p99_frame_latency_ms": line.get("p99_frame_latency_ms"),
+            "cpu_baseline_injections_s": get("cpu_baseline", "value")}
 
 
 def contamination(G, S, h, scene, K_views, dev, count=256):
@@ -569,6 +632,42 @@ def campaign_analytics(G, S, dev):
     res["scaling"] = {"sizes": sizes, "upsets_per_size": "20,000 on log-scale sign/exponent bits (words 3-5, bits 23-31)",
                       "error": "per-variant MSE (800x800x3)", **fits,
                       "guard_mean_error_factor_at_largest": mean["no_guard"][-1] / max(mean["field_guard"][-1], 1e-30)}
+    return res
+
+
+def batching_formats(G, S, dev):
+    """The 134,826-Gaussian campaign (4 clusters, SH 3, 800x800, one view, 50,000
+    upsets stratified over every (word, bit) cell of the format) in each storage
+    format, fp32, fp16 and bf16, with the guard off and with per-primitive (PRIM)
+    boxes on the 14 non-SH-rest words: injections/s of the whole campaign at
+    32 variants per launch and at the batch the autotuner picks."""
+    import torch
+    res = {"workload": "134,826 Gaussians (4 clusters, SH 3), 800x800, 1 view, 50,000 stratified upsets"}
+    for fmt, fname in ((S.FP32, "fp32"), (S.FP16, "fp16"), (S.BF16, "bf16")):
+        sc, cams, fl = S.batching_workload(fmt, count=50_000)
+        h = G.gs_load_scene(sc.planes, sc.n, 3, fmt)
+        lo, hi = S.prim_boxes(sc, 14, S.SEED_BASE + 60)
+        G.gs_set_prim_box(h, lo, hi, 14)
+        G.gs_set_views(h, cams)
+        d = G.to_device(fl, dev)
+        out = G.device_bytes(len(fl) * 24, dev)
+        b_auto, _ = G.gs_autotune(h, d, 8192, G.GS_GUARD_OFF, S.GUARD_WORDS_DEFAULT)
+        row = {"autotuned_batch": b_auto}
+        for gname, gmode in (("guard_off", G.GS_GUARD_OFF), ("prim_guard", G.GS_GUARD_PRIM)):
+            for bname, b in (("batch_32", 32), ("batch_auto", b_auto)):
+                G.gs_set_batch(h, b)
+                G.gs_inject_and_render(h, d[:8 * 512], 512, 1, gmode, S.GUARD_WORDS_DEFAULT, out)   # warm, capture
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                G.gs_inject_and_render(h, d, len(fl), 1, gmode, S.GUARD_WORDS_DEFAULT, out)
+                e1.record()
+                torch.cuda.synchronize()
+                row[f"{gname}_{bname}"] = len(fl) / (e0.elapsed_time(e1) / 1000.0)
+        res[fname] = row
+        G.gs_free_scene(h)
+        del d, out
+    torch.cuda.empty_cache()
     return res
 
 
@@ -700,34 +799,64 @@ def serving(args, G, S, dev):
     for t in inflight:
         G.gs_server_wait(srv, t)
     cap_rps = n_cap / (time.perf_counter() - c0)
-    # open loop: Poisson arrivals at fractions of capacity; latency = arrival -> done
-    poisson = []
-    for load in (0.5, 0.8, 0.95):
-        rate = load * cap_rps
-        n = 150
-        gaps = rng.exponential(1.0 / rate, size=n)
-        reqs = [make(1000 + i) for i in range(n)]
+    # open loop: Poisson arrivals at fractions of capacity; latency = scheduled
+    # arrival -> done (the arrival time is passed to the server, so a submitter
+    # that falls behind does not hide queueing)
+    def open_loop(server, rate, n, seed_off):
+        gaps = rng.exponential(1000.0 / rate, size=n)   # ms
+        reqs = [make(seed_off + i) for i in range(n)]
+        off = G.gs_server_now(server) - time.perf_counter() * 1000.0   # server ms = perf ms + off
+        t_first = G.gs_server_now(server) + 2.0
+        arrivals = t_first + np.cumsum(gaps)
         tickets = []
-        start = time.perf_counter()
-        arrival = 0.0
-        base_ms = None
         for i in range(n):
-            arrival += gaps[i]
-            while time.perf_counter() - start < arrival:
-                time.sleep(0.0002)
-            tickets.append(G.gs_server_submit(srv, reqs[i]))
-        lat = []
+            while time.perf_counter() * 1000.0 + off < arrivals[i]:
+                time.sleep(0.0001)
+            tickets.append(G.gs_server_submit(server, reqs[i], float(arrivals[i])))
+        lat, last = [], 0.0
         for t in tickets:
-            r = G.gs_server_wait(srv, t)
+            r = G.gs_server_wait(server, t)
             lat.append(r["t_done_ms"] - r["t_submit_ms"])
-        span = time.perf_counter() - start
-        poisson.append({"load": load, "offered_rps": rate, "throughput_rps": n / span,
-                        "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99), "mean_ms": sum(lat) / n})
+            last = max(last, r["t_done_ms"])
+        span_s = (last - t_first) / 1000.0
+        return {"requests": n, "offered_rps": rate, "throughput_rps": n / span_s, "p50_ms": _pct(lat, 0.5),
+                "p99_ms": _pct(lat, 0.99), "mean_ms": sum(lat) / n}
+
+    n_open = 2000
+    poisson = []
+    for j, load in enumerate((0.5, 0.8, 0.95)):
+        row = open_loop(srv, load * cap_rps, n_open, 1000 + j * n_open)
+        row["load"] = load
+        poisson.append(row)
     G.gs_server_destroy(srv)
+    # the same mix at 80% load under a budget that holds the resident scenes and
+    # the render scratch of two requests at most: admission has to wait for memory
+    srv = G.gs_server_create(1 << 50, 1)   # one slot: the scratch of the largest request alone
+    big = [G.gs_server_add_scene(srv, hh) for hh in handles][-1]
+    cam_big = S.ring_cameras(1, 1600, 1040)[0]
+    G.gs_server_wait(srv, G.gs_server_submit(srv, G.make_request(G.GS_REQ_RENDER, big, cam_big, dev_rgb=pool[0])))
+    st0 = G.gs_server_stats(srv)
+    G.gs_server_destroy(srv)
+    scratch_big = st0["scratch"]
+    budget = st0["resident"] + 2 * scratch_big + (64 << 20)
+    srv = G.gs_server_create(budget, slots)
+    ids = [G.gs_server_add_scene(srv, hh) for hh in handles]
+    for i in range(8):
+        G.gs_server_wait(srv, G.gs_server_submit(srv, make(i)))
+    tight = open_loop(srv, 0.8 * cap_rps, n_open, 20000)
+    stt = G.gs_server_stats(srv)
+    G.gs_server_destroy(srv)
+    tight.update({"load": 0.8, "budget_bytes": budget, "resident_bytes": st0["resident"],
+                  "scratch_bytes_largest_request": scratch_big,
+                  "delayed_by_budget_frac": stt["mem_delayed"] / (n_open + 8), "refused": 0})
     # upset storm on the largest scene: 1,000 upsets accumulate per frame
     storm = {}
-    for guard in (1, 0):
+    lo3, hi3 = S.prim_boxes(scenes[3], 14, S.SEED_BASE + 44)
+    for name, guard in (("guard_prim", G.GS_GUARD_PRIM), ("guard_field", G.GS_GUARD_FIELD),
+                        ("guard_off", G.GS_GUARD_OFF)):
         h = G.gs_load_scene(scenes[3].planes, scenes[3].n, 3, S.FP16)
+        if guard == G.GS_GUARD_PRIM:
+            G.gs_set_prim_box(h, lo3, hi3, 14)
         srv = G.gs_server_create(200 << 30, 1)
         sid = G.gs_server_add_scene(srv, h)
         cam = S.ring_cameras(1, 1600, 1040)[0]
@@ -738,7 +867,7 @@ def serving(args, G, S, dev):
         lat = []
         for f in range(frames + 5):
             fi = f % frames
-            r = G.make_request(G.GS_REQ_STORM, sid, cam, guard_mode=0 if guard else -1,
+            r = G.make_request(G.GS_REQ_STORM, sid, cam, guard_mode=guard,
                                word_mask=S.GUARD_WORDS_DEFAULT, dev_flips=d_fl[fi * 8000:(fi + 1) * 8000], nflips=1000,
                                dev_rgb=img)
             resp = G.gs_server_wait(srv, G.gs_server_submit(srv, r))
@@ -747,7 +876,7 @@ def serving(args, G, S, dev):
         finite = bool(torch.isfinite(img).all().item())
         G.gs_server_destroy(srv)
         G.gs_free_scene(h)
-        storm["guard_on" if guard else "guard_off"] = {
+        storm[name] = {
             "frames": frames, "upsets_per_frame": 1000, "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99),
             "mean_ms": sum(lat) / len(lat), "last_frame_finite": finite}
     for h in handles:
@@ -757,8 +886,9 @@ def serving(args, G, S, dev):
     return {"scenes": list(sizes), "storage": "fp16", "slots": slots, "capacity_rps": cap_rps,
             "mix": "90% renders (random scene, 800x800 or 1600x1040, random view), 10% 1,000-upset campaigns on the "
                    "134,826-Gaussian scene (800x800)",
-            "poisson": poisson, "storm": storm,
-            "latency": "host ms from arrival (open loop) or submission (storm) to completion of the request's stream"}
+            "poisson": poisson, "budget_bound": tight, "storm": storm,
+            "latency": "host ms from the scheduled arrival (open loop, passed to the server) or submission (storm) "
+                       "to completion of the request's stream"}
 
 
 def guard_frame(G, S, h, n, dev, guard_ms):

@@ -254,9 +254,12 @@ GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
  * test, [6] because no pixel is reached, [7] because every reached pixel
  * stopped before the change, [8] list entries walked by a warp of the
  * dirty-tile blend (survivors of its box cull), [9] of them blended by at
- * least one of its pixels, [10] 8x4 pixel blocks re-blended, [11] reserved
- * (graphs are bypassed while counting).  gs_read_work copies those 12 counts
- * into host_counts[12] and resets them (synchronises). */
+ * least one of its pixels, [10] 8x4 pixel blocks re-blended, and the SM
+ * cycles the dirty-tile blend's warps spend per phase: [11] setting up a block
+ * (work queue, plan item, checkpoint, sublist searches), [12] the walk over
+ * its entries, [13] the comparison with the clean image and the reductions
+ * (graphs are bypassed while counting).  gs_read_work copies those 14 counts
+ * into host_counts[14] and resets them (synchronises). */
 GS_API gs_status gs_count_work(gs_scene* scene, int enable);
 GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
 /* Kernel timing for measurement: while enabled, CUDA events bracket the two
@@ -358,8 +361,14 @@ GS_API gs_status gs_server_submit(gs_server* server, const gs_request* req, doub
 GS_API gs_status gs_server_wait(gs_server* server, uint64_t ticket, int timeout_ms, gs_response* out);
 /* Remove a request that has not started (GS_ERR_BUSY once it has). */
 GS_API gs_status gs_server_cancel(gs_server* server, uint64_t ticket);
-/* [budget, resident bytes, scratch bytes held, queued, completed] */
+/* host_stats[6]: [budget, resident bytes, scratch bytes held, queued, completed,
+ * requests that started only after waiting for HBM budget (passed over at
+ * least once because their render scratch did not fit)] */
 GS_API gs_status gs_server_stats(gs_server* server, uint64_t* host_stats);
+/* The server's clock: host milliseconds since gs_server_create, the time base
+ * of arrival_ms and of the response times (so a caller can pass the scheduled
+ * arrival of an open-loop request and have its queueing counted). */
+GS_API gs_status gs_server_now(gs_server* server, double* now_ms);
 /* Finishes every queued request, then stops the workers. */
 GS_API gs_status gs_server_destroy(gs_server* server);
 

@@ -935,7 +935,7 @@ gs_status gs_count_work(gs_scene* s, int enable) {
 gs_status gs_read_work(gs_scene* s, uint64_t* host_counts) {
     if (!s || !host_counts) return set_error(GS_ERR_ARG, "NULL argument");
     if (!s->work_ctr) return set_error(GS_ERR_STATE, "work counting is off");
-    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 12, cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 14, cudaMemcpyDeviceToHost));
     GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 16));
     return GS_OK;
 }

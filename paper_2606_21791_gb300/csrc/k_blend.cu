@@ -811,7 +811,11 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
     const int lane = threadIdx.x & 31;
     WarpRing& R = rings[threadIdx.x >> 5];
     const uint32_t nheavy = counts[3], ngroups = counts[3] + counts[4];
+    // measurement builds: SM cycles each warp spends per phase (set-up of a group,
+    // the walk, the comparison and reductions)
+    long long t_pro = 0, t_walk = 0, t_epi = 0;
     while (true) {
+        long long c0 = COUNT ? clock64() : 0;
         uint32_t gi = 0;
         if (lane == 0) gi = atomicAdd(&queue[0], 1u);
         gi = __shfl_sync(0xffffffffu, gi, 0);
@@ -901,6 +905,7 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
         const BlendRec* next_src = src_of(kWarpRing - 1);
         unsigned int nev = 0, staged = 0;
         unsigned steps[2] = {0u, 0u};
+        long long c1 = COUNT ? clock64() : 0;
         for (uint32_t c = 0; c < nch; c++) {
             __syncwarp();   // every lane is done with the slot the next issue overwrites
             issue(c + kWarpRing - 1, next_src);
@@ -927,6 +932,7 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
             walk_survivors<COUNT, false>(m, 0, fetch, g, p, nev, base, steps);
             if (__all_sync(0xffffffffu, p.done)) break;
         }
+        long long c2 = COUNT ? clock64() : 0;
         // compare the active pixels with the clean image; every other pixel keeps
         // its clean value (Delta = 0), and the clean image's non-finite pixels are
         // counted once per view at finalize
@@ -995,7 +1001,15 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
                 atomicAdd(&work[9], (unsigned long long)steps[1]);
                 atomicAdd(&work[10], 1ull);
             }
+            t_pro += c1 - c0;
+            t_walk += c2 - c1;
+            t_epi += clock64() - c2;
         }
+    }
+    if (COUNT && lane == 0) {
+        atomicAdd(&work[11], (unsigned long long)t_pro);
+        atomicAdd(&work[12], (unsigned long long)t_walk);
+        atomicAdd(&work[13], (unsigned long long)t_epi);
     }
     cp_async_wait_all();   // leave no copy in flight
 }

@@ -43,6 +43,7 @@ struct Req {
     int status = -1;   // -1 queued, -2 running, >= 0 finished with this gs_status
     std::string err;
     int slot = -1;
+    bool mem_waited = false;   // passed over at least once because its scratch did not fit the budget
 };
 
 struct SceneEntry {
@@ -96,6 +97,7 @@ struct gs_server {
     uint64_t scratch_total = 0;
     bool stop = false;
     uint64_t completed = 0;
+    uint64_t mem_delayed = 0;   // started requests that had waited for budget
 };
 
 namespace {
@@ -170,6 +172,7 @@ void worker(gs_server* sv, int slot_id) {
                 uint64_t add = need > sl.scratch ? need - sl.scratch : 0;
                 if (base + add > sv->budget) {
                     mem_blocked = true;
+                    q->mem_waited = true;
                     continue;
                 }
                 pick = q;
@@ -204,6 +207,7 @@ void worker(gs_server* sv, int slot_id) {
         sv->scratch_total += extra;
         pick->status = -2;
         pick->slot = slot_id;
+        if (pick->mem_waited) sv->mem_delayed++;
         pick->t_start = now_ms(sv->t0);
         gs_scene* scene = e.s;
         lk.unlock();
@@ -344,6 +348,13 @@ gs_status gs_server_stats(gs_server* sv, uint64_t* host_stats) {
     host_stats[2] = sv->scratch_total;
     host_stats[3] = sv->queue.size();
     host_stats[4] = sv->completed;
+    host_stats[5] = sv->mem_delayed;
+    return GS_OK;
+}
+
+gs_status gs_server_now(gs_server* sv, double* now_ms_out) {
+    if (!sv || !now_ms_out) return set_error(GS_ERR_ARG, "bad gs_server_now arguments");
+    *now_ms_out = now_ms(sv->t0);
     return GS_OK;
 }
 

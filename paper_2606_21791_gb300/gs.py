@@ -80,6 +80,7 @@ SIGNATURES = {
     "gs_server_wait": (_i32, [_vp, _u64, _i32, _vp]),
     "gs_server_cancel": (_i32, [_vp, _u64]),
     "gs_server_stats": (_i32, [_vp, _vp]),
+    "gs_server_now": (_i32, [_vp, _vp]),
     "gs_server_destroy": (_i32, [_vp]),
 }
 
@@ -298,12 +299,13 @@ def gs_count_work(scene, enable: bool):
 
 
 def gs_read_work(scene):
-    c = np.zeros(12, dtype=np.uint64)
+    c = np.zeros(14, dtype=np.uint64)
     _check(load_library().gs_read_work(scene, _ptr(c)), "gs_read_work")
     return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2]), "tiles_unchanged": int(c[3]),
             "dropped_stop_key": int(c[4]), "dropped_tile_reach": int(c[5]), "dropped_no_reach": int(c[6]),
             "dropped_pixel_stop": int(c[7]), "warp_steps": int(c[8]), "warp_steps_blending": int(c[9]),
-            "blocks_blended": int(c[10])}
+            "blocks_blended": int(c[10]), "cycles_setup": int(c[11]), "cycles_walk": int(c[12]),
+            "cycles_compare": int(c[13])}
 
 
 def gs_time_kernels(scene, enable: bool):
@@ -398,9 +400,15 @@ def gs_server_cancel(server, ticket: int):
 
 
 def gs_server_stats(server) -> dict:
-    st = np.zeros(5, dtype=np.uint64)
+    st = np.zeros(6, dtype=np.uint64)
     _check(load_library().gs_server_stats(server, _ptr(st)), "gs_server_stats")
-    return dict(zip(("budget", "resident", "scratch", "queued", "completed"), (int(x) for x in st)))
+    return dict(zip(("budget", "resident", "scratch", "queued", "completed", "mem_delayed"), (int(x) for x in st)))
+
+
+def gs_server_now(server) -> float:
+    t = np.zeros(1, dtype=np.float64)
+    _check(load_library().gs_server_now(server, _ptr(t)), "gs_server_now")
+    return float(t[0])
 
 
 def gs_server_destroy(server):

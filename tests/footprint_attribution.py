@@ -115,19 +115,25 @@ def attribute(G, h, scene, cams, flips, g_fp, o_fp, fpv=1, guard=-1, mask=0, box
                 if (v, j) not in jobs:
                     continue
                 img_o, mg_o = jobs[(v, j)].result()
-                dg = change(imgs_g[k], clean_g[k])
-                do = change(img_o, clean_o[j][0])
-                fg, fo = dg > THR, do > THR
-                assert int(fg.sum()) == int(g_fp[v, j]), (v, k, int(fg.sum()), int(g_fp[v, j]))
-                assert int(fo.sum()) == int(o_fp[v, j]), (v, k, int(fo.sum()), int(o_fp[v, j]))
-                diff = fg != fo
-                near_d = np.abs(do.astype(np.float64) - float(THR)) <= MARGIN
-                mc = clean_o[j][1]
-                near_a = np.minimum(mg_o[..., 0], mc[..., 0]) <= MARGIN
-                near_s = np.minimum(mg_o[..., 1], mc[..., 1]) <= MARGIN
-                res["pixels"] += int(diff.sum())
-                res["delta"] += int((diff & near_d).sum())
-                res["alpha"] += int((diff & ~near_d & near_a).sum())
-                res["stop"] += int((diff & ~near_d & ~near_a & near_s).sum())
-                res["unexplained"] += int((diff & ~near_d & ~near_a & ~near_s).sum())
+                c = classify(imgs_g[k], clean_g[k], img_o, mg_o, clean_o[j][0], clean_o[j][1])
+                assert c["gpu_footprint"] == int(g_fp[v, j]), (v, k, c, int(g_fp[v, j]))
+                assert c["oracle_footprint"] == int(o_fp[v, j]), (v, k, c, int(o_fp[v, j]))
+                for key in ("pixels", "delta", "alpha", "stop", "unexplained"):
+                    res[key] += c[key]
     return res
+
+
+def classify(img_g, clean_g, img_o, margins_o, clean_o, clean_margins_o):
+    """Per-pixel footprint decisions of one (variant, view) on both sides and the
+    class of every pixel where they differ (see the module docstring)."""
+    dg = change(img_g, clean_g)
+    do = change(img_o, clean_o)
+    fg, fo = dg > THR, do > THR
+    diff = fg != fo
+    near_d = np.abs(do.astype(np.float64) - float(THR)) <= MARGIN
+    near_a = np.minimum(margins_o[..., 0], clean_margins_o[..., 0]) <= MARGIN
+    near_s = np.minimum(margins_o[..., 1], clean_margins_o[..., 1]) <= MARGIN
+    return {"gpu_footprint": int(fg.sum()), "oracle_footprint": int(fo.sum()), "pixels": int(diff.sum()),
+            "delta": int((diff & near_d).sum()), "alpha": int((diff & ~near_d & near_a).sum()),
+            "stop": int((diff & ~near_d & ~near_a & near_s).sum()),
+            "unexplained": int((diff & ~near_d & ~near_a & ~near_s).sum())}

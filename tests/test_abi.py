@@ -99,6 +99,7 @@ def test_invalid_arguments_are_refused_before_the_device(lib):
         "gs_server_wait": (None, 0, 0, None),
         "gs_server_cancel": (None, 0),
         "gs_server_stats": (None, None),
+        "gs_server_now": (None, None),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == gs.GS_ERR_ARG, name

@@ -28,6 +28,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
     assert d["ms_per_step"] > 0 and d["n_gpus"] == 1 and d["data"] == "synthetic"
     assert d["config"]["workload"] == bench.WORKLOAD and d["config"]["gaussians"] == 2_000_000
+    from paper_2606_21791_gb300 import synth as S
+    _, cams, flips = S.scale_workload(n=1000)
+    assert d["config"] == bench.workload_config(2_000_000, cams, len(flips))   # the GPU arm's config
+    assert "oracle" in d["engine"] and "not extrapolated in pixels" in d["cpu_baseline"]["sample"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
