@@ -481,7 +481,7 @@ def main():
         "gpu_launches": 6 * args.steps,
         "records_gathered_on_rank0": None if gathered is None else int(gathered.shape[0]),
         "mpix_s_effective": value * K_views * Wd * Hd / 1e6,
-        "mpix_s_blended": work["blocks_blended"] * 32 * world / t_total / 1e6,
+        "mpix_s_blended": work["blocks_blended"] * 64 * world / t_total / 1e6,   # 8x8 blocks
         "plain_loop": plain,
         "render_stages": stages,
         "contamination": contam,

@@ -254,7 +254,7 @@ GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
  * test, [6] because no pixel is reached, [7] because every reached pixel
  * stopped before the change, [8] list entries walked by a warp of the
  * dirty-tile blend (survivors of its box cull), [9] of them blended by at
- * least one of its pixels, [10] 8x4 pixel blocks re-blended, and the SM
+ * least one of its pixels, [10] 8x8 pixel blocks re-blended, and the SM
  * cycles the dirty-tile blend's warps spend per phase: [11] setting up a block
  * (work queue, plan item, checkpoint, sublist searches), [12] the walk over
  * its entries, [13] the comparison with the clean image and the reductions

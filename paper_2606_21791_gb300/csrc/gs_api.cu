@@ -629,9 +629,9 @@ static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cud
         }
         GS_TRY(launch_stop_keys(v.ranges, v.tile_stop, v.dk, v.ids, ntiles, v.stop_key, st));
         v.npairs = np;
-        // per (tile, 8x4 block) sublists of the clean lists
+        // per (tile, 8x8 block) sublists of the clean lists
         {
-            const uint64_t nb = (uint64_t)ntiles * 8;
+            const uint64_t nb = (uint64_t)ntiles * kDirtyBlocks;
             uint32_t* counts = nullptr;
             unsigned long long* scratch = nullptr;
             GS_TRY(dmalloc((void**)&v.bl_off, sizeof(uint32_t) * (nb + 1)));

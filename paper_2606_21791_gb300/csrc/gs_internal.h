@@ -16,6 +16,9 @@ namespace gs {
 
 constexpr int kTile = 16;             // render tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;
+// The dirty-tile blend works on 8x8 pixel blocks of a tile (one warp, two pixels
+// per lane); a block is the 8x4 halves w and w + 2 of the natural pixel order.
+constexpr int kDirtyBlocks = kTilePix / 64;
 constexpr int kMaxWords = 59;
 constexpr int kMaxPairs = 8192;       // (variant, view) pairs per dirty-tile launch (one scan block)
 constexpr int kMaxBatch = 2048;       // variants per dirty-tile launch (also <= kMaxPairs / views)
@@ -84,7 +87,8 @@ struct CmpAcc {
 // Screen cells of the contamination masks: an 8x8 grid, cell of pixel (x, y) =
 // (8x / W, 8y / H), bit 8 cy + cx.
 __host__ __device__ inline unsigned long long cell_bit(int x, int y, int W, int H) {
-    const int cx = (int)(((long long)x * 8) / W), cy = (int)(((long long)y * 8) / H);
+    // x < W <= 65535 * 16, so 8 x fits 32 bits
+    const int cx = (int)((unsigned)x * 8u / (unsigned)W), cy = (int)((unsigned)y * 8u / (unsigned)H);
     return 1ull << (cy * 8 + cx);
 }
 // cells met by the pixels of a tile rect (packed x0 | y0 << 16, x1 | y1 << 16, half open in tiles)
@@ -109,7 +113,7 @@ struct ViewPtrs {
     const uint32_t* stop;    // clean stop index of every pixel
     const uint32_t* tile_stop;   // largest stop index of each tile
     const unsigned long long* stop_key;   // (depth bits, id) of the list entry at tile_stop; ~0 if none
-    const uint32_t* bl_off;      // per (tile, 8x4 block): start of its sublist in bl_pos (ntiles * 8 + 1)
+    const uint32_t* bl_off;      // per (tile, 8x8 block): start of its sublist in bl_pos (ntiles * kDirtyBlocks + 1)
     const uint32_t* bl_pos;      // positions (in the tile's list) of the entries whose box meets the block
     const BlendRec* bl_rec;      // their records, same order
     const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
@@ -176,7 +180,7 @@ struct ViewState {
     uint32_t* stop = nullptr;        // [H*W] list index that stopped each clean pixel
     uint32_t* tile_stop = nullptr;   // [ntiles] largest stop index in each tile
     unsigned long long* stop_key = nullptr;   // [ntiles] (depth bits << 32 | id) of the entry at tile_stop (~0: none)
-    uint32_t* bl_off = nullptr;      // [ntiles * 8 + 1] start of each (tile, 8x4 block) sublist in bl_pos
+    uint32_t* bl_off = nullptr;      // [ntiles * kDirtyBlocks + 1] start of each (tile, 8x8 block) sublist in bl_pos
     uint32_t* bl_pos = nullptr;      // list positions whose box meets the block, ascending per sublist
     BlendRec* bl_rec = nullptr;      // the records of those entries, in the same order (streamed by the blend)
     float4* ck = nullptr;            // clean-blend checkpoints [total][256 pixels]
@@ -257,7 +261,7 @@ struct gs_scene {
     unsigned int* queue = nullptr;
     void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
     uint2* cand = nullptr;                  // candidate tiles of the plan's first pass [plan_cap]
-    uint32_t* groups = nullptr;             // 8x4 pixel blocks to re-blend, (item << 3) | block [8 * plan_cap]
+    uint32_t* groups = nullptr;             // 8x8 pixel blocks to re-blend, (item << 3) | block [8 * plan_cap]
     gs::SsimBufs ssim{};                    // dirty-tile SSIM buffers (allocated on first use, else NULL)
     uint64_t plan_cap = 0;
     unsigned int* clean_nonfin = nullptr;   // [K] non-finite pixels of each clean view

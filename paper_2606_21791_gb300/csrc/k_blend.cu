@@ -105,6 +105,10 @@ __device__ __forceinline__ void pix_of(int tile_x, int tile_y, int u, int& px, i
     py = tile_y * kTile + (w >> 1) * 4 + (l >> 3);
 }
 
+// First (upper) 8x4 half, in the natural pixel order, of 8x8 block b of a tile;
+// the lower half is block_half(b) + 2.
+__host__ __device__ constexpr int block_half(int b) { return (b & 1) + 4 * (b >> 1); }
+
 // 2^x (hardware approximation, flushes subnormal results to zero)
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -166,6 +170,27 @@ struct EntryQ {
     float cc, opac, r, g, b;
 };
 
+// One front-to-back step of an entry at one pixel, alpha already computed (ok:
+// the blend takes the entry there; live: the pixel has not stopped): alpha
+// capped at 0.99 (NaN kept), stop when T would drop below 1e-4, else
+// C += colour * alpha * T.  Every operation is rounded on its own, so each
+// kernel that inlines it computes the same bits.  Returns whether the pixel
+// stopped at this entry.
+__device__ __forceinline__ bool apply_entry(Pix& p, bool live, bool ok, float a, float cr, float cg, float cb) {
+    const bool act = live && ok;
+    const float al = a > 0.99f ? 0.99f : a;   // keeps NaN
+    const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, al));
+    const bool stop_here = act && Tn < 1e-4f;
+    const bool upd = act && !(Tn < 1e-4f);
+    const float w = __fmul_rn(al, p.T);
+    p.c0 = upd ? __fmaf_rn(cr, w, p.c0) : p.c0;
+    p.c1 = upd ? __fmaf_rn(cg, w, p.c1) : p.c1;
+    p.c2 = upd ? __fmaf_rn(cb, w, p.c2) : p.c2;
+    p.T = upd ? Tn : p.T;
+    p.done = p.done || stop_here;
+    return stop_here;
+}
+
 // Walk the survivors m (bit i: entry c + i) in list order for this lane's pixel.
 // steps (measurement builds only): [0] entries walked by the warp, [1] of them
 // blended by at least one lane.
@@ -196,19 +221,9 @@ __device__ __forceinline__ void walk_survivors(unsigned m, int c, const Fetch& f
         for (int k = 0; k < kAlphaGroup; k++) {
             const bool live = v[k] && !p.done;
             if (COUNT) nev += live ? 1u : 0u;
-            const bool act = live && ok[k];
-            if (COUNT && steps) steps[1] += __any_sync(0xffffffffu, act) ? 1u : 0u;
-            const float al = a[k] > 0.99f ? 0.99f : a[k];   // keeps NaN
-            const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, al));
-            const bool stop_here = act && Tn < 1e-4f;
-            const bool upd = act && !(Tn < 1e-4f);
-            const float w = __fmul_rn(al, p.T);
-            p.c0 = upd ? __fmaf_rn(cr[k], w, p.c0) : p.c0;
-            p.c1 = upd ? __fmaf_rn(cg[k], w, p.c1) : p.c1;
-            p.c2 = upd ? __fmaf_rn(cb[k], w, p.c2) : p.c2;
-            p.T = upd ? Tn : p.T;
+            if (COUNT && steps) steps[1] += __any_sync(0xffffffffu, live && ok[k]) ? 1u : 0u;
+            const bool stop_here = apply_entry(p, live, ok[k], a[k], cr[k], cg[k], cb[k]);
             if (TRACK) p.stop = stop_here ? base + (uint32_t)e[k] : p.stop;
-            p.done = p.done || stop_here;
         }
     }
 }
@@ -687,14 +702,14 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
             if (COUNT) (cut == 0xffffffffu ? drop_reach : drop_stop)++;
             continue;
         }
-        // the item's 7 16-byte parts, one per lane; one group per 8x4 block with an
+        // the item's 7 16-byte parts, one per lane; one group per 8x8 block with an
         // active pixel, (slot << 3) | block.  Groups of tiles with a long walk
         // ahead (from the checkpoint the blend resumes at) go to the front of the
         // group array and are blended first, the others to the back.
         uint32_t word = 0;
 #pragma unroll
-        for (int q = 0; q < kBT / 32; q++) word = lane == q ? reach[q] : word;
-        const unsigned gm = __ballot_sync(0xffffffffu, lane < kBT / 32 && word != 0u);
+        for (int b = 0; b < kDirtyBlocks; b++) word = lane == b ? reach[block_half(b)] | reach[block_half(b) + 2] : word;
+        const unsigned gm = __ballot_sync(0xffffffffu, lane < kDirtyBlocks && word != 0u);
         const uint32_t Lm = (rg.y - rg.x) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         const uint32_t walk = Lm - min(cut / (uint32_t)kCkStride, v.ck_cnt[tile]) * (uint32_t)kCkStride;
         const bool heavy = walk >= (uint32_t)kHeavyWalk;
@@ -745,8 +760,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gmem) : "memory");
 }
 
-// Dirty-tile blend, one warp per work unit: an 8x4 pixel block of a planned
-// tile that holds an active pixel (the plan's groups, (item << 3) | block).
+// Dirty-tile blend, one warp per work unit: an 8x8 pixel block of a planned
+// tile that holds an active pixel (the plan's groups, (item << 3) | block), two
+// pixels per lane (one column, four rows apart, so the exponent's x terms are
+// shared).
 // The warp streams the tile's merged list -- the clean list with the old entry
 // removed and the corrupted record inserted -- through a ring of kWarpRing
 // chunks of 32 entries in shared memory, filled by cp.async gathers issued
@@ -799,8 +816,78 @@ __device__ __forceinline__ void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// walk_survivors for two pixels per lane in the same column (pixel centres
+// (pxc, pyA) and (pxc, pyB)): the x offset and the terms of the Gaussian's
+// exponent that depend on it alone are computed once for both, each rounded as
+// gauss_power rounds it, so every pixel gets the bits of the one-pixel walk.
+template <bool COUNT, class Fetch>
+__device__ __forceinline__ void walk_survivors2(unsigned m, const Fetch& fetch, float pxc, float pyA, float pyB, Pix& pA,
+                                                Pix& pB, unsigned int& nev, unsigned* steps) {
+    if (COUNT) steps[0] += __popc(m);
+    while (m) {
+        int e[kAlphaGroup];
+        bool v[kAlphaGroup], okA[kAlphaGroup], okB[kAlphaGroup];
+        float aA[kAlphaGroup], aB[kAlphaGroup], cr[kAlphaGroup], cg[kAlphaGroup], cb[kAlphaGroup];
+#pragma unroll
+        for (int k = 0; k < kAlphaGroup; k++) {
+            v[k] = m != 0u;
+            e[k] = v[k] ? __ffs(m) - 1 : 0;
+            m &= m - 1u;
+        }
+#pragma unroll
+        for (int k = 0; k < kAlphaGroup; k++) {
+            const EntryQ q = fetch(e[k]);
+            const float dx = __fsub_rn(q.q0.x, pxc);
+            const float t1 = __fmul_rn(__fmul_rn(q.q0.z, dx), dx);
+            const float bdx = __fmul_rn(q.q0.w, dx);
+            const float dyA = __fsub_rn(q.q0.y, pyA), dyB = __fsub_rn(q.q0.y, pyB);
+            const float hA = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyA), dyA)));
+            const float hB = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyB), dyB)));
+            const float powA = __fsub_rn(hA, __fmul_rn(bdx, dyA));
+            const float powB = __fsub_rn(hB, __fmul_rn(bdx, dyB));
+            aA[k] = q.opac * ex2_approx(__fmul_rn(powA, kLog2e));
+            aB[k] = q.opac * ex2_approx(__fmul_rn(powB, kLog2e));
+            okA[k] = !(powA > 0.0f) && !(aA[k] < 1.0f / 255.0f);
+            okB[k] = !(powB > 0.0f) && !(aB[k] < 1.0f / 255.0f);
+            cr[k] = q.r;
+            cg[k] = q.g;
+            cb[k] = q.b;
+        }
+#pragma unroll
+        for (int k = 0; k < kAlphaGroup; k++) {
+            const bool liveA = v[k] && !pA.done, liveB = v[k] && !pB.done;
+            if (COUNT) {
+                nev += (liveA ? 1u : 0u) + (liveB ? 1u : 0u);
+                steps[1] += __any_sync(0xffffffffu, (liveA && okA[k]) || (liveB && okB[k])) ? 1u : 0u;
+            }
+            apply_entry(pA, liveA, okA[k], aA[k], cr[k], cg[k], cb[k]);
+            apply_entry(pB, liveB, okB[k], aB[k], cr[k], cg[k], cb[k]);
+        }
+    }
+}
+
+// One pixel's part of a block's comparison: fixed-point squared error, peak
+// difference, footprint / non-finite / clean-non-finite flags and screen cell.
+struct BlockCmp {
+    unsigned long long fx = 0ull, cells = 0ull;
+    float m = 0.0f;
+    unsigned foot = 0u, bad = 0u, clean_bad = 0u;
+};
+
+__device__ __forceinline__ void block_cmp_add(BlockCmp& b, bool active, float v0, float v1, float v2, const float* c,
+                                              int px, int py, int W, int H) {
+    if (!active) return;
+    const PixCmp r = pixel_compare(v0, v1, v2, c);
+    b.fx += r.fx;
+    b.m = fmaxf(b.m, r.m);
+    b.foot += r.foot ? 1u : 0u;
+    b.bad += r.nonfin ? 1u : 0u;
+    b.clean_bad += !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2])) ? 1u : 0u;
+    if (r.foot) b.cells |= cell_bit(px, py, W, H);
+}
+
 template <bool COUNT>
-__global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* __restrict__ views, int K,
+__global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* __restrict__ views, int K,
                                                               const PlanItem* __restrict__ plan,
                                                               const uint32_t* __restrict__ groups, uint32_t gcap,
                                                               const unsigned int* __restrict__ counts,
@@ -823,45 +910,57 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
         // heavy groups first (front of the array), then the light ones (from the back)
         const uint32_t code = groups[gi < nheavy ? gi : gcap - 1u - (gi - nheavy)];
         const PlanItem* it = &plan[code >> 3];
-        const int w = (int)(code & 7u);
+        const int b = (int)(code & 7u);            // 8x8 block of the tile
+        const int wA = block_half(b), wB = wA + 2;   // its upper and lower 8x4 halves
         const uint4 f5 = reinterpret_cast<const uint4*>(it)[5];   // bk, tile, s, e
         const uint4 f6 = reinterpret_cast<const uint4*>(it)[6];   // pp, ins, cut, flags
-        const uint32_t amask = it->mask[w];
+        const uint32_t amA = it->mask[wA], amB = it->mask[wB];
         const int bk = (int)f5.x;
-        const uint32_t tile = f5.y, s0 = f5.z, pp = f6.x, ins = f6.y, cut = f6.z;
+        const uint32_t tile = f5.y, pp = f6.x, ins = f6.y, cut = f6.z;
         const bool has_old = f6.w & 1u, has_new = f6.w & 2u;
-        const uint32_t L = (f5.w - f5.z) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         const ViewPtrs& v = views[bk % K];
         const int tx = (int)(tile % (uint32_t)v.tiles_x), ty = (int)(tile / (uint32_t)v.tiles_x);
-        PixGeo g;
-        pix_of(tx, ty, w * 32 + lane, g.px, g.py);
-        g.pxc = (float)g.px + 0.5f;
-        g.pyc = (float)g.py + 0.5f;
-        const bool active = (amask >> lane) & 1u;   // decided by the plan (inside the image)
-        g.inside = active;
-        g.wx0 = (float)__reduce_min_sync(0xffffffffu, active ? g.px : 0x7fffffff) + 0.5f;
-        g.wx1 = (float)__reduce_max_sync(0xffffffffu, active ? g.px : -1) + 0.5f;
-        g.wy0 = (float)__reduce_min_sync(0xffffffffu, active ? g.py : 0x7fffffff) + 0.5f;
-        g.wy1 = (float)__reduce_max_sync(0xffffffffu, active ? g.py : -1) + 0.5f;
-        Pix p{1.0f, 0.0f, 0.0f, 0.0f, !active, 0u};
+        // lane: pixel A of the upper half, pixel B four rows below it
+        int px, pyA;
+        pix_of(tx, ty, wA * 32 + lane, px, pyA);
+        const int pyB = pyA + 4;
+        const float pxc = (float)px + 0.5f, pycA = (float)pyA + 0.5f, pycB = (float)pyB + 0.5f;
+        const bool actA = (amA >> lane) & 1u, actB = (amB >> lane) & 1u;   // decided by the plan (inside the image)
+        const bool act = actA || actB;
+        PixGeo g;   // the box of the block's active pixel centres
+        g.wx0 = (float)__reduce_min_sync(0xffffffffu, act ? px : 0x7fffffff) + 0.5f;
+        g.wx1 = (float)__reduce_max_sync(0xffffffffu, act ? px : -1) + 0.5f;
+        g.wy0 = (float)__reduce_min_sync(0xffffffffu, actA ? pyA : (actB ? pyB : 0x7fffffff)) + 0.5f;
+        g.wy1 = (float)__reduce_max_sync(0xffffffffu, actB ? pyB : (actA ? pyA : -1)) + 0.5f;
+        Pix pA{1.0f, 0.0f, 0.0f, 0.0f, !actA, 0u}, pB{1.0f, 0.0f, 0.0f, 0.0f, !actB, 0u};
         // The merged list equals the clean list before `cut`, so an active pixel
         // (not stopped before `cut`) can resume from the clean blend's state at the
         // last checkpoint at or before `cut`.
         const uint32_t cstar = min(cut / (uint32_t)kCkStride, v.ck_cnt[tile]);
         const uint32_t start = cstar * (uint32_t)kCkStride;
-        if (active && cstar > 0) {
-            const float4 st = v.ck[(size_t)(v.ck_off[tile] + cstar - 1) * kBT + (uint32_t)(w * 32 + lane)];
-            p.T = st.x;
-            p.c0 = st.y;
-            p.c1 = st.z;
-            p.c2 = st.w;
+        if (cstar > 0) {
+            const float4* ckt = v.ck + (size_t)(v.ck_off[tile] + cstar - 1) * kBT;
+            if (actA) {
+                const float4 st = ckt[wA * 32 + lane];
+                pA.T = st.x;
+                pA.c0 = st.y;
+                pA.c1 = st.z;
+                pA.c2 = st.w;
+            }
+            if (actB) {
+                const float4 st = ckt[wB * 32 + lane];
+                pB.T = st.x;
+                pB.c0 = st.y;
+                pB.c1 = st.z;
+                pB.c2 = st.w;
+            }
         }
         // This block's sublist of the clean list (the entries whose box meets the
         // block, positions ascending) from `start`, without the old entry and with the
         // corrupted record at its place: every entry outside the sublist fails the
         // cull below anyway.
-        const uint32_t boff = v.bl_off[(size_t)tile * 8 + w];
-        const uint32_t blen = v.bl_off[(size_t)tile * 8 + w + 1] - boff;
+        const uint32_t boff = v.bl_off[(size_t)tile * kDirtyBlocks + b];
+        const uint32_t blen = v.bl_off[(size_t)tile * kDirtyBlocks + b + 1] - boff;
         const uint32_t* B = v.bl_pos + boff;
         const uint32_t k0 = warp_lower_bound_u32(B, 0, blen, start);
         bool has_kpp = false;
@@ -879,7 +978,6 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
         }
         const uint32_t Lb = (blen - k0) - (has_kpp ? 1u : 0u) + (has_new ? 1u : 0u);
         const uint32_t nch = (Lb + 31u) / 32u;
-        (void)L;
         // source of this lane's entry in chunk c (NULL past the end)
         auto src_of = [&](uint32_t c) -> const BlendRec* {
             const uint32_t m = c * 32u + (uint32_t)lane;
@@ -918,54 +1016,57 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
             staged += (uint32_t)cnt;
             bool pass = false;
             if (lane < cnt) {
-                const float4 a = R.q[slot][0][lane], b = R.q[slot][1][lane];
+                const float4 a = R.q[slot][0][lane], bb = R.q[slot][1][lane];
                 // the entry's box [mx - ex, mx + ex] x [my - ey, my + ey] against the block's,
                 // then the conservative conic test over the block's pixel centres
-                pass = !(a.x + b.z < g.wx0 || a.x - b.z > g.wx1 || a.y + b.w < g.wy0 || a.y - b.w > g.wy1) &&
-                       rect_reachable(a.x, a.y, a.z, a.w, b.x, b.y, g.wx0, g.wx1, g.wy0, g.wy1);
+                pass = !(a.x + bb.z < g.wx0 || a.x - bb.z > g.wx1 || a.y + bb.w < g.wy0 || a.y - bb.w > g.wy1) &&
+                       rect_reachable(a.x, a.y, a.z, a.w, bb.x, bb.y, g.wx0, g.wx1, g.wy0, g.wy1);
             }
             const unsigned m = __ballot_sync(0xffffffffu, pass);
             auto fetch = [&](int e) {
                 const float4 q1 = R.q[slot][1][e], q2 = R.q[slot][2][e];
                 return EntryQ{R.q[slot][0][e], q1.x, q1.y, q2.x, q2.y, q2.z};
             };
-            walk_survivors<COUNT, false>(m, 0, fetch, g, p, nev, base, steps);
-            if (__all_sync(0xffffffffu, p.done)) break;
+            walk_survivors2<COUNT>(m, fetch, pxc, pycA, pycB, pA, pB, nev, steps);
+            if (__all_sync(0xffffffffu, pA.done && pB.done)) break;
         }
         long long c2 = COUNT ? clock64() : 0;
         // compare the active pixels with the clean image; every other pixel keeps
         // its clean value (Delta = 0), and the clean image's non-finite pixels are
         // counted once per view at finalize
-        const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
-        if (sb.deltas) {   // dirty-tile SSIM: keep the block's new values (delta index = work-queue index)
+        const float a0 = __fadd_rn(pA.c0, pA.T), a1 = __fadd_rn(pA.c1, pA.T), a2 = __fadd_rn(pA.c2, pA.T);
+        const float b0 = __fadd_rn(pB.c0, pB.T), b1 = __fadd_rn(pB.c1, pB.T), b2 = __fadd_rn(pB.c2, pB.T);
+        const float* cA = v.clean + ((size_t)pyA * v.W + px) * 3;
+        const float* cB = v.clean + ((size_t)pyB * v.W + px) * 3;
+        if (sb.deltas) {   // dirty-tile SSIM: keep the block's new values, two 32-pixel delta units per group
             const uint32_t slot = code >> 3;
-            if (gi < sb.delta_cap && slot < sb.slot_cap) {
-                if (active) sb.deltas[(size_t)gi * 32 + lane] = make_float4(v0, v1, v2, 0.0f);
-                if (lane == 0) sb.slot_group[(size_t)slot * 8 + w] = gi;
-                // where the changed pixels are: which neighbouring tiles their SSIM windows reach
-                bool ch = false;
-                if (active) {
-                    const float* c = v.clean + ((size_t)g.py * v.W + g.px) * 3;
-                    ch = __float_as_uint(v0) != __float_as_uint(c[0]) || __float_as_uint(v1) != __float_as_uint(c[1]) ||
-                         __float_as_uint(v2) != __float_as_uint(c[2]);
+            if (2u * gi + 1u < sb.delta_cap && slot < sb.slot_cap) {
+                if (actA) sb.deltas[(size_t)(2u * gi) * 32 + lane] = make_float4(a0, a1, a2, 0.0f);
+                if (actB) sb.deltas[(size_t)(2u * gi + 1u) * 32 + lane] = make_float4(b0, b1, b2, 0.0f);
+                if (lane == 0) {
+                    sb.slot_group[(size_t)slot * 8 + wA] = 2u * gi;
+                    sb.slot_group[(size_t)slot * 8 + wB] = 2u * gi + 1u;
                 }
-                const int lx = g.px % kTile, ly = g.py % kTile;
-                const unsigned f = ch ? (16u | (lx < 5 ? 1u : 0u) | (lx > kTile - 6 ? 2u : 0u) | (ly < 5 ? 4u : 0u) |
-                                         (ly > kTile - 6 ? 8u : 0u))
-                                      : 0u;
+                // where the changed pixels are: which neighbouring tiles their SSIM windows reach
+                auto edge = [&](bool a, int x, int y, float n0, float n1, float n2, const float* c) -> unsigned {
+                    const bool ch = a && (__float_as_uint(n0) != __float_as_uint(c[0]) ||
+                                          __float_as_uint(n1) != __float_as_uint(c[1]) ||
+                                          __float_as_uint(n2) != __float_as_uint(c[2]));
+                    const int lx = x % kTile, ly = y % kTile;
+                    return ch ? (16u | (lx < 5 ? 1u : 0u) | (lx > kTile - 6 ? 2u : 0u) | (ly < 5 ? 4u : 0u) |
+                                 (ly > kTile - 6 ? 8u : 0u))
+                              : 0u;
+                };
+                const unsigned f = edge(actA, px, pyA, a0, a1, a2, cA) | edge(actB, px, pyB, b0, b1, b2, cB);
                 const unsigned fo = __reduce_or_sync(0xffffffffu, f);
                 if (lane == 0 && fo) atomicOr(&sb.slot_flags[slot], fo);
             } else if (lane == 0) {
                 atomicOr(sb.overflow, 1u);
             }
         }
-        PixCmp r{0ull, 0.0f, false, false};
-        bool clean_bad = false;
-        if (active) {
-            const float* c = v.clean + ((size_t)g.py * v.W + g.px) * 3;
-            r = pixel_compare(v0, v1, v2, c);
-            clean_bad = !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]));
-        }
+        BlockCmp r;
+        block_cmp_add(r, actA, a0, a1, a2, cA, px, pyA, v.W, v.H);
+        block_cmp_add(r, actB, b0, b1, b2, cB, px, pyB, v.W, v.H);
         unsigned long long fx = r.fx;
         float mx = r.m;
 #pragma unroll
@@ -973,13 +1074,13 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
             fx += __shfl_xor_sync(0xffffffffu, fx, o);
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
-        const unsigned nfoot = __popc(__ballot_sync(0xffffffffu, r.foot));
-        const unsigned nbad = __popc(__ballot_sync(0xffffffffu, r.nonfin));
-        const unsigned ncb = __popc(__ballot_sync(0xffffffffu, clean_bad));
+        const unsigned nfoot = __reduce_add_sync(0xffffffffu, r.foot);
+        const unsigned nbad = __reduce_add_sync(0xffffffffu, r.bad);
+        const unsigned ncb = __reduce_add_sync(0xffffffffu, r.clean_bad);
         // screen cells holding a footprint pixel (contamination of a sort-first partition)
-        unsigned long long cells = r.foot ? cell_bit(g.px, g.py, v.W, v.H) : 0ull;
-        cells = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)cells) |
-                ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(cells >> 32)) << 32);
+        const unsigned long long cells =
+            (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)r.cells) |
+            ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(r.cells >> 32)) << 32);
         if (lane == 0) {
             CmpAcc* A = &acc[bk];
             if (cells) atomicOr(&A->reg_actual, cells);
@@ -992,7 +1093,9 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 8) void k_dirty(const ViewPtrs* _
         if (COUNT) {
             const unsigned wn = __reduce_add_sync(0xffffffffu, nev);
             // a tile counts once, on its first group (lowest block with an active pixel)
-            const bool first = __ballot_sync(0xffffffffu, lane < w && it->mask[lane & 7] != 0u) == 0u;
+            const bool first =
+                __ballot_sync(0xffffffffu, lane < b && (it->mask[block_half(lane & 3)] |
+                                                        it->mask[block_half(lane & 3) + 2]) != 0u) == 0u;
             if (lane == 0) {
                 if (wn) atomicAdd(&work[0], (unsigned long long)wn);
                 if (first) atomicAdd(&work[1], 1ull);
@@ -1233,7 +1336,7 @@ void fill_view_ptrs(void* host_dst, const ViewState& vs) {
 }
 
 // ---------------------------------------------------------------------------
-// Per (tile, 8x4 block) sublists of the clean tile lists: the positions of the
+// Per (tile, 8x8 block) sublists of the clean tile lists: the positions of the
 // entries whose box [mx - ex, mx + ex] x [my - ey, my + ey] meets the block's
 // pixel-centre box (the same comparisons as the dirty-tile cull, on a box that
 // contains every active-pixel box of the block, so an entry left out would be
@@ -1248,41 +1351,41 @@ __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __re
     for (int t = warp; t < ntiles; t += nwarps) {
         const uint2 rg = ranges[t];
         const int tx = t % tiles_x, ty = t / tiles_x;
-        uint32_t base[8];
+        uint32_t base[kDirtyBlocks];
 #pragma unroll
-        for (int w = 0; w < 8; w++) base[w] = FILL ? off[(size_t)t * 8 + w] : 0u;
+        for (int b = 0; b < kDirtyBlocks; b++) base[b] = FILL ? off[(size_t)t * kDirtyBlocks + b] : 0u;
         for (uint32_t j0 = 0; j0 < rg.y - rg.x; j0 += 32) {
             const uint32_t j = j0 + (uint32_t)lane;
-            unsigned m8 = 0u;
+            unsigned mb = 0u;
             uint32_t id = 0;
             if (j < rg.y - rg.x) {
                 id = ids[rg.x + j];
                 const float4* r = reinterpret_cast<const float4*>(recs + id);
                 const float4 a = __ldg(r), b = __ldg(r + 1);   // (mx, my, ca, cb), (cc, opac, ex, ey)
 #pragma unroll
-                for (int w = 0; w < 8; w++) {
-                    const float wx0 = (float)(tx * kTile + (w & 1) * 8) + 0.5f, wx1 = wx0 + 7.0f;
-                    const float wy0 = (float)(ty * kTile + (w >> 1) * 4) + 0.5f, wy1 = wy0 + 3.0f;
+                for (int k = 0; k < kDirtyBlocks; k++) {
+                    const float wx0 = (float)(tx * kTile + (k % (kTile / 8)) * 8) + 0.5f, wx1 = wx0 + 7.0f;
+                    const float wy0 = (float)(ty * kTile + (k / (kTile / 8)) * 8) + 0.5f, wy1 = wy0 + 7.0f;
                     const bool pass = !(a.x + b.z < wx0 || a.x - b.z > wx1 || a.y + b.w < wy0 || a.y - b.w > wy1);
-                    m8 |= pass ? (1u << w) : 0u;
+                    mb |= pass ? (1u << k) : 0u;
                 }
             }
 #pragma unroll
-            for (int w = 0; w < 8; w++) {
-                const unsigned bw = __ballot_sync(0xffffffffu, (m8 >> w) & 1u);
-                if (FILL && ((m8 >> w) & 1u)) {
-                    const uint32_t q = base[w] + __popc(bw & ((1u << lane) - 1u));
+            for (int k = 0; k < kDirtyBlocks; k++) {
+                const unsigned bw = __ballot_sync(0xffffffffu, (mb >> k) & 1u);
+                if (FILL && ((mb >> k) & 1u)) {
+                    const uint32_t q = base[k] + __popc(bw & ((1u << lane) - 1u));
                     pos[q] = j;
                     brec[q] = recs[id];
                 }
-                base[w] += (uint32_t)__popc(bw);
+                base[k] += (uint32_t)__popc(bw);
             }
         }
-        if (!FILL && lane < 8) {
+        if (!FILL && lane < kDirtyBlocks) {
             uint32_t c = 0;
 #pragma unroll
-            for (int w = 0; w < 8; w++) c = lane == w ? base[w] : c;
-            counts[(size_t)t * 8 + lane] = c;
+            for (int k = 0; k < kDirtyBlocks; k++) c = lane == k ? base[k] : c;
+            counts[(size_t)t * kDirtyBlocks + lane] = c;
         }
     }
 }
