@@ -319,10 +319,12 @@ def main():
     if args.batch > 0:
         G.gs_set_batch(h, args.batch)
         B = args.batch
+        tile = G.gs_get_tile(h)
         log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; batch B={B} (set)")
     else:
-        B, us_per = G.gs_autotune(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
-        log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned batch B={B} ({us_per:.1f} us/variant)")
+        tile, B, us_per = G.gs_autotune_tile(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
+        log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned tile {tile[0]}x{tile[1]}, batch B={B} "
+            f"({us_per:.2f} us/variant)")
 
     out = G.device_bytes(B * K_views * 24, dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -475,7 +477,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(scene.n, cams, nflips, world),
-        "engine": {"name": ENGINE, "batch": B, "batch_from": "set" if args.batch > 0 else "autotuner"},
+        "engine": {"name": ENGINE, "batch": B, "tile": f"{tile[0]}x{tile[1]}",
+                   "batch_and_tile_from": "set" if args.batch > 0 else "autotuner (tiles 16x16, 8x8, 32x8; batches 8-2048)"},
         "e2e": e2e,
         # per step: injector, item scan, two plan kernels, dirty-tile blend, finalise
         "gpu_launches": 6 * args.steps,

@@ -241,7 +241,8 @@ GS_API gs_status gs_inject_and_render_regions(gs_scene* scene, const gs_flip* de
  * unchanged) and bit-identical to gs_ssim on the full re-rendered frame.  The
  * SSIM buffers (about 270 MB plus 16 B per (variant, view, tile)) are
  * allocated on first use; GS_ERR_CAPACITY if a batch has more dirty tiles
- * than they hold (retry with a smaller gs_set_batch). */
+ * than they hold (retry with a smaller gs_set_batch).  The SSIM needs the
+ * default 16 x 16 render tiles (GS_ERR_STATE with another gs_set_tile shape). */
 GS_API gs_status gs_inject_and_render_ex(gs_scene* scene, const gs_flip* dev_flips, int B, int guard_mode,
                                          uint64_t word_mask, gs_result* dev_out, uint64_t* dev_regions,
                                          double* dev_ssim, void* stream);
@@ -288,6 +289,26 @@ GS_API gs_status gs_set_batch(gs_scene* scene, int batch);
  * Synchronises the stream. */
 GS_API gs_status gs_autotune(gs_scene* scene, const gs_flip* dev_flips, int count, int guard_mode, uint64_t word_mask,
                              int* best_batch, float* best_us_per_variant, void* stream);
+/* Render tile shape of a scene: tile_w x tile_h pixels, each in {8, 16, 32},
+ * 64 <= tile_w * tile_h <= 256 (default 16 x 16; else GS_ERR_ARG).  The tiles
+ * are the bins of the tile lists and the unit of the dirty-tile engine (Sec. 6
+ * of the paper names tile binning among the renderer's stages; the shape
+ * itself is the renderer's, not the paper's).  Every later render, campaign
+ * and plain-loop call uses it; if gs_set_views was called, its clean per-view
+ * state is rebuilt for the new tiles (same errors as gs_set_views; on failure
+ * the views are dropped).  Images and records do not depend on the shape
+ * except through the binning: pixels are blended front to back over the same
+ * primitives whatever tile holds them. */
+GS_API gs_status gs_set_tile(gs_scene* scene, int tile_w, int tile_h, void* stream);
+GS_API gs_status gs_get_tile(gs_scene* scene, int* tile_w, int* tile_h);
+/* Autotuner over tile shape and batch: for each of the shapes 16 x 16, 8 x 8
+ * and 32 x 8 it rebuilds the views (gs_set_tile) and runs gs_autotune over
+ * dev_flips[0, count); the scene keeps the fastest (shape, batch), which is
+ * returned with its time per variant (us, may be NULL).  On an error the scene
+ * is put back to its previous shape and batch.  Synchronises the stream. */
+GS_API gs_status gs_autotune_tile(gs_scene* scene, const gs_flip* dev_flips, int count, int guard_mode,
+                                  uint64_t word_mask, int* best_tile_w, int* best_tile_h, int* best_batch,
+                                  float* best_us_per_variant, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points (for stage-isolated checks).
@@ -299,7 +320,9 @@ GS_API gs_status gs_autotune(gs_scene* scene, const gs_flip* dev_flips, int coun
  * sorted by (tile, depth, primitive) via a stable LSD radix sort.  If the total
  * exceeds ids_cap, *host_total is set and GS_ERR_CAPACITY returned.  Blocks
  * until done.
- * gs_blend_lists: blend given records and lists into H*W*3 float32.
+ * gs_blend_lists: blend given records and lists into H*W*3 float32.  Both
+ * work on 16 x 16 tiles (gs_preprocess uses the scene's tile shape for the
+ * records' tile rects).
  * ------------------------------------------------------------------------- */
 GS_API gs_status gs_preprocess(gs_scene* scene, const gs_camera* host_cam, gs_record* dev_out, void* stream);
 GS_API gs_status gs_bin_tiles(const float* dev_depth, const int32_t* dev_rects, uint64_t n, int tiles_x, int tiles_y,

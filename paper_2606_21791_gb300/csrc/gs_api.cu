@@ -38,12 +38,12 @@ size_t view_ptrs_size();
 gs_status launch_stop_keys(const uint2* ranges, const uint32_t* tile_stop, const uint32_t* dk, const uint32_t* ids,
                            int ntiles, unsigned long long* out, cudaStream_t st);
 void fill_view_ptrs(void* host_dst, const ViewState& vs);
-gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int ntiles, int tiles_x,
+gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                         uint32_t* counts, const uint32_t* off, uint32_t* pos, BlendRec* brec, cudaStream_t st);
 gs_status launch_exclusive_scan(const uint32_t* in, uint64_t n, uint32_t* out, unsigned long long* scratch,
                                 unsigned long long* total, cudaStream_t st);
 uint64_t scan_scratch_len(uint64_t n);
-gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
                                   const uint32_t* ck_cnt, unsigned int* clean_nonfin, cudaStream_t st);
 int ck_stride_value();
@@ -66,9 +66,10 @@ gs_status cuda_error(cudaError_t e, const char* what) {
     return set_error(GS_ERR_CUDA, m);
 }
 
-// the camera sizes and focal lengths the kernels accept (tile coordinates fit 16 bits)
+// the camera sizes and focal lengths the kernels accept (tile coordinates fit 16
+// bits for the smallest tile edge, 8)
 bool valid_camera(const gs_camera& c) {
-    return c.width > 0 && c.height > 0 && c.width <= 65535 * kTile && c.height <= 65535 * kTile && c.fx > 0 &&
+    return c.width > 0 && c.height > 0 && c.width <= 65535 * 8 && c.height <= 65535 * 8 && c.fx > 0 &&
            c.fy > 0 && std::isfinite(c.fx) && std::isfinite(c.fy);
 }
 
@@ -254,7 +255,7 @@ gs_status ensure_batch_buffers(gs_scene* s, int B, int fpv) {
     if (s->plan_cap >= (1ull << 29)) return set_error(GS_ERR_CAPACITY, "too many dirty tiles per batch for this view size");
     GS_TRY(dmalloc(&s->plan, plan_item_size() * s->plan_cap));
     GS_TRY(dmalloc((void**)&s->cand, sizeof(uint2) * s->plan_cap));
-    GS_TRY(dmalloc((void**)&s->groups, sizeof(uint32_t) * (kTilePix / 32) * s->plan_cap));
+    GS_TRY(dmalloc((void**)&s->groups, sizeof(uint32_t) * kDirtyBlocks * s->plan_cap));
     s->cap_B = cb;
     s->cap_flips = cf;
     return GS_OK;
@@ -286,7 +287,7 @@ gs_status enqueue_dirty(gs_scene* s, int B, int guard_mode, uint64_t mask, bool 
     if (s->ev_k0) GS_CUDA(cudaEventRecordWithFlags(s->ev_k0, st, cudaEventRecordExternal));
     const SsimBufs sb = ssim ? s->ssim : SsimBufs{};
     GS_TRY(launch_dirty_blend(s->dev_views, s->desc, s->item_off, B * K, K, s->plan, s->cand, s->groups,
-                              (uint32_t)((kTilePix / 32) * s->plan_cap), s->acc, s->queue, s->work_ctr, s->ev_kp, sb,
+                              (uint32_t)(kDirtyBlocks * s->plan_cap), s->acc, s->queue, s->work_ctr, s->ev_kp, sb,
                               st));
     if (s->ev_k1) GS_CUDA(cudaEventRecordWithFlags(s->ev_k1, st, cudaEventRecordExternal));
     GS_TRY(launch_finalize_dirty(s->acc, B * K, s->res_stage, s->clean_nonfin, K, st));
@@ -536,11 +537,11 @@ gs_status gs_render(gs_scene* s, const gs_camera* host_cams, int K, float* dev_r
     size_t off = 0;
     for (int k = 0; k < K; k++) {
         if (!valid_camera(host_cams[k])) return set_error(GS_ERR_ARG, "invalid camera");
-        DevCamera cam = make_dev_camera(host_cams[k]);
+        DevCamera cam = make_dev_camera(host_cams[k], s->tile_w, s->tile_h);
         uint32_t* ids = nullptr;
         uint64_t np = 0;
         GS_TRY(render_lists_sized(s, s->work, cam, &ids, &np, st, ev));
-        GS_TRY(launch_blend_image(s->work.recs, ids, s->work.ranges, cam.W, cam.H, dev_rgb + off, st));
+        GS_TRY(launch_blend_image(s->work.recs, ids, s->work.ranges, cam, dev_rgb + off, st));
         if (ev) GS_CUDA(cudaEventRecord(ev[3], st));
         s->render_pairs = np;
         off += (size_t)cam.W * cam.H * 3;
@@ -577,7 +578,7 @@ static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cud
     int max_tiles = 0;
     for (int k = 0; k < K; k++) {
         ViewState& v = s->views[k];
-        v.cam = make_dev_camera(host_cams[k]);
+        v.cam = make_dev_camera(host_cams[k], s->tile_w, s->tile_h);
         dcams[k] = v.cam;
         int ntiles = v.cam.tiles_x * v.cam.tiles_y;
         uint32_t* ids = nullptr;
@@ -596,8 +597,8 @@ static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cud
         GS_CUDA(cudaMemcpyAsync(v.rects, s->work.rects, sizeof(uint2) * s->n, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ids, ids, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, st));
         GS_CUDA(cudaMemcpyAsync(v.ranges, s->work.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
-        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop,
-                                       nullptr, nullptr, nullptr, s->clean_nonfin + k, st));
+        GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam, v.clean, v.stop, v.tile_stop, nullptr, nullptr,
+                                       nullptr, s->clean_nonfin + k, st));
         GS_TRY(launch_gather_depth(v.recs, v.ids, np, v.dk, st));
         // checkpoints of the clean blend: per tile, every ck_stride list entries up to
         // (before) the tile's last stop index, at most ck_max_per_tile
@@ -618,20 +619,21 @@ static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cud
             }
             if (total >= 0xffffffffull) return set_error(GS_ERR_CAPACITY, "too many blend checkpoints");
             v.ck_total = total;
-            GS_TRY(dmalloc((void**)&v.ck, sizeof(float4) * kTilePix * std::max<uint64_t>(total, 1)));
+            GS_TRY(dmalloc((void**)&v.ck, sizeof(float4) * (size_t)(v.cam.tile_w * v.cam.tile_h) *
+                                              std::max<uint64_t>(total, 1)));
             GS_TRY(dmalloc((void**)&v.ck_off, 4 * ntiles));
             GS_TRY(dmalloc((void**)&v.ck_cnt, 4 * ntiles));
             GS_CUDA(cudaMemcpyAsync(v.ck_off, off.data(), 4 * ntiles, cudaMemcpyHostToDevice, st));
             GS_CUDA(cudaMemcpyAsync(v.ck_cnt, cnt.data(), 4 * ntiles, cudaMemcpyHostToDevice, st));
-            GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam.W, v.cam.H, v.clean, v.stop, v.tile_stop,
-                                           v.ck, v.ck_off, v.ck_cnt, nullptr, st));
+            GS_TRY(launch_blend_image_stop(v.recs, v.ids, v.ranges, v.cam, v.clean, v.stop, v.tile_stop, v.ck,
+                                           v.ck_off, v.ck_cnt, nullptr, st));
             GS_CUDA(cudaStreamSynchronize(st));
         }
         GS_TRY(launch_stop_keys(v.ranges, v.tile_stop, v.dk, v.ids, ntiles, v.stop_key, st));
         v.npairs = np;
         // per (tile, 8x8 block) sublists of the clean lists
         {
-            const uint64_t nb = (uint64_t)ntiles * kDirtyBlocks;
+            const uint64_t nb = (uint64_t)ntiles * (uint64_t)((v.cam.tile_w * v.cam.tile_h) / 64);
             uint32_t* counts = nullptr;
             unsigned long long* scratch = nullptr;
             GS_TRY(dmalloc((void**)&v.bl_off, sizeof(uint32_t) * (nb + 1)));
@@ -639,7 +641,7 @@ static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cud
             GS_TRY(dmalloc((void**)&scratch, sizeof(unsigned long long) * (scan_scratch_len(nb) + 3)));
             unsigned long long* total = scratch + scan_scratch_len(nb);
             gs_status bs =
-                launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, counts, nullptr, nullptr, nullptr, st);
+                launch_blists(v.recs, v.ids, v.ranges, v.cam, counts, nullptr, nullptr, nullptr, st);
             if (bs == GS_OK) bs = launch_exclusive_scan(counts, nb, v.bl_off, scratch, total, st);
             unsigned long long tot = 0;
             if (bs == GS_OK && cudaMemcpyAsync(&tot, total, sizeof(tot), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -653,8 +655,7 @@ static gs_status build_views(gs_scene* s, const gs_camera* host_cams, int K, cud
             GS_CUDA(cudaMemcpyAsync(v.bl_off + nb, &tot32, sizeof(tot32), cudaMemcpyHostToDevice, st));
             GS_TRY(dmalloc((void**)&v.bl_pos, sizeof(uint32_t) * std::max<uint64_t>(tot, 1)));
             GS_TRY(dmalloc((void**)&v.bl_rec, sizeof(BlendRec) * std::max<uint64_t>(tot, 1)));
-            GS_TRY(launch_blists(v.recs, v.ids, v.ranges, ntiles, v.cam.tiles_x, nullptr, v.bl_off, v.bl_pos, v.bl_rec,
-                                 st));
+            GS_TRY(launch_blists(v.recs, v.ids, v.ranges, v.cam, nullptr, v.bl_off, v.bl_pos, v.bl_rec, st));
             GS_CUDA(cudaStreamSynchronize(st));
         }
         fill_view_ptrs(vptrs.data() + view_ptrs_size() * k, v);
@@ -690,8 +691,32 @@ gs_status gs_set_views(gs_scene* s, const gs_camera* host_cams, int K, void* str
     const gs_status rs = build_views(s, host_cams, K, (cudaStream_t)stream);
     // a failure part way (out of memory, a capacity limit) leaves no half-built
     // views behind: campaign calls then report GS_ERR_STATE instead of reading them
-    if (rs != GS_OK) free_views(s);
-    return rs;
+    if (rs != GS_OK) {
+        free_views(s);
+        s->host_cams.clear();
+        return rs;
+    }
+    s->host_cams.assign(host_cams, host_cams + K);
+    return GS_OK;
+}
+
+gs_status gs_set_tile(gs_scene* s, int tile_w, int tile_h, void* stream) {
+    if (!s || !tile_shape_ok(tile_w, tile_h))
+        return set_error(GS_ERR_ARG, "tile shape must be tw x th with tw, th in {8, 16, 32} and 64 <= tw * th <= 256");
+    if (tile_w == s->tile_w && tile_h == s->tile_h) return GS_OK;
+    s->tile_w = tile_w;
+    s->tile_h = tile_h;
+    if (s->host_cams.empty()) return GS_OK;
+    // rebuild the clean per-view state for the new tiles
+    const std::vector<gs_camera> cams = s->host_cams;
+    return gs_set_views(s, cams.data(), (int)cams.size(), stream);
+}
+
+gs_status gs_get_tile(gs_scene* s, int* tile_w, int* tile_h) {
+    if (!s || !tile_w || !tile_h) return set_error(GS_ERR_ARG, "bad gs_get_tile arguments");
+    *tile_w = s->tile_w;
+    *tile_h = s->tile_h;
+    return GS_OK;
 }
 
 gs_status gs_clean_image(gs_scene* s, int k, float* dev_rgb, void* stream) {
@@ -737,8 +762,10 @@ gs_status inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int gu
     const int K = s->K;
     const int max_chunk = max_batch(K);
     const int chunk = s->batch > 0 ? std::min(s->batch, max_chunk) : max_chunk;
-    GS_TRY(ensure_batch_buffers(s, chunk, 1));
     const bool ssim = dev_ssim != nullptr;
+    if (ssim && (s->tile_w != kTile || s->tile_h != kTile))
+        return set_error(GS_ERR_STATE, "the dirty-tile SSIM needs 16 x 16 render tiles (gs_set_tile)");
+    GS_TRY(ensure_batch_buffers(s, chunk, 1));
     if (ssim) GS_TRY(ensure_ssim_buffers(s));
     for (int b0 = 0; b0 < B; b0 += chunk) {
         int nb = std::min(chunk, B - b0);
@@ -788,7 +815,7 @@ gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B
             const ViewState& v = s->views[k];
             uint32_t* ids = nullptr;
             GS_TRY(render_lists(s, s->work, v.cam, &ids, st));
-            GS_TRY(launch_blend_compare(s->work.recs, ids, s->work.ranges, v.cam.W, v.cam.H, v.clean, s->acc + k,
+            GS_TRY(launch_blend_compare(s->work.recs, ids, s->work.ranges, v.cam, v.clean, s->acc + k,
                                         s->work_ctr, st));
         }
         GS_TRY(launch_restore_sites(s->planes, s->fmt, s->n, s->nwords, f, fpv, s->saved, st));
@@ -800,7 +827,7 @@ gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B
 gs_status gs_preprocess(gs_scene* s, const gs_camera* host_cam, gs_record* dev_out, void* stream) {
     if (!s || !host_cam || !dev_out) return set_error(GS_ERR_ARG, "bad gs_preprocess arguments");
     if (!valid_camera(*host_cam)) return set_error(GS_ERR_ARG, "invalid camera");
-    DevCamera cam = make_dev_camera(*host_cam);
+    DevCamera cam = make_dev_camera(*host_cam, s->tile_w, s->tile_h);
     return launch_preprocess(s, cam, nullptr, nullptr, nullptr, nullptr, dev_out, (cudaStream_t)stream);
 }
 
@@ -846,14 +873,18 @@ gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uint32_t* 
                          int W, int H, float* dev_rgb, void* stream) {
     if (!dev_offsets || !dev_rgb || W < 1 || H < 1 || (n > 0 && !dev_recs)) return set_error(GS_ERR_ARG, "bad gs_blend_lists arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    int ntiles = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+    gs_camera hc{};   // lists of 16 x 16 tiles
+    hc.width = W;
+    hc.height = H;
+    const DevCamera cam = make_dev_camera(hc, kTile, kTile);
+    const int ntiles = cam.tiles_x * cam.tiles_y;
     BlendRec* recs = nullptr;
     uint2* ranges = nullptr;
     GS_CUDA(cudaMallocAsync((void**)&recs, sizeof(BlendRec) * std::max<uint64_t>(n, 1), st));
     GS_CUDA(cudaMallocAsync((void**)&ranges, sizeof(uint2) * ntiles, st));
     gs_status rs = launch_records_to_blend(dev_recs, n, recs, st);
     if (rs == GS_OK) rs = launch_offsets_to_ranges(dev_offsets, ntiles, ranges, st);
-    if (rs == GS_OK) rs = launch_blend_image(recs, dev_ids, ranges, W, H, dev_rgb, st);
+    if (rs == GS_OK) rs = launch_blend_image(recs, dev_ids, ranges, cam, dev_rgb, st);
     cudaFreeAsync(recs, st);
     cudaFreeAsync(ranges, st);
     return rs;
@@ -916,6 +947,46 @@ gs_status gs_autotune(gs_scene* s, const gs_flip* dev_flips, int count, int guar
     s->batch = best;
     *best_batch = best;
     if (best_us_per_variant) *best_us_per_variant = best_t;
+    return GS_OK;
+}
+
+gs_status gs_autotune_tile(gs_scene* s, const gs_flip* dev_flips, int count, int guard_mode, uint64_t word_mask,
+                           int* best_tile_w, int* best_tile_h, int* best_batch, float* best_us_per_variant,
+                           void* stream) {
+    GS_TRY(check_flip_args(s, dev_flips, count, 1, guard_mode, word_mask));
+    if (count < 1 || !best_tile_w || !best_tile_h || !best_batch)
+        return set_error(GS_ERR_ARG, "bad gs_autotune_tile arguments");
+    const int shapes[3][2] = {{16, 16}, {8, 8}, {32, 8}};
+    const int prev_w = s->tile_w, prev_h = s->tile_h, prev_batch = s->batch;
+    int bw = prev_w, bh = prev_h, bb = 0;
+    float bt = 1e30f;
+    gs_status rs = GS_OK;
+    for (const auto& sh : shapes) {
+        rs = gs_set_tile(s, sh[0], sh[1], stream);
+        if (rs != GS_OK) break;
+        int b = 0;
+        float us = 0.0f;
+        rs = gs_autotune(s, dev_flips, count, guard_mode, word_mask, &b, &us, stream);
+        if (rs != GS_OK) break;
+        if (us < bt) {
+            bt = us;
+            bw = sh[0];
+            bh = sh[1];
+            bb = b;
+        }
+    }
+    if (rs != GS_OK) {   // leave the scene as it was (views rebuilt for the previous tiles)
+        const std::string msg = gs_last_error();
+        gs_set_tile(s, prev_w, prev_h, stream);
+        s->batch = prev_batch;
+        return set_error(rs, msg);
+    }
+    GS_TRY(gs_set_tile(s, bw, bh, stream));
+    s->batch = bb;
+    *best_tile_w = bw;
+    *best_tile_h = bh;
+    *best_batch = bb;
+    if (best_us_per_variant) *best_us_per_variant = bt;
     return GS_OK;
 }
 

@@ -14,11 +14,21 @@
 
 namespace gs {
 
-constexpr int kTile = 16;             // render tile edge (pixels)
-constexpr int kTilePix = kTile * kTile;
-// The dirty-tile blend works on 8x8 pixel blocks of a tile (one warp, two pixels
-// per lane); a block is the 8x4 halves w and w + 2 of the natural pixel order.
-constexpr int kDirtyBlocks = kTilePix / 64;
+// Render tiles are tw x th pixels, tw and th in {8, 16, 32} with 64 <= tw * th
+// <= 256 (a scene's shape is set by gs_set_tile; 16 x 16 by default).  A tile's
+// pixels are numbered in 8x4 blocks ("natural order"): pixel u = 32 w + lane of
+// block w sits at (8 (w % nbx) + lane % 8, 4 (w / nbx) + lane / 8), nbx = tw / 8.
+// The dirty-tile blend works on 8x8 blocks (one warp, two pixels per lane):
+// block b is the 8x4 blocks wA = b % nbx + 2 nbx (b / nbx) and wA + nbx.
+constexpr int kTile = 16;                   // default tile edge; the full-frame SSIM's own tile edge
+constexpr int kTilePix = 256;               // most pixels in a tile
+constexpr int kDirtyBlocks = kTilePix / 64; // most 8x8 blocks in a tile
+__host__ __device__ inline bool tile_shape_ok(int tw, int th) {
+    const bool ew = tw == 8 || tw == 16 || tw == 32, eh = th == 8 || th == 16 || th == 32;
+    return ew && eh && tw * th >= 64 && tw * th <= kTilePix;
+}
+// log2 of the 8x4 blocks per tile row (tw / 8 = 1, 2, 4)
+__host__ __device__ inline int tile_lgx(int tw) { return tw == 8 ? 0 : (tw == 16 ? 1 : 2); }
 constexpr int kMaxWords = 59;
 constexpr int kMaxPairs = 8192;       // (variant, view) pairs per dirty-tile launch (one scan block)
 constexpr int kMaxBatch = 2048;       // variants per dirty-tile launch (also <= kMaxPairs / views)
@@ -67,6 +77,7 @@ struct DevCamera {
     int W, H;
     float znear, zfar;
     int tiles_x, tiles_y;
+    int tile_w, tile_h;   // render tile shape
 };
 
 // Per (variant, view) comparison accumulator (integer/ordered atomics only, so
@@ -91,13 +102,14 @@ __host__ __device__ inline unsigned long long cell_bit(int x, int y, int W, int 
     const int cx = (int)((unsigned)x * 8u / (unsigned)W), cy = (int)((unsigned)y * 8u / (unsigned)H);
     return 1ull << (cy * 8 + cx);
 }
-// cells met by the pixels of a tile rect (packed x0 | y0 << 16, x1 | y1 << 16, half open in tiles)
-__host__ __device__ inline unsigned long long rect_cells(uint2 rect, int W, int H, int tile) {
+// cells met by the pixels of a tile rect (packed x0 | y0 << 16, x1 | y1 << 16, half
+// open in tiles of tw x th pixels)
+__host__ __device__ inline unsigned long long rect_cells(uint2 rect, int W, int H, int tw, int th) {
     const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
     if (x1 <= x0 || y1 <= y0) return 0ull;
-    const int px1 = min(x1 * tile, W) - 1, py1 = min(y1 * tile, H) - 1;
-    const int cx0 = (int)(((long long)x0 * tile * 8) / W), cx1 = (int)(((long long)px1 * 8) / W);
-    const int cy0 = (int)(((long long)y0 * tile * 8) / H), cy1 = (int)(((long long)py1 * 8) / H);
+    const int px1 = min(x1 * tw, W) - 1, py1 = min(y1 * th, H) - 1;
+    const int cx0 = (int)(((long long)x0 * tw * 8) / W), cx1 = (int)(((long long)px1 * 8) / W);
+    const int cy0 = (int)(((long long)y0 * th * 8) / H), cy1 = (int)(((long long)py1 * 8) / H);
     unsigned long long m = 0ull;
     for (int cy = cy0; cy <= cy1; cy++)
         for (int cx = cx0; cx <= cx1; cx++) m |= 1ull << (cy * 8 + cx);
@@ -119,7 +131,7 @@ struct ViewPtrs {
     const float4* ck;            // clean-blend checkpoints (T, C) of every pixel
     const uint32_t* ck_off;      // first checkpoint of each tile
     const uint32_t* ck_cnt;      // checkpoints of each tile (after kCkStride, 2 kCkStride, ... entries)
-    int W, H, tiles_x, pad;
+    int W, H, tiles_x, tile_w, tile_h, pad[3];
 };
 
 // One dirty tile that needs re-blending (112 B).  ins is the insertion position
@@ -183,7 +195,7 @@ struct ViewState {
     uint32_t* bl_off = nullptr;      // [ntiles * kDirtyBlocks + 1] start of each (tile, 8x8 block) sublist in bl_pos
     uint32_t* bl_pos = nullptr;      // list positions whose box meets the block, ascending per sublist
     BlendRec* bl_rec = nullptr;      // the records of those entries, in the same order (streamed by the blend)
-    float4* ck = nullptr;            // clean-blend checkpoints [total][256 pixels]
+    float4* ck = nullptr;            // clean-blend checkpoints [total][pixels of a tile]
     uint32_t* ck_off = nullptr;      // [ntiles]
     uint32_t* ck_cnt = nullptr;      // [ntiles]
     uint64_t ck_total = 0;
@@ -249,6 +261,8 @@ struct gs_scene {
     uint64_t full_cap_pairs = 0;
     int max_tiles = 0;
     gs::RenderWork work;                    // scratch of the full render pipeline
+    int tile_w = gs::kTile, tile_h = gs::kTile;   // render tile shape (gs_set_tile)
+    std::vector<gs_camera> host_cams;       // the cameras of gs_set_views (rebuilt on a tile change)
 
     // batch buffers (dirty engine and plain loop)
     int cap_B = 0;
@@ -261,7 +275,7 @@ struct gs_scene {
     unsigned int* queue = nullptr;
     void* plan = nullptr;                   // dirty tiles to re-blend (PlanItem[plan_cap])
     uint2* cand = nullptr;                  // candidate tiles of the plan's first pass [plan_cap]
-    uint32_t* groups = nullptr;             // 8x8 pixel blocks to re-blend, (item << 3) | block [8 * plan_cap]
+    uint32_t* groups = nullptr;             // 8x8 pixel blocks to re-blend, (item << 3) | block [kDirtyBlocks * plan_cap]
     gs::SsimBufs ssim{};                    // dirty-tile SSIM buffers (allocated on first use, else NULL)
     uint64_t plan_cap = 0;
     unsigned int* clean_nonfin = nullptr;   // [K] non-finite pixels of each clean view
@@ -292,7 +306,7 @@ gs_status launch_restore_sites(void* planes, int fmt, uint64_t n, int nwords, co
                                const uint32_t* saved, cudaStream_t st);
 
 // k_preprocess.cu
-DevCamera make_dev_camera(const gs_camera& c);
+DevCamera make_dev_camera(const gs_camera& c, int tile_w, int tile_h);
 
 // gs_api.cu: the camera sizes and focal lengths the kernels accept
 bool valid_camera(const gs_camera& c);
@@ -303,10 +317,10 @@ void free_render_work(RenderWork& w);
 gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, uint32_t* keys, uint32_t* vals,
                                uint2* prects, cudaStream_t st);
 
-// k_blend.cu
-gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+// k_blend.cu (full-frame kernels take the view's camera for its size and tile shape)
+gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                              float* img, cudaStream_t st);
-gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                                const float* clean, CmpAcc* acc, unsigned long long* work, cudaStream_t st);
 gs_status launch_compare(const float* a, const float* b, int H, int W, CmpAcc* acc, cudaStream_t st);
 gs_status launch_finalize(const CmpAcc* acc, int count, gs_result* out, cudaStream_t st);

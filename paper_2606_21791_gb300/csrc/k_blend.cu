@@ -73,7 +73,8 @@ struct Pix {
     uint32_t stop;   // list index of the entry that stopped the pixel (T would drop below 1e-4)
 };
 
-// Pixel geometry of thread `tid` in a tile: warp w covers an 8x4 block.
+// Pixel geometry of thread `tid` in a tw x th tile: warp w covers the 8x4 block w
+// of the natural order.
 struct PixGeo {
     int px, py;
     float pxc, pyc;
@@ -81,11 +82,12 @@ struct PixGeo {
     bool inside;
 };
 
-__device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int W, int H) {
+__device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int tw, int th, int W, int H) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lg = tile_lgx(tw);
     PixGeo g;
-    int bx = tile_x * kTile + (warp & 1) * 8;
-    int by = tile_y * kTile + (warp >> 1) * 4;
+    int bx = tile_x * tw + (warp & ((1 << lg) - 1)) * 8;
+    int by = tile_y * th + (warp >> lg) * 4;
     g.px = bx + (lane & 7);
     g.py = by + (lane >> 3);
     g.pxc = (float)g.px + 0.5f;
@@ -98,16 +100,18 @@ __device__ __forceinline__ PixGeo pix_geo(int tile_x, int tile_y, int W, int H) 
     return g;
 }
 
-// Natural pixel of thread index u in a tile (the pix_geo mapping).
-__device__ __forceinline__ void pix_of(int tile_x, int tile_y, int u, int& px, int& py) {
-    const int w = u >> 5, l = u & 31;
-    px = tile_x * kTile + (w & 1) * 8 + (l & 7);
-    py = tile_y * kTile + (w >> 1) * 4 + (l >> 3);
+// Natural pixel of index u in a tw x th tile (the pix_geo mapping).
+__device__ __forceinline__ void pix_of(int tile_x, int tile_y, int tw, int th, int u, int& px, int& py) {
+    const int w = u >> 5, l = u & 31, lg = tile_lgx(tw);
+    px = tile_x * tw + (w & ((1 << lg) - 1)) * 8 + (l & 7);
+    py = tile_y * th + (w >> lg) * 4 + (l >> 3);
 }
 
-// First (upper) 8x4 half, in the natural pixel order, of 8x8 block b of a tile;
-// the lower half is block_half(b) + 2.
-__host__ __device__ constexpr int block_half(int b) { return (b & 1) + 4 * (b >> 1); }
+// 8x8 block b of a tile with 8x4 blocks per row nbx = 1 << lg: its upper 8x4
+// block in the natural order (the lower one is that + nbx) and its offset in the tile.
+__host__ __device__ inline int block_upper(int b, int lg) { return (b & ((1 << lg) - 1)) + ((b >> lg) << (lg + 1)); }
+__host__ __device__ inline int block_x0(int b, int lg) { return (b & ((1 << lg) - 1)) * 8; }
+__host__ __device__ inline int block_y0(int b, int lg) { return (b >> lg) * 8; }
 
 // 2^x (hardware approximation, flushes subnormal results to zero)
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -154,6 +158,7 @@ struct CkWrite {
     float4* ck;      // NULL: no checkpoints
     uint32_t off;    // first checkpoint of this tile
     uint32_t count;  // checkpoints of this tile
+    uint32_t pix;    // pixels of a tile (one checkpoint holds one state per pixel)
 };
 
 // Survivors a warp takes at a time: their alphas do not depend on the pixel
@@ -251,14 +256,14 @@ __device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s
 
 template <bool COUNT, bool TRACK>
 __device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t base, const PixGeo& g, Pix& p,
-                                            unsigned int& nev, const CkWrite& ckw = CkWrite{nullptr, 0u, 0u}) {
+                                            unsigned int& nev, const CkWrite& ckw = CkWrite{nullptr, 0u, 0u, 0u}) {
     for (int c = 0; c < cnt; c += 32) {
         if (__all_sync(0xffffffffu, p.done)) return;
         if (ckw.ck && base + (uint32_t)c > 0 && ((base + (uint32_t)c) % kCkStride) == 0) {
             // the state after entries [0, base + c) of the list
             const uint32_t j = (base + (uint32_t)c) / kCkStride;
             if (j <= ckw.count)
-                ckw.ck[(size_t)(ckw.off + j - 1) * kBT + threadIdx.x] = make_float4(p.T, p.c0, p.c1, p.c2);
+                ckw.ck[(size_t)(ckw.off + j - 1) * ckw.pix + threadIdx.x] = make_float4(p.T, p.c0, p.c1, p.c2);
         }
         blend_chunk<COUNT, TRACK>(s.box, s.q0, s.q1, s.qb, c, cnt, base, g, p, nev);
     }
@@ -311,8 +316,7 @@ __device__ __forceinline__ void compare_tile(const PixGeo& g, float v0, float v1
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         float mm = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kBT / 32; w++) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
             t += wsse[w];
             mm = fmaxf(mm, wmax[w]);
         }
@@ -335,9 +339,11 @@ __device__ __forceinline__ void add_work(unsigned long long* work, unsigned int 
 // MODE 0: write the image; 1: compare with the clean image; 2: write the image
 // and each pixel's stop index (0xffffffff if it never stopped), which the
 // dirty-tile kernel uses to leave pixels that stopped before a change untouched.
+// One block of tw * th threads per tw x th tile.
 template <int MODE, bool COUNT>
 __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
                                                    const uint2* __restrict__ ranges, int W, int H, int tiles_x,
+                                                   int tw, int th,
                                                    float* __restrict__ img, const float* __restrict__ clean,
                                                    CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop,
                                                    uint32_t* __restrict__ tile_stop, float4* __restrict__ ck,
@@ -346,19 +352,20 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
                                                    unsigned int* __restrict__ clean_nonfin) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
-    const CkWrite ckw{ck, ck ? ck_off[tile] : 0u, ck ? ck_cnt[tile] : 0u};
-    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
+    const uint32_t P = blockDim.x;   // pixels of a tile
+    const CkWrite ckw{ck, ck ? ck_off[tile] : 0u, ck ? ck_cnt[tile] : 0u, P};
+    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, tw, th, W, H);
     Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, 0xffffffffu};
     const uint2 rg = ranges[tile];
     unsigned int nev = 0, staged = 0;
-    for (uint32_t base = rg.x; base < rg.y; base += kBT) {
-        int cnt = (int)min((uint32_t)kBT, rg.y - base);
+    for (uint32_t base = rg.x; base < rg.y; base += P) {
+        int cnt = (int)min(P, rg.y - base);
         if ((int)threadIdx.x < cnt) stage_put(s, threadIdx.x, load_rec(recs, ids[base + threadIdx.x]));
         __syncthreads();
         staged += cnt;
         blend_batch<COUNT, MODE == 2>(s, cnt, base - rg.x, g, p, nev, ckw);
         // also the barrier that lets the next batch overwrite the stage
-        if (__syncthreads_count(p.done) == kBT) break;
+        if (__syncthreads_count(p.done) == (int)P) break;
     }
     if (COUNT) add_work(work, nev, staged);
     const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
@@ -384,7 +391,7 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
             __syncthreads();
             if (threadIdx.x == 0) {
                 uint32_t t = 0;
-                for (int w = 0; w < kBT / 32; w++) t = max(t, wmax[w]);
+                for (int w = 0; w < (int)(P >> 5); w++) t = max(t, wmax[w]);
                 tile_stop[tile] = t;
             }
         }
@@ -396,7 +403,7 @@ __global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__
 __global__ __launch_bounds__(kBT) void k_compare(const float* __restrict__ a, const float* __restrict__ b, int W, int H,
                                                 int tiles_x, CmpAcc* acc) {
     const int tile = blockIdx.x;
-    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, W, H);
+    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, kTile, kTile, W, H);
     float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
     if (g.inside) {
         const float* q = a + ((size_t)g.py * W + g.px) * 3;
@@ -603,9 +610,9 @@ __global__ __launch_bounds__(256) void k_plan_filter(const ViewPtrs* __restrict_
             if (has_new) kmin = min(kmin, ((unsigned long long)__float_as_uint(d.rec.depth) << 32) | d.prim);
             const bool stopped = v.stop_key[tile] < kmin;
             if (!stopped) {
-                const float rx0 = (float)(tx * kTile) + 0.5f, ry0 = (float)(ty * kTile) + 0.5f;
-                const float rx1 = fminf((float)(tx * kTile + kTile - 1), (float)(v.W - 1)) + 0.5f;
-                const float ry1 = fminf((float)(ty * kTile + kTile - 1), (float)(v.H - 1)) + 0.5f;
+                const float rx0 = (float)(tx * v.tile_w) + 0.5f, ry0 = (float)(ty * v.tile_h) + 0.5f;
+                const float rx1 = fminf((float)(tx * v.tile_w + v.tile_w - 1), (float)(v.W - 1)) + 0.5f;
+                const float ry1 = fminf((float)(ty * v.tile_h + v.tile_h - 1), (float)(v.H - 1)) + 0.5f;
                 keep = (has_new && tile_reachable(d.rec, rx0, rx1, ry0, ry1)) ||
                        (has_old && tile_reachable(v.recs[d.prim], rx0, rx1, ry0, ry1));
             }
@@ -661,14 +668,15 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
         const BlendRec nrec = d.rec;
         const BlendRec orec = has_old ? v.recs[d.prim] : nrec;
         const uint32_t prim = d.prim;
+        const int nw = (v.tile_w * v.tile_h) >> 5;   // 8x4 blocks of the tile
         unsigned reach[kBT / 32];
         bool any = false;
 #pragma unroll
         for (int q = 0; q < kBT / 32; q++) {
             int px, py;
-            pix_of(itx, ity, q * 32 + lane, px, py);
+            pix_of(itx, ity, v.tile_w, v.tile_h, q * 32 + lane, px, py);
             const float x = (float)px + 0.5f, y = (float)py + 0.5f;
-            const bool r = px < v.W && py < v.H &&
+            const bool r = q < nw && px < v.W && py < v.H &&
                            ((has_old && affects(orec, x, y)) || (has_new && affects(nrec, x, y)));
             reach[q] = __ballot_sync(0xffffffffu, r);
             any |= reach[q] != 0u;
@@ -691,7 +699,7 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
 #pragma unroll
             for (int q = 0; q < kBT / 32; q++) {
                 int px, py;
-                pix_of(itx, ity, q * 32 + lane, px, py);
+                pix_of(itx, ity, v.tile_w, v.tile_h, q * 32 + lane, px, py);
                 bool a = false;
                 if ((reach[q] >> lane) & 1u) a = v.stop[(size_t)py * v.W + px] >= cut;
                 reach[q] = __ballot_sync(0xffffffffu, a);   // now: active pixels
@@ -706,10 +714,17 @@ __global__ __launch_bounds__(256, 4) void k_plan_exact(const ViewPtrs* __restric
         // active pixel, (slot << 3) | block.  Groups of tiles with a long walk
         // ahead (from the checkpoint the blend resumes at) go to the front of the
         // group array and are blended first, the others to the back.
+        const int lg = tile_lgx(v.tile_w), nb = nw >> 1;
         uint32_t word = 0;
 #pragma unroll
-        for (int b = 0; b < kDirtyBlocks; b++) word = lane == b ? reach[block_half(b)] | reach[block_half(b) + 2] : word;
-        const unsigned gm = __ballot_sync(0xffffffffu, lane < kDirtyBlocks && word != 0u);
+        for (int b = 0; b < kDirtyBlocks; b++) {
+            const int wa = block_upper(b, lg), wb = wa + (1 << lg);
+            uint32_t bw = 0;
+#pragma unroll
+            for (int q = 0; q < kBT / 32; q++) bw |= (q == wa || q == wb) ? reach[q] : 0u;
+            word = lane == b ? bw : word;
+        }
+        const unsigned gm = __ballot_sync(0xffffffffu, lane < nb && word != 0u);
         const uint32_t Lm = (rg.y - rg.x) - (has_old ? 1u : 0u) + (has_new ? 1u : 0u);
         const uint32_t walk = Lm - min(cut / (uint32_t)kCkStride, v.ck_cnt[tile]) * (uint32_t)kCkStride;
         const bool heavy = walk >= (uint32_t)kHeavyWalk;
@@ -895,8 +910,8 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
                                                               unsigned int* __restrict__ queue,
                                                               unsigned long long* work, SsimBufs sb) {
     __shared__ WarpRing rings[kDirtyWarps];
-    const int lane = threadIdx.x & 31;
-    WarpRing& R = rings[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpRing& R = rings[warp];
     const uint32_t nheavy = counts[3], ngroups = counts[3] + counts[4];
     // measurement builds: SM cycles each warp spends per phase (set-up of a group,
     // the walk, the comparison and reductions)
@@ -911,27 +926,31 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
         const uint32_t code = groups[gi < nheavy ? gi : gcap - 1u - (gi - nheavy)];
         const PlanItem* it = &plan[code >> 3];
         const int b = (int)(code & 7u);            // 8x8 block of the tile
-        const int wA = block_half(b), wB = wA + 2;   // its upper and lower 8x4 halves
         const uint4 f5 = reinterpret_cast<const uint4*>(it)[5];   // bk, tile, s, e
         const uint4 f6 = reinterpret_cast<const uint4*>(it)[6];   // pp, ins, cut, flags
-        const uint32_t amA = it->mask[wA], amB = it->mask[wB];
         const int bk = (int)f5.x;
         const uint32_t tile = f5.y, pp = f6.x, ins = f6.y, cut = f6.z;
         const bool has_old = f6.w & 1u, has_new = f6.w & 2u;
         const ViewPtrs& v = views[bk % K];
+        const int tw = v.tile_w, th = v.tile_h, lg = tile_lgx(tw), nb = (tw * th) >> 6;
+        const int wA = block_upper(b, lg), wB = wA + (1 << lg);   // the block's upper and lower 8x4 halves
+        const uint32_t amA = it->mask[wA], amB = it->mask[wB];
         const int tx = (int)(tile % (uint32_t)v.tiles_x), ty = (int)(tile / (uint32_t)v.tiles_x);
         // lane: pixel A of the upper half, pixel B four rows below it
-        int px, pyA;
-        pix_of(tx, ty, wA * 32 + lane, px, pyA);
+        const int px = tx * tw + block_x0(b, lg) + (lane & 7);
+        const int pyA = ty * th + block_y0(b, lg) + (lane >> 3);
         const int pyB = pyA + 4;
-        const float pxc = (float)px + 0.5f, pycA = (float)pyA + 0.5f, pycB = (float)pyB + 0.5f;
-        const bool actA = (amA >> lane) & 1u, actB = (amB >> lane) & 1u;   // decided by the plan (inside the image)
-        const bool act = actA || actB;
+        const bool inA = (amA >> lane) & 1u, inB = (amB >> lane) & 1u;   // decided by the plan (inside the image)
+        const bool act = inA || inB;
         PixGeo g;   // the box of the block's active pixel centres
         g.wx0 = (float)__reduce_min_sync(0xffffffffu, act ? px : 0x7fffffff) + 0.5f;
         g.wx1 = (float)__reduce_max_sync(0xffffffffu, act ? px : -1) + 0.5f;
-        g.wy0 = (float)__reduce_min_sync(0xffffffffu, actA ? pyA : (actB ? pyB : 0x7fffffff)) + 0.5f;
-        g.wy1 = (float)__reduce_max_sync(0xffffffffu, actB ? pyB : (actA ? pyA : -1)) + 0.5f;
+        g.wy0 = (float)__reduce_min_sync(0xffffffffu, inA ? pyA : (inB ? pyB : 0x7fffffff)) + 0.5f;
+        g.wy1 = (float)__reduce_max_sync(0xffffffffu, inB ? pyB : (inA ? pyA : -1)) + 0.5f;
+        // this lane's pixels: A in the upper half, B four rows below it
+        const int x0 = px, y0 = pyA, u0 = wA * 32 + lane, y1 = pyB, u1 = wB * 32 + lane;
+        const bool actA = inA, actB = inB;
+        const float pxc = (float)x0 + 0.5f, pycA = (float)y0 + 0.5f, pycB = (float)y1 + 0.5f;
         Pix pA{1.0f, 0.0f, 0.0f, 0.0f, !actA, 0u}, pB{1.0f, 0.0f, 0.0f, 0.0f, !actB, 0u};
         // The merged list equals the clean list before `cut`, so an active pixel
         // (not stopped before `cut`) can resume from the clean blend's state at the
@@ -939,16 +958,16 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
         const uint32_t cstar = min(cut / (uint32_t)kCkStride, v.ck_cnt[tile]);
         const uint32_t start = cstar * (uint32_t)kCkStride;
         if (cstar > 0) {
-            const float4* ckt = v.ck + (size_t)(v.ck_off[tile] + cstar - 1) * kBT;
+            const float4* ckt = v.ck + (size_t)(v.ck_off[tile] + cstar - 1) * (uint32_t)(tw * th);
             if (actA) {
-                const float4 st = ckt[wA * 32 + lane];
+                const float4 st = ckt[u0];
                 pA.T = st.x;
                 pA.c0 = st.y;
                 pA.c1 = st.z;
                 pA.c2 = st.w;
             }
             if (actB) {
-                const float4 st = ckt[wB * 32 + lane];
+                const float4 st = ckt[u1];
                 pB.T = st.x;
                 pB.c0 = st.y;
                 pB.c1 = st.z;
@@ -959,8 +978,8 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
         // block, positions ascending) from `start`, without the old entry and with the
         // corrupted record at its place: every entry outside the sublist fails the
         // cull below anyway.
-        const uint32_t boff = v.bl_off[(size_t)tile * kDirtyBlocks + b];
-        const uint32_t blen = v.bl_off[(size_t)tile * kDirtyBlocks + b + 1] - boff;
+        const uint32_t boff = v.bl_off[(size_t)tile * nb + b];
+        const uint32_t blen = v.bl_off[(size_t)tile * nb + b + 1] - boff;
         const uint32_t* B = v.bl_pos + boff;
         const uint32_t k0 = warp_lower_bound_u32(B, 0, blen, start);
         bool has_kpp = false;
@@ -1036,11 +1055,12 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
         // counted once per view at finalize
         const float a0 = __fadd_rn(pA.c0, pA.T), a1 = __fadd_rn(pA.c1, pA.T), a2 = __fadd_rn(pA.c2, pA.T);
         const float b0 = __fadd_rn(pB.c0, pB.T), b1 = __fadd_rn(pB.c1, pB.T), b2 = __fadd_rn(pB.c2, pB.T);
-        const float* cA = v.clean + ((size_t)pyA * v.W + px) * 3;
-        const float* cB = v.clean + ((size_t)pyB * v.W + px) * 3;
+        const float* cA = v.clean + ((size_t)y0 * v.W + x0) * 3;
+        const float* cB = v.clean + ((size_t)y1 * v.W + px) * 3;
         if (sb.deltas) {   // dirty-tile SSIM: keep the block's new values, two 32-pixel delta units per group
             const uint32_t slot = code >> 3;
             if (2u * gi + 1u < sb.delta_cap && slot < sb.slot_cap) {
+                // delta unit 2 gi: upper half, 2 gi + 1: lower half; one entry per pixel of the half
                 if (actA) sb.deltas[(size_t)(2u * gi) * 32 + lane] = make_float4(a0, a1, a2, 0.0f);
                 if (actB) sb.deltas[(size_t)(2u * gi + 1u) * 32 + lane] = make_float4(b0, b1, b2, 0.0f);
                 if (lane == 0) {
@@ -1052,12 +1072,12 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
                     const bool ch = a && (__float_as_uint(n0) != __float_as_uint(c[0]) ||
                                           __float_as_uint(n1) != __float_as_uint(c[1]) ||
                                           __float_as_uint(n2) != __float_as_uint(c[2]));
-                    const int lx = x % kTile, ly = y % kTile;
-                    return ch ? (16u | (lx < 5 ? 1u : 0u) | (lx > kTile - 6 ? 2u : 0u) | (ly < 5 ? 4u : 0u) |
-                                 (ly > kTile - 6 ? 8u : 0u))
+                    const int lx = x - tx * tw, ly = y - ty * th;
+                    return ch ? (16u | (lx < 5 ? 1u : 0u) | (lx > tw - 6 ? 2u : 0u) | (ly < 5 ? 4u : 0u) |
+                                 (ly > th - 6 ? 8u : 0u))
                               : 0u;
                 };
-                const unsigned f = edge(actA, px, pyA, a0, a1, a2, cA) | edge(actB, px, pyB, b0, b1, b2, cB);
+                const unsigned f = edge(actA, x0, y0, a0, a1, a2, cA) | edge(actB, px, y1, b0, b1, b2, cB);
                 const unsigned fo = __reduce_or_sync(0xffffffffu, f);
                 if (lane == 0 && fo) atomicOr(&sb.slot_flags[slot], fo);
             } else if (lane == 0) {
@@ -1065,8 +1085,8 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
             }
         }
         BlockCmp r;
-        block_cmp_add(r, actA, a0, a1, a2, cA, px, pyA, v.W, v.H);
-        block_cmp_add(r, actB, b0, b1, b2, cB, px, pyB, v.W, v.H);
+        block_cmp_add(r, actA, a0, a1, a2, cA, x0, y0, v.W, v.H);
+        block_cmp_add(r, actB, b0, b1, b2, cB, px, y1, v.W, v.H);
         unsigned long long fx = r.fx;
         float mx = r.m;
 #pragma unroll
@@ -1094,8 +1114,8 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
             const unsigned wn = __reduce_add_sync(0xffffffffu, nev);
             // a tile counts once, on its first group (lowest block with an active pixel)
             const bool first =
-                __ballot_sync(0xffffffffu, lane < b && (it->mask[block_half(lane & 3)] |
-                                                        it->mask[block_half(lane & 3) + 2]) != 0u) == 0u;
+                __ballot_sync(0xffffffffu, lane < b && (it->mask[block_upper(lane & 3, lg)] |
+                                                        it->mask[block_upper(lane & 3, lg) + (1 << lg)]) != 0u) == 0u;
             if (lane == 0) {
                 if (wn) atomicAdd(&work[0], (unsigned long long)wn);
                 if (first) atomicAdd(&work[1], 1ull);
@@ -1150,37 +1170,41 @@ __global__ void k_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* 
 
 }  // namespace
 
-gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H, float* img,
-                             cudaStream_t st) {
-    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
+                             float* img, cudaStream_t st) {
+    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h;
     if (tx * ty == 0) return GS_OK;
-    k_blend_full<0, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr,
-                                                     nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    k_blend_full<0, false><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h, img,
+                                                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
-gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                                const float* clean, CmpAcc* acc, unsigned long long* work, cudaStream_t st) {
-    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h;
     if (tx * ty == 0) return GS_OK;
     if (work)
-        k_blend_full<1, true><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, work, nullptr,
-                                                       nullptr, nullptr, nullptr, nullptr, nullptr);
+        k_blend_full<1, true><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h,
+                                                     nullptr, clean, acc, work, nullptr, nullptr, nullptr, nullptr,
+                                                     nullptr, nullptr);
     else
-        k_blend_full<1, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, nullptr, clean, acc, nullptr,
-                                                        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        k_blend_full<1, false><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h,
+                                                      nullptr, clean, acc, nullptr, nullptr, nullptr, nullptr,
+                                                      nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
-gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int W, int H,
+gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
                                   const uint32_t* ck_cnt, unsigned int* clean_nonfin, cudaStream_t st) {
-    int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h;
     if (tx * ty == 0) return GS_OK;
-    k_blend_full<2, false><<<tx * ty, kBT, 0, st>>>(recs, ids, ranges, W, H, tx, img, nullptr, nullptr, nullptr, stop,
-                                                     tile_stop, ck, ck_off, ck_cnt, clean_nonfin);
+    k_blend_full<2, false><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h, img,
+                                                   nullptr, nullptr, nullptr, stop, tile_stop, ck, ck_off, ck_cnt,
+                                                   clean_nonfin);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -1330,8 +1354,10 @@ void fill_view_ptrs(void* host_dst, const ViewState& vs) {
     v.ck_cnt = vs.ck_cnt;
     v.W = vs.cam.W;
     v.H = vs.cam.H;
-    v.tiles_x = (vs.cam.W + kTile - 1) / kTile;
-    v.pad = 0;
+    v.tiles_x = vs.cam.tiles_x;
+    v.tile_w = vs.cam.tile_w;
+    v.tile_h = vs.cam.tile_h;
+    v.pad[0] = v.pad[1] = v.pad[2] = 0;
     memcpy(host_dst, &v, sizeof(v));
 }
 
@@ -1344,16 +1370,18 @@ void fill_view_ptrs(void* host_dst, const ViewState& vs) {
 // ---------------------------------------------------------------------------
 template <bool FILL>
 __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
-                         const uint2* __restrict__ ranges, int ntiles, int tiles_x, uint32_t* __restrict__ counts,
-                         const uint32_t* __restrict__ off, uint32_t* __restrict__ pos, BlendRec* __restrict__ brec) {
+                         const uint2* __restrict__ ranges, int ntiles, int tiles_x, int tw, int th,
+                         uint32_t* __restrict__ counts, const uint32_t* __restrict__ off, uint32_t* __restrict__ pos,
+                         BlendRec* __restrict__ brec) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int lg = tile_lgx(tw), nb = (tw * th) >> 6;   // 8x8 blocks per tile
     for (int t = warp; t < ntiles; t += nwarps) {
         const uint2 rg = ranges[t];
         const int tx = t % tiles_x, ty = t / tiles_x;
         uint32_t base[kDirtyBlocks];
 #pragma unroll
-        for (int b = 0; b < kDirtyBlocks; b++) base[b] = FILL ? off[(size_t)t * kDirtyBlocks + b] : 0u;
+        for (int b = 0; b < kDirtyBlocks; b++) base[b] = (FILL && b < nb) ? off[(size_t)t * nb + b] : 0u;
         for (uint32_t j0 = 0; j0 < rg.y - rg.x; j0 += 32) {
             const uint32_t j = j0 + (uint32_t)lane;
             unsigned mb = 0u;
@@ -1364,9 +1392,10 @@ __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __re
                 const float4 a = __ldg(r), b = __ldg(r + 1);   // (mx, my, ca, cb), (cc, opac, ex, ey)
 #pragma unroll
                 for (int k = 0; k < kDirtyBlocks; k++) {
-                    const float wx0 = (float)(tx * kTile + (k % (kTile / 8)) * 8) + 0.5f, wx1 = wx0 + 7.0f;
-                    const float wy0 = (float)(ty * kTile + (k / (kTile / 8)) * 8) + 0.5f, wy1 = wy0 + 7.0f;
-                    const bool pass = !(a.x + b.z < wx0 || a.x - b.z > wx1 || a.y + b.w < wy0 || a.y - b.w > wy1);
+                    const float wx0 = (float)(tx * tw + block_x0(k, lg)) + 0.5f, wx1 = wx0 + 7.0f;
+                    const float wy0 = (float)(ty * th + block_y0(k, lg)) + 0.5f, wy1 = wy0 + 7.0f;
+                    const bool pass =
+                        k < nb && !(a.x + b.z < wx0 || a.x - b.z > wx1 || a.y + b.w < wy0 || a.y - b.w > wy1);
                     mb |= pass ? (1u << k) : 0u;
                 }
             }
@@ -1381,21 +1410,26 @@ __global__ void k_blists(const BlendRec* __restrict__ recs, const uint32_t* __re
                 base[k] += (uint32_t)__popc(bw);
             }
         }
-        if (!FILL && lane < kDirtyBlocks) {
+        if (!FILL && lane < nb) {
             uint32_t c = 0;
 #pragma unroll
             for (int k = 0; k < kDirtyBlocks; k++) c = lane == k ? base[k] : c;
-            counts[(size_t)t * kDirtyBlocks + lane] = c;
+            counts[(size_t)t * nb + lane] = c;
         }
     }
 }
 
-gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, int ntiles, int tiles_x,
+gs_status launch_blists(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                         uint32_t* counts, const uint32_t* off, uint32_t* pos, BlendRec* brec, cudaStream_t st) {
+    const int ntiles = cam.tiles_x * cam.tiles_y;
     if (ntiles <= 0) return GS_OK;
     const int blocks = std::max(1, std::min((ntiles + 7) / 8, num_sms() * 16));
-    if (pos) k_blists<true><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, nullptr, off, pos, brec);
-    else k_blists<false><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, tiles_x, counts, nullptr, nullptr, nullptr);
+    if (pos)
+        k_blists<true><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, cam.tiles_x, cam.tile_w, cam.tile_h, nullptr,
+                                               off, pos, brec);
+    else
+        k_blists<false><<<blocks, 256, 0, st>>>(recs, ids, ranges, ntiles, cam.tiles_x, cam.tile_w, cam.tile_h, counts,
+                                                nullptr, nullptr, nullptr);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

@@ -222,10 +222,10 @@ __device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const De
     float my = cam.fy * (p1 / z) + cam.cy;
     if (!isfinite(mx) || !isfinite(my)) return false;
 
-    const float tw = (float)kTile;
+    const float tw = (float)cam.tile_w, th = (float)cam.tile_h;
     const float ftx = (float)cam.tiles_x, fty = (float)cam.tiles_y;
     float fx0 = floorf((mx - rad) / tw), fx1 = floorf((mx + rad) / tw) + 1.0f;
-    float fy0 = floorf((my - rad) / tw), fy1 = floorf((my + rad) / tw) + 1.0f;
+    float fy0 = floorf((my - rad) / th), fy1 = floorf((my + rad) / th) + 1.0f;
     fx0 = fminf(fmaxf(fx0, 0.0f), ftx);   // operands finite here
     fy0 = fminf(fmaxf(fy0, 0.0f), fty);
     fx1 = fminf(fmaxf(fx1, 0.0f), ftx);
@@ -295,24 +295,36 @@ __device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const De
     return true;
 }
 
+constexpr int kPrepThreads = 128;
+
+// A primitive's words, staged in shared memory (this thread's column only).
 template <int FMT>
-struct PlaneSrc {
-    const void* planes;
-    uint64_t n, i;
-    __device__ float operator()(int w) const { return decode<FMT>(load_bits<FMT>(planes, n, w, i)); }
+struct StagedSrc {
+    const uint32_t (*sw)[kPrepThreads];
+    int t;
+    __device__ float operator()(int w) const { return decode<FMT>(sw[w][t]); }
 };
 
-// full preprocess: records, packed rects, depth-sort keys (invisible: 0xffffffff)
+// full preprocess: records, packed rects, depth-sort keys (invisible: 0xffffffff).
+// One thread per primitive.  Each thread first copies its primitive's stored
+// words into shared memory, eight loads in flight at a time (a warp reads 32
+// consecutive words of one plane per load), then computes from there: the
+// planes stream at full width instead of one dependent load per use.
 template <int FMT>
-__global__ __launch_bounds__(256) void k_preprocess(const void* planes, uint64_t n, int sh_degree, DevCamera cam,
-                                                    BlendRec* recs, uint2* rects, uint32_t* keys, uint32_t* vals,
-                                                    gs_record* dbg) {
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ __launch_bounds__(kPrepThreads) void k_preprocess(const void* planes, uint64_t n, int nwords,
+                                                             int sh_degree, DevCamera cam, BlendRec* recs,
+                                                             uint2* rects, uint32_t* keys, uint32_t* vals,
+                                                             gs_record* dbg) {
+    __shared__ uint32_t sw[kMaxWords][kPrepThreads];
+    const int t = threadIdx.x;
+    uint64_t i = (uint64_t)blockIdx.x * kPrepThreads + t;
     if (i >= n) return;
+#pragma unroll 8
+    for (int w = 0; w < nwords; w++) sw[w][t] = load_bits<FMT>(planes, n, w, i);
     BlendRec rec;
     uint2 rect = make_uint2(0, 0);
     float rad = 0.0f;
-    bool vis = preprocess_core(PlaneSrc<FMT>{planes, n, i}, sh_degree, cam, rec, rect, rad);
+    bool vis = preprocess_core(StagedSrc<FMT>{sw, t}, sh_degree, cam, rec, rect, rad);
     if (!vis) {
         rec = BlendRec{0, 0, 0, 0, 0, 0, -INFINITY, -INFINITY, 0, 0, 0, 0};
         rect = make_uint2(0, 0);
@@ -458,8 +470,9 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     z.ssim_fx = 0ull;
     // contamination prediction: the cells the primitive's tile rects meet, before
     // and after the upset, when its stored words changed
-    z.reg_pred = changed ? rect_cells(orect, cams[k].W, cams[k].H, kTile) |
-                               rect_cells(make_uint2(nx0 | (ny0 << 16), nx1 | (ny1 << 16)), cams[k].W, cams[k].H, kTile)
+    const int tw = cams[k].tile_w, th = cams[k].tile_h;
+    z.reg_pred = changed ? rect_cells(orect, cams[k].W, cams[k].H, tw, th) |
+                               rect_cells(make_uint2(nx0 | (ny0 << 16), nx1 | (ny1 << 16)), cams[k].W, cams[k].H, tw, th)
                          : 0ull;
     acc[bk] = z;
 }
@@ -516,7 +529,7 @@ __global__ __launch_bounds__(1024) void k_items_scan(const uint32_t* n_items, in
 
 }  // namespace
 
-DevCamera make_dev_camera(const gs_camera& c) {
+DevCamera make_dev_camera(const gs_camera& c, int tile_w, int tile_h) {
     DevCamera d;
     memcpy(d.R, c.R, sizeof(d.R));
     memcpy(d.t, c.t, sizeof(d.t));
@@ -528,21 +541,26 @@ DevCamera make_dev_camera(const gs_camera& c) {
     d.H = c.height;
     d.znear = c.znear;
     d.zfar = c.zfar;
-    d.tiles_x = (c.width + kTile - 1) / kTile;
-    d.tiles_y = (c.height + kTile - 1) / kTile;
+    d.tile_w = tile_w;
+    d.tile_h = tile_h;
+    d.tiles_x = (c.width + tile_w - 1) / tile_w;
+    d.tiles_y = (c.height + tile_h - 1) / tile_h;
     return d;
 }
 
 gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects, uint32_t* keys,
                             uint32_t* vals, gs_record* dbg, cudaStream_t st) {
     if (s->n == 0) return GS_OK;
-    unsigned blocks = (unsigned)div_up(s->n, 256);
+    const unsigned blocks = (unsigned)div_up(s->n, kPrepThreads);
     if (s->fmt == GS_FP32)
-        k_preprocess<GS_FP32><<<blocks, 256, 0, st>>>(s->planes, s->n, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+        k_preprocess<GS_FP32><<<blocks, kPrepThreads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam, recs,
+                                                               rects, keys, vals, dbg);
     else if (s->fmt == GS_FP16)
-        k_preprocess<GS_FP16><<<blocks, 256, 0, st>>>(s->planes, s->n, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+        k_preprocess<GS_FP16><<<blocks, kPrepThreads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam, recs,
+                                                               rects, keys, vals, dbg);
     else
-        k_preprocess<GS_BF16><<<blocks, 256, 0, st>>>(s->planes, s->n, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+        k_preprocess<GS_BF16><<<blocks, kPrepThreads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam, recs,
+                                                               rects, keys, vals, dbg);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

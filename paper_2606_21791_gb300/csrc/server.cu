@@ -73,7 +73,8 @@ uint64_t scene_resident_bytes(const gs_scene* s) {
     if (s->pbox_lo) b += 2ull * s->n * s->nbox_words * word_bytes(s->fmt);
     for (const auto& v : s->views)
         b += s->n * (sizeof(BlendRec) + 8) + v.npairs * 8 + (uint64_t)v.cam.tiles_x * v.cam.tiles_y * 8 +
-             (uint64_t)v.cam.W * v.cam.H * 16 + v.ck_total * 4096 + (uint64_t)v.cam.tiles_x * v.cam.tiles_y * 12;
+             (uint64_t)v.cam.W * v.cam.H * 16 + v.ck_total * 16ull * (uint64_t)(v.cam.tile_w * v.cam.tile_h) +
+             (uint64_t)v.cam.tiles_x * v.cam.tiles_y * 12;
     b += render_scratch_bytes(s->work.n, s->work.cap_pairs, s->work.ntiles_cap);
     return b;
 }
@@ -115,7 +116,7 @@ uint64_t request_need(gs_server* sv, const Req* q) {
     const gs_request& r = q->r;
     if (r.kind == GS_REQ_CAMPAIGN) return 0;   // runs in the scene's own (resident) buffers
     const gs_scene* s = sv->scenes[r.scene].s;
-    DevCamera cam = make_dev_camera(r.cam);
+    DevCamera cam = make_dev_camera(r.cam, s->tile_w, s->tile_h);
     int ntiles = cam.tiles_x * cam.tiles_y;
     return render_scratch_bytes(s->n, std::max<uint64_t>(8 * s->n, 1024), ntiles);
 }
@@ -145,11 +146,11 @@ gs_status execute(gs_scene* s, Slot& sl, Req* q) {
         if (r.dev_clamps)
             GS_CUDA(cudaMemcpyAsync(r.dev_clamps, sl.clamps, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
     }
-    DevCamera cam = make_dev_camera(r.cam);
+    DevCamera cam = make_dev_camera(r.cam, s->tile_w, s->tile_h);
     uint32_t* ids = nullptr;
     uint64_t np = 0;
     GS_TRY(render_lists_sized_ext(s, sl.work, cam, &ids, &np, st));
-    if (r.dev_rgb) GS_TRY(launch_blend_image(sl.work.recs, ids, sl.work.ranges, cam.W, cam.H, r.dev_rgb, st));
+    if (r.dev_rgb) GS_TRY(launch_blend_image(sl.work.recs, ids, sl.work.ranges, cam, r.dev_rgb, st));
     GS_CUDA(cudaStreamSynchronize(st));
     return GS_OK;
 }

@@ -71,6 +71,9 @@ SIGNATURES = {
     "gs_read_render_ms": (_i32, [_vp, _vp, _vp]),
     "gs_read_work": (_i32, [_vp, _vp]),
     "gs_autotune": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp]),
+    "gs_set_tile": (_i32, [_vp, _i32, _i32, _vp]),
+    "gs_get_tile": (_i32, [_vp, _vp, _vp]),
+    "gs_autotune_tile": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp, _vp]),
     "gs_preprocess": (_i32, [_vp, _vp, _vp, _vp]),
     "gs_bin_tiles": (_i32, [_vp, _vp, _u64, _i32, _i32, _vp, _vp, _u64, _vp, _vp]),
     "gs_blend_lists": (_i32, [_vp, _u64, _vp, _vp, _i32, _i32, _vp, _vp]),
@@ -339,6 +342,25 @@ def gs_autotune(scene, dev_flips, count: int, guard_mode: int, word_mask: int, s
     _check(load_library().gs_autotune(scene, _ptr(dev_flips), count, guard_mode, word_mask, C.byref(b), C.byref(us),
                                       _stream(stream)), "gs_autotune")
     return b.value, us.value
+
+
+def gs_set_tile(scene, tile_w: int, tile_h: int, stream=None):
+    _check(load_library().gs_set_tile(scene, tile_w, tile_h, _stream(stream)), "gs_set_tile")
+
+
+def gs_get_tile(scene):
+    w, h = C.c_int(), C.c_int()
+    _check(load_library().gs_get_tile(scene, C.byref(w), C.byref(h)), "gs_get_tile")
+    return w.value, h.value
+
+
+def gs_autotune_tile(scene, dev_flips, count: int, guard_mode: int, word_mask: int, stream=None):
+    """Returns ((tile_w, tile_h), batch, us per variant) the scene now uses."""
+    tw, th, b = C.c_int(), C.c_int(), C.c_int()
+    us = C.c_float()
+    _check(load_library().gs_autotune_tile(scene, _ptr(dev_flips), count, guard_mode, word_mask, C.byref(tw),
+                                           C.byref(th), C.byref(b), C.byref(us), _stream(stream)), "gs_autotune_tile")
+    return (tw.value, th.value), b.value, us.value
 
 
 def gs_preprocess(scene, cam, dev_out, stream=None):

@@ -73,19 +73,20 @@ def gpu_clean_images(G, h, cams):
     return out
 
 
-def oracle_variant(scene, cam, flips, guard=-1, mask=0, box_lo=None, box_hi=None):
+def oracle_variant(scene, cam, flips, guard=-1, mask=0, box_lo=None, box_hi=None, tile=(16, 16)):
     p = O.apply_flips(scene.planes, scene.fmt, flips)
     if guard in (0, 1):
         if guard == 0 and box_lo is None:
             box_lo, box_hi = O.field_box(scene.planes, scene.fmt)
         p, _ = O.guard(p, scene.fmt, mask, guard, box_lo, box_hi)
-    return O.render_margins(p, scene.fmt, scene.sh_degree, cam)
+    return O.render_margins(p, scene.fmt, scene.sh_degree, cam, tile)
 
 
 def attribute(G, h, scene, cams, flips, g_fp, o_fp, fpv=1, guard=-1, mask=0, box_lo=None, box_hi=None,
-              views=None, nthreads=8):
+              views=None, nthreads=8, tile=(16, 16)):
     """g_fp, o_fp: footprint counts [nvar, len(views)] from the engine and the
-    oracle campaign; views: the camera indices they cover (default all).
+    oracle campaign; views: the camera indices they cover (default all); tile:
+    the render tile shape of both sides.
     Returns {"variants": pairs compared, "mismatched_pairs": ..., "pixels": ...,
     "delta": ..., "alpha": ..., "stop": ..., "unexplained": ...}; asserts that
     each side's footprint count equals its own per-pixel decisions."""
@@ -101,13 +102,13 @@ def attribute(G, h, scene, cams, flips, g_fp, o_fp, fpv=1, guard=-1, mask=0, box
     sel = [cams[k] for k in views]
     clean_g = gpu_clean_images(G, h, cams)
     with cf.ThreadPoolExecutor(max_workers=nthreads) as ex:   # the oracle's C calls release the GIL
-        clean_o = list(ex.map(lambda c: O.render_margins(scene.planes, scene.fmt, scene.sh_degree, c), sel))
+        clean_o = list(ex.map(lambda c: O.render_margins(scene.planes, scene.fmt, scene.sh_degree, c, tile), sel))
         jobs = {}
         for v in bad:
             fv = flips[v * fpv:(v + 1) * fpv]
             for j, k in enumerate(views):
                 if g_fp[v, j] != o_fp[v, j]:
-                    jobs[(v, j)] = ex.submit(oracle_variant, scene, cams[k], fv, guard, mask, box_lo, box_hi)
+                    jobs[(v, j)] = ex.submit(oracle_variant, scene, cams[k], fv, guard, mask, box_lo, box_hi, tile)
         for v in bad:
             fv = flips[v * fpv:(v + 1) * fpv]
             imgs_g = gpu_variant_images(G, h, scene, cams, fv, guard, mask)

@@ -91,6 +91,9 @@ def test_invalid_arguments_are_refused_before_the_device(lib):
         "gs_read_render_ms": (None, None, None),
         "gs_set_batch": (None, 0),
         "gs_autotune": (None, None, 0, -1, 1, None, None, None),
+        "gs_set_tile": (None, 16, 16, None),
+        "gs_get_tile": (None, None, None),
+        "gs_autotune_tile": (None, None, 0, -1, 1, None, None, None, None, None),
         "gs_preprocess": (None, None, None, None),
         "gs_bin_tiles": (None, None, 5, 1, 1, None, None, 1, None, None),
         "gs_blend_lists": (None, 0, None, None, 1, 1, None, None),

@@ -714,3 +714,120 @@ def test_campaign_edge_cases(G):
         assert (r["sse"] == 0).all()
     finally:
         G.gs_free_scene(h)
+
+
+# ---------------------------------------------------------------------------
+# render tile shapes (gs_set_tile, gs_autotune_tile)
+# ---------------------------------------------------------------------------
+TILE_SHAPES = [(8, 8), (32, 8), (16, 8)]
+
+
+@pytest.mark.parametrize("tile", TILE_SHAPES)
+def test_tile_shape_matches_oracle(G, tile):
+    """At each tile shape: the records' tile rects are the oracle's bit for bit,
+    the render agrees with the oracle's render at that shape, and a FIELD-guarded
+    campaign over two ragged views agrees in PSNR with every footprint decision
+    equal or attributed to a threshold."""
+    sc = S.make_scene(30000, 3, S.FP32, 93, layout="clusters")
+    cams = S.ring_cameras(2, 200, 120)   # ragged against every tile edge
+    flips = S.flips_stratified(59 * 32, sc.n, sc.nwords, S.FP32, 94)[::8]
+    h = _load(G, sc)
+    try:
+        G.gs_set_tile(h, *tile)
+        assert G.gs_get_tile(h) == tile
+        g = _gpu_records(G, h, cams[0], sc.n)
+        o = O.preprocess(sc.planes, S.FP32, 3, cams[0], tile)
+        vis = o["visible"] == 1
+        assert np.array_equal(g["visible"], o["visible"])
+        for f in ("x0", "y0", "x1", "y1", "radius"):
+            assert np.array_equal(g[f][vis], o[f][vis]), f
+        imgs = _render_gpu(G, h, cams)
+        for k in range(2):
+            assert _pix_agree(imgs[k], O.render(sc.planes, S.FP32, 3, cams[k], tile)) >= PIX_FRAC
+        G.gs_set_views(h, cams)
+        gr = _campaign_gpu(G, h, flips, 2, guard=0)
+        lo, hi = O.field_box(sc.planes, S.FP32)
+        orc, cl, _ = O.campaign(sc.planes, S.FP32, 3, cams, flips, guard_mode=0, word_mask=S.GUARD_WORDS_DEFAULT,
+                                box_lo=lo, box_hi=hi, tile=tile, nthreads=O.max_threads())
+        assert np.array_equal(gr["clamps"][:, 0], cl.astype(np.uint32))
+        npx = 200 * 120 * 3
+        gp = np.array([_psnr(x, npx) for x in gr["sse"].ravel()])
+        op = np.array([_psnr(x, npx) for x in orc["sse"].ravel()])
+        assert np.abs(gp - op).max() <= PSNR_TOL
+        assert np.array_equal(gr["nonfinite"] > 0, orc["nonfinite"] > 0)
+        att = FA.attribute(G, h, sc, cams, flips, gr["footprint"], orc["footprint"], guard=0,
+                           mask=S.GUARD_WORDS_DEFAULT, tile=tile)
+        print(f"footprint attribution, tiles {tile}:", att)
+        assert att["unexplained"] == 0, att
+    finally:
+        G.gs_free_scene(h)
+
+
+@pytest.mark.parametrize("tile", TILE_SHAPES)
+@pytest.mark.parametrize("guard", [-1, 1])
+def test_dirty_tile_equals_full_rerender_at_tile_shapes(G, tile, guard):
+    """The dirty-tile engine on other tile shapes: records bit-identical to full
+    re-renders of the same variants (guard off and PRIM boxes), the scene left
+    unchanged."""
+    sc = S.make_scene(30000, 3, S.FP32, 95, layout="clusters")
+    cams = S.ring_cameras(2, 328, 244)
+    flips = S.flips_stratified(59 * 32, sc.n, sc.nwords, S.FP32, 96)
+    h = _load(G, sc)
+    try:
+        if guard == 1:
+            lo, hi = S.prim_boxes(sc, 14, 97)
+            G.gs_set_prim_box(h, lo, hi, 14)
+        G.gs_set_views(h, cams)
+        G.gs_set_tile(h, *tile)   # rebuilds the views for the new tiles
+        a = _campaign_gpu(G, h, flips, 2, guard=guard)
+        b = _campaign_gpu(G, h, flips, 2, guard=guard, full=True)
+        for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+            assert np.array_equal(a[f], b[f]), f
+        assert (a["footprint"] > 0).any()
+        assert np.array_equal(_read(G, h, sc), sc.planes)
+    finally:
+        G.gs_free_scene(h)
+
+
+def test_autotune_tile_and_batch(G):
+    """gs_autotune_tile leaves the scene on one of the candidate shapes with its
+    batch; records at that shape equal a direct call; the dirty-tile SSIM is
+    refused on other shapes than 16 x 16 and works again after switching back."""
+    torch = _torch()
+    sc = S.make_scene(20000, 3, S.FP32, 98, layout="clusters")
+    cams = S.ring_cameras(2, 240, 160)
+    flips = S.flips_stratified(59 * 32, sc.n, sc.nwords, S.FP32, 99)
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        d = G.to_device(flips)
+        (tw, th), b, us = G.gs_autotune_tile(h, d, len(flips), -1, S.GUARD_WORDS_DEFAULT)
+        assert (tw, th) in [(16, 16), (8, 8), (32, 8)] and b in (8, 16, 32, 64, 128, 256, 512, 1024, 2048)
+        assert G.gs_get_tile(h) == (tw, th) and us > 0
+        a = _campaign_gpu(G, h, flips, 2)
+        full = _campaign_gpu(G, h, flips, 2, full=True)
+        for f in ("sse", "maxabs", "footprint", "nonfinite"):
+            assert np.array_equal(a[f], full[f]), f
+        G.gs_set_tile(h, 8, 8)
+        out = G.device_bytes(len(flips) * 2 * 24)
+        ss = torch.zeros(len(flips) * 2, dtype=torch.float64, device="cuda")
+        with pytest.raises(G.GsError) as e:
+            G.gs_inject_and_render_ex(h, d, len(flips), -1, S.GUARD_WORDS_DEFAULT, out, None, ss)
+        assert e.value.status == G.GS_ERR_STATE
+        G.gs_set_tile(h, 16, 16)
+        G.gs_inject_and_render_ex(h, d, len(flips), -1, S.GUARD_WORDS_DEFAULT, out, None, ss)
+        torch.cuda.synchronize()
+        # the same as a scene that never left 16 x 16 tiles, bit for bit
+        h2 = _load(G, sc)
+        try:
+            G.gs_set_views(h2, cams)
+            out2 = G.device_bytes(len(flips) * 2 * 24)
+            ss2 = torch.zeros_like(ss)
+            G.gs_inject_and_render_ex(h2, d, len(flips), -1, S.GUARD_WORDS_DEFAULT, out2, None, ss2)
+            torch.cuda.synchronize()
+            assert np.array_equal(ss.cpu().numpy(), ss2.cpu().numpy())
+            assert np.array_equal(G.from_device(out, G.RESULT_DTYPE), G.from_device(out2, G.RESULT_DTYPE))
+        finally:
+            G.gs_free_scene(h2)
+    finally:
+        G.gs_free_scene(h)
