@@ -196,17 +196,23 @@ __device__ __forceinline__ bool apply_entry(Pix& p, bool live, bool ok, float a,
     return stop_here;
 }
 
-// Walk the survivors m (bit i: entry c + i) in list order for this lane's pixel.
+// Walk the survivors m (bit i: entry c + i) in list order for this lane's two
+// pixels, which share a column (centres (pxc, pyA) and (pxc, pyB)): the x
+// offset and the exponent's terms that depend on it alone (ca dx dx, cb dx) are
+// computed once for both, each operation rounded as gauss_power rounds it, so
+// every pixel gets the bits of a one-pixel evaluation of the same entries.
+// TRACK: record, per pixel, the list index (base + entry) where it stopped.
 // steps (measurement builds only): [0] entries walked by the warp, [1] of them
 // blended by at least one lane.
 template <bool COUNT, bool TRACK, class Fetch>
-__device__ __forceinline__ void walk_survivors(unsigned m, int c, const Fetch& fetch, const PixGeo& g, Pix& p,
-                                               unsigned int& nev, uint32_t base, unsigned* steps = nullptr) {
+__device__ __forceinline__ void walk_survivors2(unsigned m, int c, const Fetch& fetch, float pxc, float pyA,
+                                                float pyB, Pix& pA, Pix& pB, unsigned int& nev, uint32_t base,
+                                                unsigned* steps) {
     if (COUNT && steps) steps[0] += __popc(m);
     while (m) {
         int e[kAlphaGroup];
-        bool v[kAlphaGroup], ok[kAlphaGroup];
-        float a[kAlphaGroup], cr[kAlphaGroup], cg[kAlphaGroup], cb[kAlphaGroup];
+        bool v[kAlphaGroup], okA[kAlphaGroup], okB[kAlphaGroup];
+        float aA[kAlphaGroup], aB[kAlphaGroup], cr[kAlphaGroup], cg[kAlphaGroup], cb[kAlphaGroup];
 #pragma unroll
         for (int k = 0; k < kAlphaGroup; k++) {
             v[k] = m != 0u;
@@ -216,7 +222,18 @@ __device__ __forceinline__ void walk_survivors(unsigned m, int c, const Fetch& f
 #pragma unroll
         for (int k = 0; k < kAlphaGroup; k++) {
             const EntryQ q = fetch(e[k]);
-            ok[k] = v[k] && !p.done && blend_alpha(q.q0.x, q.q0.y, q.q0.z, q.q0.w, q.cc, q.opac, g.pxc, g.pyc, a[k]);
+            const float dx = __fsub_rn(q.q0.x, pxc);
+            const float t1 = __fmul_rn(__fmul_rn(q.q0.z, dx), dx);
+            const float bdx = __fmul_rn(q.q0.w, dx);
+            const float dyA = __fsub_rn(q.q0.y, pyA), dyB = __fsub_rn(q.q0.y, pyB);
+            const float hA = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyA), dyA)));
+            const float hB = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyB), dyB)));
+            const float powA = __fsub_rn(hA, __fmul_rn(bdx, dyA));
+            const float powB = __fsub_rn(hB, __fmul_rn(bdx, dyB));
+            aA[k] = q.opac * ex2_approx(__fmul_rn(powA, kLog2e));
+            aB[k] = q.opac * ex2_approx(__fmul_rn(powB, kLog2e));
+            okA[k] = !(powA > 0.0f) && !(aA[k] < 1.0f / 255.0f);
+            okB[k] = !(powB > 0.0f) && !(aB[k] < 1.0f / 255.0f);
             cr[k] = q.r;
             cg[k] = q.g;
             cb[k] = q.b;
@@ -224,48 +241,87 @@ __device__ __forceinline__ void walk_survivors(unsigned m, int c, const Fetch& f
         // apply in list order with selects (no divergent branch per entry)
 #pragma unroll
         for (int k = 0; k < kAlphaGroup; k++) {
-            const bool live = v[k] && !p.done;
-            if (COUNT) nev += live ? 1u : 0u;
-            if (COUNT && steps) steps[1] += __any_sync(0xffffffffu, live && ok[k]) ? 1u : 0u;
-            const bool stop_here = apply_entry(p, live, ok[k], a[k], cr[k], cg[k], cb[k]);
-            if (TRACK) p.stop = stop_here ? base + (uint32_t)e[k] : p.stop;
+            const bool liveA = v[k] && !pA.done, liveB = v[k] && !pB.done;
+            if (COUNT) {
+                nev += (liveA ? 1u : 0u) + (liveB ? 1u : 0u);
+                if (steps) steps[1] += __any_sync(0xffffffffu, (liveA && okA[k]) || (liveB && okB[k])) ? 1u : 0u;
+            }
+            const bool sA = apply_entry(pA, liveA, okA[k], aA[k], cr[k], cg[k], cb[k]);
+            const bool sB = apply_entry(pB, liveB, okB[k], aB[k], cr[k], cg[k], cb[k]);
+            if (TRACK) {
+                pA.stop = sA ? base + (uint32_t)e[k] : pA.stop;
+                pB.stop = sB ? base + (uint32_t)e[k] : pB.stop;
+            }
         }
     }
 }
 
+// The two pixels of a lane in a full-frame tile: 8x8 block b = warp of the
+// tile, pixel A at (lane % 8, lane / 8) of the block, B four rows below; u0 and
+// u1 are their indices in the tile's natural (8x4 block) order.
+struct Pix2Geo {
+    int px, pyA, pyB, u0, u1;
+    float pxc, pycA, pycB;
+    float wx0, wx1, wy0, wy1;   // pixel-centre box of the 8x8 block
+    bool inA, inB;
+};
+
+__device__ __forceinline__ Pix2Geo pix2_geo(int tile_x, int tile_y, int tw, int th, int W, int H) {
+    const int lane = threadIdx.x & 31, b = threadIdx.x >> 5, lg = tile_lgx(tw);
+    Pix2Geo g;
+    const int bx = tile_x * tw + block_x0(b, lg), by = tile_y * th + block_y0(b, lg);
+    g.px = bx + (lane & 7);
+    g.pyA = by + (lane >> 3);
+    g.pyB = g.pyA + 4;
+    g.u0 = block_upper(b, lg) * 32 + lane;
+    g.u1 = g.u0 + (32 << lg);
+    g.pxc = (float)g.px + 0.5f;
+    g.pycA = (float)g.pyA + 0.5f;
+    g.pycB = (float)g.pyB + 0.5f;
+    g.wx0 = (float)bx + 0.5f;
+    g.wx1 = (float)bx + 7.5f;
+    g.wy0 = (float)by + 0.5f;
+    g.wy1 = (float)by + 7.5f;
+    g.inA = g.px < W && g.pyA < H;
+    g.inB = g.px < W && g.pyB < H;
+    return g;
+}
+
 // Entries [c, c + 32) of a staged batch for one warp: cull 32 boxes against the
-// warp's pixel block with one ballot, then walk the survivors in list order.
+// warp's 8x8 pixel block with one ballot, then walk the survivors in list order.
 template <bool COUNT, bool TRACK>
-__device__ __forceinline__ void blend_chunk(const float4* box, const float4* q0s, const float4* q1s, const float* qbs,
-                                            int c, int cnt, uint32_t base, const PixGeo& g, Pix& p,
-                                            unsigned int& nev) {
+__device__ __forceinline__ void blend_chunk2(const Stage& s, int c, int cnt, uint32_t base, const Pix2Geo& g, Pix& pA,
+                                             Pix& pB, unsigned int& nev) {
     const int lane = threadIdx.x & 31;
     const int j = c + lane;
     bool pass = false;
     if (j < cnt) {
-        const float4 bx = box[j];
+        const float4 bx = s.box[j];
         pass = !(bx.y < g.wx0 || bx.x > g.wx1 || bx.w < g.wy0 || bx.z > g.wy1);
     }
     const unsigned m = __ballot_sync(0xffffffffu, pass);
     auto fetch = [&](int e) {
-        const float4 q1 = q1s[e];
-        return EntryQ{q0s[e], q1.x, q1.y, q1.z, q1.w, qbs[e]};
+        const float4 q1 = s.q1[e];
+        return EntryQ{s.q0[e], q1.x, q1.y, q1.z, q1.w, s.qb[e]};
     };
-    walk_survivors<COUNT, TRACK>(m, c, fetch, g, p, nev, base);
+    walk_survivors2<COUNT, TRACK>(m, c, fetch, g.pxc, g.pycA, g.pycB, pA, pB, nev, base, nullptr);
 }
 
 template <bool COUNT, bool TRACK>
-__device__ __forceinline__ void blend_batch(const Stage& s, int cnt, uint32_t base, const PixGeo& g, Pix& p,
-                                            unsigned int& nev, const CkWrite& ckw = CkWrite{nullptr, 0u, 0u, 0u}) {
+__device__ __forceinline__ void blend_batch2(const Stage& s, int cnt, uint32_t base, const Pix2Geo& g, Pix& pA,
+                                             Pix& pB, unsigned int& nev, const CkWrite& ckw) {
     for (int c = 0; c < cnt; c += 32) {
-        if (__all_sync(0xffffffffu, p.done)) return;
+        if (__all_sync(0xffffffffu, pA.done && pB.done)) return;
         if (ckw.ck && base + (uint32_t)c > 0 && ((base + (uint32_t)c) % kCkStride) == 0) {
             // the state after entries [0, base + c) of the list
             const uint32_t j = (base + (uint32_t)c) / kCkStride;
-            if (j <= ckw.count)
-                ckw.ck[(size_t)(ckw.off + j - 1) * ckw.pix + threadIdx.x] = make_float4(p.T, p.c0, p.c1, p.c2);
+            if (j <= ckw.count) {
+                float4* row = ckw.ck + (size_t)(ckw.off + j - 1) * ckw.pix;
+                row[g.u0] = make_float4(pA.T, pA.c0, pA.c1, pA.c2);
+                row[g.u1] = make_float4(pB.T, pB.c0, pB.c1, pB.c2);
+            }
         }
-        blend_chunk<COUNT, TRACK>(s.box, s.q0, s.q1, s.qb, c, cnt, base, g, p, nev);
+        blend_chunk2<COUNT, TRACK>(s, c, cnt, base, g, pA, pB, nev);
     }
 }
 
@@ -336,67 +392,120 @@ __device__ __forceinline__ void add_work(unsigned long long* work, unsigned int 
     }
 }
 
+// Both pixels of a lane against the clean image, added to *acc for the block
+// (fixed-point squared errors: the sum does not depend on the order).
+__device__ __forceinline__ void compare_tile2(const Pix2Geo& g, float a0, float a1, float a2, float b0, float b1,
+                                              float b2, const float* clean, int W, CmpAcc* acc) {
+    __shared__ unsigned long long wsse[kBT / 32];
+    __shared__ float wmax[kBT / 32];
+    __shared__ unsigned wfoot[kBT / 32], wbad[kBT / 32];
+    PixCmp rA{0ull, 0.0f, false, false}, rB{0ull, 0.0f, false, false};
+    if (g.inA) rA = pixel_compare(a0, a1, a2, clean + ((size_t)g.pyA * W + g.px) * 3);
+    if (g.inB) rB = pixel_compare(b0, b1, b2, clean + ((size_t)g.pyB * W + g.px) * 3);
+    unsigned long long fx = rA.fx + rB.fx;
+    float m = fmaxf(rA.m, rB.m);
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    const unsigned nf = __reduce_add_sync(0xffffffffu, (rA.foot ? 1u : 0u) + (rB.foot ? 1u : 0u));
+    const unsigned nb = __reduce_add_sync(0xffffffffu, (rA.nonfin ? 1u : 0u) + (rB.nonfin ? 1u : 0u));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        wsse[warp] = fx;
+        wmax[warp] = m;
+        wfoot[warp] = nf;
+        wbad[warp] = nb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        float mm = 0.0f;
+        unsigned nfoot = 0, nbad = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            t += wsse[w];
+            mm = fmaxf(mm, wmax[w]);
+            nfoot += wfoot[w];
+            nbad += wbad[w];
+        }
+        if (t) atomicAdd(&acc->sse_fx, t);
+        if (mm > 0.0f) atomicMax(&acc->maxabs_bits, __float_as_uint(mm));
+        if (nfoot) atomicAdd(&acc->footprint, nfoot);
+        if (nbad) atomicAdd(&acc->nonfinite, nbad);
+    }
+}
+
 // MODE 0: write the image; 1: compare with the clean image; 2: write the image
 // and each pixel's stop index (0xffffffff if it never stopped), which the
 // dirty-tile kernel uses to leave pixels that stopped before a change untouched.
-// One block of tw * th threads per tw x th tile.
+// One block of tw * th / 2 threads per tw x th tile: warp b blends the tile's
+// 8x8 block b, two pixels per lane (the dirty-tile kernel's walk).
 template <int MODE, bool COUNT>
-__global__ __launch_bounds__(kBT) void k_blend_full(const BlendRec* __restrict__ recs, const uint32_t* __restrict__ ids,
-                                                   const uint2* __restrict__ ranges, int W, int H, int tiles_x,
-                                                   int tw, int th,
-                                                   float* __restrict__ img, const float* __restrict__ clean,
-                                                   CmpAcc* acc, unsigned long long* work, uint32_t* __restrict__ stop,
-                                                   uint32_t* __restrict__ tile_stop, float4* __restrict__ ck,
-                                                   const uint32_t* __restrict__ ck_off,
-                                                   const uint32_t* __restrict__ ck_cnt,
-                                                   unsigned int* __restrict__ clean_nonfin) {
+__global__ __launch_bounds__(kBT / 2) void k_blend_full(const BlendRec* __restrict__ recs,
+                                                       const uint32_t* __restrict__ ids,
+                                                       const uint2* __restrict__ ranges, int W, int H, int tiles_x,
+                                                       int tw, int th, float* __restrict__ img,
+                                                       const float* __restrict__ clean, CmpAcc* acc,
+                                                       unsigned long long* work, uint32_t* __restrict__ stop,
+                                                       uint32_t* __restrict__ tile_stop, float4* __restrict__ ck,
+                                                       const uint32_t* __restrict__ ck_off,
+                                                       const uint32_t* __restrict__ ck_cnt,
+                                                       unsigned int* __restrict__ clean_nonfin) {
     __shared__ Stage s;
     const int tile = blockIdx.x;
-    const uint32_t P = blockDim.x;   // pixels of a tile
+    const uint32_t P = (uint32_t)(tw * th);   // pixels of a tile = records staged per batch
     const CkWrite ckw{ck, ck ? ck_off[tile] : 0u, ck ? ck_cnt[tile] : 0u, P};
-    const PixGeo g = pix_geo(tile % tiles_x, tile / tiles_x, tw, th, W, H);
-    Pix p{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, 0xffffffffu};
+    const Pix2Geo g = pix2_geo(tile % tiles_x, tile / tiles_x, tw, th, W, H);
+    Pix pA{1.0f, 0.0f, 0.0f, 0.0f, !g.inA, 0xffffffffu}, pB{1.0f, 0.0f, 0.0f, 0.0f, !g.inB, 0xffffffffu};
     const uint2 rg = ranges[tile];
     unsigned int nev = 0, staged = 0;
     for (uint32_t base = rg.x; base < rg.y; base += P) {
-        int cnt = (int)min(P, rg.y - base);
-        if ((int)threadIdx.x < cnt) stage_put(s, threadIdx.x, load_rec(recs, ids[base + threadIdx.x]));
+        const int cnt = (int)min(P, rg.y - base);
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) stage_put(s, j, load_rec(recs, ids[base + j]));
         __syncthreads();
         staged += cnt;
-        blend_batch<COUNT, MODE == 2>(s, cnt, base - rg.x, g, p, nev, ckw);
+        blend_batch2<COUNT, MODE == 2>(s, cnt, base - rg.x, g, pA, pB, nev, ckw);
         // also the barrier that lets the next batch overwrite the stage
-        if (__syncthreads_count(p.done) == (int)P) break;
+        if (__syncthreads_count(pA.done && pB.done) == (int)blockDim.x) break;
     }
     if (COUNT) add_work(work, nev, staged);
-    const float v0 = __fadd_rn(p.c0, p.T), v1 = __fadd_rn(p.c1, p.T), v2 = __fadd_rn(p.c2, p.T);   // over white
+    const float a0 = __fadd_rn(pA.c0, pA.T), a1 = __fadd_rn(pA.c1, pA.T), a2 = __fadd_rn(pA.c2, pA.T);   // over white
+    const float b0 = __fadd_rn(pB.c0, pB.T), b1 = __fadd_rn(pB.c1, pB.T), b2 = __fadd_rn(pB.c2, pB.T);
     if (MODE != 1) {
-        if (g.inside) {
-            const size_t px = (size_t)g.py * W + g.px;
-            float* o = img + px * 3;
-            o[0] = v0;
-            o[1] = v1;
-            o[2] = v2;
-            if (MODE == 2) stop[px] = p.stop;
+        if (g.inA) {
+            const size_t px = (size_t)g.pyA * W + g.px;
+            img[px * 3] = a0;
+            img[px * 3 + 1] = a1;
+            img[px * 3 + 2] = a2;
+            if (MODE == 2) stop[px] = pA.stop;
+        }
+        if (g.inB) {
+            const size_t px = (size_t)g.pyB * W + g.px;
+            img[px * 3] = b0;
+            img[px * 3 + 1] = b1;
+            img[px * 3 + 2] = b2;
+            if (MODE == 2) stop[px] = pB.stop;
         }
         if (MODE == 2 && clean_nonfin) {
-            const bool bad = g.inside && !(isfinite(v0) && isfinite(v1) && isfinite(v2));
-            const int nbad = __syncthreads_count(bad);
-            if (threadIdx.x == 0 && nbad) atomicAdd(clean_nonfin, (unsigned)nbad);
+            const int bad = (g.inA && !(isfinite(a0) && isfinite(a1) && isfinite(a2)) ? 1 : 0) +
+                            (g.inB && !(isfinite(b0) && isfinite(b1) && isfinite(b2)) ? 1 : 0);
+            const unsigned wb = __reduce_add_sync(0xffffffffu, (unsigned)bad);
+            if ((threadIdx.x & 31) == 0 && wb) atomicAdd(clean_nonfin, wb);
         }
         if (MODE == 2) {
             // the tile's largest stop index: a change at or after it leaves every pixel as it is
             __shared__ uint32_t wmax[kBT / 32];
-            const uint32_t m = __reduce_max_sync(0xffffffffu, g.inside ? p.stop : 0u);
+            const uint32_t m = __reduce_max_sync(0xffffffffu, max(g.inA ? pA.stop : 0u, g.inB ? pB.stop : 0u));
             if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
             __syncthreads();
             if (threadIdx.x == 0) {
                 uint32_t t = 0;
-                for (int w = 0; w < (int)(P >> 5); w++) t = max(t, wmax[w]);
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = max(t, wmax[w]);
                 tile_stop[tile] = t;
             }
         }
     } else {
-        compare_tile(g, v0, v1, v2, clean, W, acc);
+        compare_tile2(g, a0, a1, a2, b0, b1, b2, clean, W, acc);
     }
 }
 
@@ -831,56 +940,6 @@ __device__ __forceinline__ void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// walk_survivors for two pixels per lane in the same column (pixel centres
-// (pxc, pyA) and (pxc, pyB)): the x offset and the terms of the Gaussian's
-// exponent that depend on it alone are computed once for both, each rounded as
-// gauss_power rounds it, so every pixel gets the bits of the one-pixel walk.
-template <bool COUNT, class Fetch>
-__device__ __forceinline__ void walk_survivors2(unsigned m, const Fetch& fetch, float pxc, float pyA, float pyB, Pix& pA,
-                                                Pix& pB, unsigned int& nev, unsigned* steps) {
-    if (COUNT) steps[0] += __popc(m);
-    while (m) {
-        int e[kAlphaGroup];
-        bool v[kAlphaGroup], okA[kAlphaGroup], okB[kAlphaGroup];
-        float aA[kAlphaGroup], aB[kAlphaGroup], cr[kAlphaGroup], cg[kAlphaGroup], cb[kAlphaGroup];
-#pragma unroll
-        for (int k = 0; k < kAlphaGroup; k++) {
-            v[k] = m != 0u;
-            e[k] = v[k] ? __ffs(m) - 1 : 0;
-            m &= m - 1u;
-        }
-#pragma unroll
-        for (int k = 0; k < kAlphaGroup; k++) {
-            const EntryQ q = fetch(e[k]);
-            const float dx = __fsub_rn(q.q0.x, pxc);
-            const float t1 = __fmul_rn(__fmul_rn(q.q0.z, dx), dx);
-            const float bdx = __fmul_rn(q.q0.w, dx);
-            const float dyA = __fsub_rn(q.q0.y, pyA), dyB = __fsub_rn(q.q0.y, pyB);
-            const float hA = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyA), dyA)));
-            const float hB = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyB), dyB)));
-            const float powA = __fsub_rn(hA, __fmul_rn(bdx, dyA));
-            const float powB = __fsub_rn(hB, __fmul_rn(bdx, dyB));
-            aA[k] = q.opac * ex2_approx(__fmul_rn(powA, kLog2e));
-            aB[k] = q.opac * ex2_approx(__fmul_rn(powB, kLog2e));
-            okA[k] = !(powA > 0.0f) && !(aA[k] < 1.0f / 255.0f);
-            okB[k] = !(powB > 0.0f) && !(aB[k] < 1.0f / 255.0f);
-            cr[k] = q.r;
-            cg[k] = q.g;
-            cb[k] = q.b;
-        }
-#pragma unroll
-        for (int k = 0; k < kAlphaGroup; k++) {
-            const bool liveA = v[k] && !pA.done, liveB = v[k] && !pB.done;
-            if (COUNT) {
-                nev += (liveA ? 1u : 0u) + (liveB ? 1u : 0u);
-                steps[1] += __any_sync(0xffffffffu, (liveA && okA[k]) || (liveB && okB[k])) ? 1u : 0u;
-            }
-            apply_entry(pA, liveA, okA[k], aA[k], cr[k], cg[k], cb[k]);
-            apply_entry(pB, liveB, okB[k], aB[k], cr[k], cg[k], cb[k]);
-        }
-    }
-}
-
 // One pixel's part of a block's comparison: fixed-point squared error, peak
 // difference, footprint / non-finite / clean-non-finite flags and screen cell.
 struct BlockCmp {
@@ -1046,7 +1105,7 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
                 const float4 q1 = R.q[slot][1][e], q2 = R.q[slot][2][e];
                 return EntryQ{R.q[slot][0][e], q1.x, q1.y, q2.x, q2.y, q2.z};
             };
-            walk_survivors2<COUNT>(m, fetch, pxc, pycA, pycB, pA, pB, nev, steps);
+            walk_survivors2<COUNT, false>(m, 0, fetch, pxc, pycA, pycB, pA, pB, nev, base, steps);
             if (__all_sync(0xffffffffu, pA.done && pB.done)) break;
         }
         long long c2 = COUNT ? clock64() : 0;
@@ -1172,7 +1231,7 @@ __global__ void k_offsets_to_ranges(const uint32_t* offsets, int ntiles, uint2* 
 
 gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                              float* img, cudaStream_t st) {
-    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h;
+    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h / 2;   // threads: two pixels each
     if (tx * ty == 0) return GS_OK;
     k_blend_full<0, false><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h, img,
                                                    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -1183,7 +1242,7 @@ gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const ui
 
 gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                                const float* clean, CmpAcc* acc, unsigned long long* work, cudaStream_t st) {
-    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h;
+    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h / 2;   // threads: two pixels each
     if (tx * ty == 0) return GS_OK;
     if (work)
         k_blend_full<1, true><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h,
@@ -1200,7 +1259,7 @@ gs_status launch_blend_compare(const BlendRec* recs, const uint32_t* ids, const 
 gs_status launch_blend_image_stop(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,
                                   float* img, uint32_t* stop, uint32_t* tile_stop, float4* ck, const uint32_t* ck_off,
                                   const uint32_t* ck_cnt, unsigned int* clean_nonfin, cudaStream_t st) {
-    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h;
+    const int tx = cam.tiles_x, ty = cam.tiles_y, P = cam.tile_w * cam.tile_h / 2;   // threads: two pixels each
     if (tx * ty == 0) return GS_OK;
     k_blend_full<2, false><<<tx * ty, P, 0, st>>>(recs, ids, ranges, cam.W, cam.H, tx, cam.tile_w, cam.tile_h, img,
                                                    nullptr, nullptr, nullptr, stop, tile_stop, ck, ck_off, ck_cnt,
