@@ -7,10 +7,13 @@ it stopped with the same records an uninterrupted run gives.
 
 Files of a campaign stored at `path` (a directory):
   records.npy    [n_upsets, K] gs_result records (numpy .npy, written in place)
-  progress.json  {"done", "n", "K", "fingerprint"}: the number of leading
-                 upsets whose records are on disk, and a SHA-256 of the upset
-                 list; replaced atomically after the records of each chunk are
-                 flushed, so "done" never counts a record that is not on disk.
+  progress.json  {"done", "n", "K", "fingerprint", "setup"}: the number of
+                 leading upsets whose records are on disk, a SHA-256 of the
+                 upset list, and a digest of what else the records depend on
+                 (scene, cameras, guard mode and box, word mask, tile shape:
+                 `campaign_setup`); replaced atomically after the records of
+                 each chunk are flushed, so "done" never counts a record that
+                 is not on disk.
 
 The chunk runner is the caller's: a function from a slice of the upset list to
 its records, e.g. on the batched engine
@@ -38,12 +41,33 @@ def flips_fingerprint(flips: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(flips).view(np.uint8).tobytes()).hexdigest()
 
 
-class ResumableCampaign:
-    """The records of one campaign (upset list `flips`, `K` views) at `path`:
-    created empty, or reopened where an earlier run stopped.  Reopening with a
-    different upset list or view count is refused."""
+def _digest(a) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).view(np.uint8).tobytes()).hexdigest()
 
-    def __init__(self, path: str, flips: np.ndarray, K: int):
+
+def campaign_setup(planes, fmt: int, sh_degree: int, cams, guard_mode: int, word_mask: int,
+                   box_lo=None, box_hi=None, tile=(16, 16)) -> dict:
+    """What a campaign's records depend on besides the upsets, as a small
+    JSON-able dict: the scene (format, SH degree, shape and a SHA-256 of its
+    stored words), the cameras' bytes, the guard mode and word mask, the
+    per-primitive box planes (if any) and the render tile shape."""
+    planes = np.asarray(planes)
+    return {"fmt": int(fmt), "sh_degree": int(sh_degree), "planes_shape": list(planes.shape),
+            "planes_sha256": _digest(planes), "cams_sha256": _digest(np.asarray(cams)),
+            "guard_mode": int(guard_mode), "word_mask": int(word_mask),
+            "box_sha256": None if box_lo is None else _digest(np.concatenate(
+                [np.asarray(box_lo).reshape(-1).view(np.uint8), np.asarray(box_hi).reshape(-1).view(np.uint8)])),
+            "tile": [int(tile[0]), int(tile[1])]}
+
+
+class ResumableCampaign:
+    """The records of one campaign (upset list `flips`, `K` views, and
+    `setup`, e.g. `campaign_setup(...)`) at `path`: created empty, or reopened
+    where an earlier run stopped.  Reopening with a different upset list, view
+    count or setup is refused (records of another scene, camera set, guard or
+    tile shape would be mixed in silently otherwise)."""
+
+    def __init__(self, path: str, flips: np.ndarray, K: int, setup: Optional[dict] = None):
         flips = np.ascontiguousarray(flips)
         if flips.dtype != FLIP_DTYPE or flips.ndim != 1:
             raise ValueError("flips must be a 1-D array of gs_flip records")
@@ -51,6 +75,7 @@ class ResumableCampaign:
             raise ValueError("K >= 1 views")
         self.path, self.flips, self.n, self.K = path, flips, len(flips), int(K)
         self.fingerprint = flips_fingerprint(flips)
+        self.setup = json.loads(json.dumps(setup or {}))   # as stored
         os.makedirs(path, exist_ok=True)
         self.rec_path = os.path.join(path, "records.npy")
         self.prog_path = os.path.join(path, "progress.json")
@@ -60,6 +85,8 @@ class ResumableCampaign:
             if (prog.get("fingerprint") != self.fingerprint or prog.get("n") != self.n
                     or prog.get("K") != self.K):
                 raise ValueError(f"another campaign (upset list or view count) is stored at {path}")
+            if prog.get("setup", {}) != self.setup:
+                raise ValueError(f"a campaign of another setup (scene, cameras, guard, tiles) is stored at {path}")
             self.records = np.lib.format.open_memmap(self.rec_path, mode="r+")
             if self.records.dtype != RESULT_DTYPE or self.records.shape != (self.n, self.K):
                 raise ValueError(f"records at {path} do not match the campaign")
@@ -75,7 +102,8 @@ class ResumableCampaign:
         self.records.flush()
         tmp = self.prog_path + ".tmp"
         with open(tmp, "w") as f:
-            json.dump({"done": int(done), "n": self.n, "K": self.K, "fingerprint": self.fingerprint}, f)
+            json.dump({"done": int(done), "n": self.n, "K": self.K, "fingerprint": self.fingerprint,
+                       "setup": self.setup}, f)
             f.flush()
             os.fsync(f.fileno())
         os.replace(tmp, self.prog_path)

@@ -10,7 +10,7 @@ import pytest
 
 from paper_2606_21791_gb300 import gs
 from paper_2606_21791_gb300 import synth as S
-from paper_2606_21791_gb300.campaign import ResumableCampaign, flips_fingerprint
+from paper_2606_21791_gb300.campaign import ResumableCampaign, campaign_setup, flips_fingerprint
 
 K = 3
 
@@ -53,7 +53,7 @@ def test_stopped_and_resumed_equals_uninterrupted(tmp_path):
     assert last.run(_records, 300) == len(fl)
     assert np.array_equal(np.load(str(tmp_path / "b" / "records.npy")), np.load(str(tmp_path / "a" / "records.npy")))
     prog = json.load(open(tmp_path / "b" / "progress.json"))
-    assert prog == {"done": len(fl), "n": len(fl), "K": K, "fingerprint": flips_fingerprint(fl)}
+    assert prog == {"done": len(fl), "n": len(fl), "K": K, "fingerprint": flips_fingerprint(fl), "setup": {}}
     assert not os.path.exists(tmp_path / "b" / "progress.json.tmp")
 
 
@@ -82,3 +82,26 @@ def test_bad_chunk_results_are_rejected_before_counting(tmp_path):
         c.run(_records, 0)
     with pytest.raises(ValueError):
         ResumableCampaign(str(tmp_path / "x"), np.zeros(4, dtype=np.uint64), K)
+
+
+def test_another_setup_is_refused(tmp_path):
+    """The same upsets against another scene, camera set, guard mode, word mask,
+    box or tile shape are another campaign."""
+    fl = _flips(200)
+    sc = S.make_scene(300, 0, S.FP32, 7)
+    cams = S.ring_cameras(K, 64, 48)
+    base = dict(planes=sc.planes, fmt=S.FP32, sh_degree=0, cams=cams, guard_mode=-1, word_mask=(1 << 14) - 1)
+    setup = campaign_setup(**base)
+    ResumableCampaign(str(tmp_path), fl, K, setup).run(_records, 100, max_chunks=1)
+    assert ResumableCampaign(str(tmp_path), fl, K, campaign_setup(**base)).done == 100   # same setup: resumes
+    other_planes = sc.planes.copy()
+    other_planes.view(np.uint32)[3, 5] ^= 1
+    lo = np.zeros((14, 300), np.uint32)
+    variants = [dict(base, planes=other_planes), dict(base, cams=S.ring_cameras(K, 64, 40)),
+                dict(base, guard_mode=0), dict(base, word_mask=1), dict(base, box_lo=lo, box_hi=lo),
+                dict(base, tile=(8, 8))]
+    for v in variants:
+        with pytest.raises(ValueError):
+            ResumableCampaign(str(tmp_path), fl, K, campaign_setup(**v))
+    with pytest.raises(ValueError):
+        ResumableCampaign(str(tmp_path), fl, K)   # no setup given: not this campaign either
