@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-analytics", action="store_true", help="skip the Table 2 / scaling-law campaigns")
     ap.add_argument("--batch", type=int, default=0,
                     help="variants per launch (default: the library's autotuner picks); for small profiling cases")
+    ap.add_argument("--tile", default="",
+                    help="render tile shape WxH (default: the library's autotuner picks with the batch)")
     ap.add_argument("--gaussians", type=int, default=2_000_000,
                     help="scene size (the 2M default is the benchmark; smaller only for profiling captures)")
     return ap.parse_args()
@@ -164,21 +166,40 @@ def clean_views(scene, cams):
     return imgs, time.perf_counter() - t0
 
 
-def cpu_baseline(scene, cams, flips, clean, t_clean):
-    """Times the oracle as it stands on the host cores on the benchmark workload
-    itself: one upset per core, each rendered in every view at full resolution
-    and compared with the clean views (OpenMP over upsets).  Nothing is
-    extrapolated: value = upsets / seconds."""
+def oracle_steps(scene, cams, flips, clean, steps, warmup):
+    """The oracle as it stands on the host cores, in steps: a step is one upset
+    per core rendered at full resolution in one view and compared with it
+    (OpenMP over upsets); the view rotates over the ring views from step to
+    step and the upsets walk the list.  Returns (seconds of each timed step,
+    cores); K steps cover K * cores (upset, view) pairs = K * cores / views
+    injections."""
     import oracle as O
     cores = O.max_threads()
-    nvar = cores
-    t0 = time.perf_counter()
-    O.campaign(scene.planes, scene.fmt, scene.sh_degree, cams, flips[:nvar], clean_imgs=clean, nthreads=cores)
-    t = time.perf_counter() - t0
+    nv = len(cams)
+    times = []
+    for i in range(warmup + steps):
+        sl = flips[(i * cores) % (len(flips) - cores):][:cores]
+        k = i % nv
+        t0 = time.perf_counter()
+        O.campaign(scene.planes, scene.fmt, scene.sh_degree, cams[k:k + 1], sl, clean_imgs=clean[k:k + 1],
+                   nthreads=cores)
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    return times, cores
+
+
+def cpu_baseline(scene, cams, flips, clean, t_clean):
+    """The oracle on the benchmark workload, the same steps as the reference
+    arm: one step per view (four), one upset per core each, whole 1600x1040
+    views, nothing extrapolated."""
+    nv = steps = len(cams)
+    times, cores = oracle_steps(scene, cams, flips, clean, steps, 0)
+    t = sum(times)
     W, H = int(cams[0]["width"]), int(cams[0]["height"])
-    return {"value": nvar / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nvar} upsets x all {len(cams)} views at {W}x{H}, {t:.1f} s on {cores} threads (OpenMP over "
-                      f"upsets), not extrapolated; clean views rendered untimed ({t_clean:.1f} s)"}
+    return {"value": steps * cores / nv / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nv} steps of {cores} upsets x 1 full {W}x{H} view (one step per ring view; OpenMP over "
+                      f"upsets), {t:.1f} s; value = {cores} upsets x {nv} views / {nv} / seconds, not extrapolated; "
+                      f"clean views rendered untimed ({t_clean:.1f} s)"}
 
 
 def cpu_model() -> str:
@@ -250,19 +271,10 @@ def run_reference(args):
     import oracle as O
     O.build()
     scene, cams, flips = S.scale_workload(n=args.gaussians)
-    cores = O.max_threads()
     K, Wu = args.steps, args.warmup
     nv = len(cams)
     clean, t_clean = clean_views(scene, cams)
-    times = []
-    for i in range(Wu + K):
-        sl = flips[(i * cores) % (len(flips) - cores):][:cores]
-        k = i % nv
-        t0 = time.perf_counter()
-        O.campaign(scene.planes, scene.fmt, scene.sh_degree, cams[k:k + 1], sl, clean_imgs=clean[k:k + 1],
-                   nthreads=cores)
-        if i >= Wu:
-            times.append(time.perf_counter() - t0)
+    times, cores = oracle_steps(scene, cams, flips, clean, K, Wu)
     total = sum(times)
     value = K * cores / nv / total
     W, H = int(cams[0]["width"]), int(cams[0]["height"])
@@ -316,11 +328,18 @@ def main():
     # each rank takes its own slice of the upset list (independent units, no collective)
     d_flips = G.to_device(flips, dev)
     nflips = len(flips)
+    if args.tile:
+        G.gs_set_tile(h, *(int(x) for x in args.tile.lower().split("x")))
     if args.batch > 0:
         G.gs_set_batch(h, args.batch)
         B = args.batch
         tile = G.gs_get_tile(h)
         log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; batch B={B} (set)")
+    elif args.tile:
+        tile = G.gs_get_tile(h)
+        B, us_per = G.gs_autotune(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
+        log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; tile {tile[0]}x{tile[1]} (set), autotuned batch "
+            f"B={B} ({us_per:.2f} us/variant)")
     else:
         tile, B, us_per = G.gs_autotune_tile(h, d_flips, 8192, G.GS_GUARD_OFF, mask)
         log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s; autotuned tile {tile[0]}x{tile[1]}, batch B={B} "
@@ -478,7 +497,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(scene.n, cams, nflips, world),
         "engine": {"name": ENGINE, "batch": B, "tile": f"{tile[0]}x{tile[1]}",
-                   "batch_and_tile_from": "set" if args.batch > 0 else "autotuner (tiles 16x16, 8x8, 32x8; batches 8-2048)"},
+                   "batch_and_tile_from": ("set" if args.batch > 0 else
+                                           "tile set, batch autotuned" if args.tile else
+                                           "autotuner (tiles 16x16, 8x8, 32x8; batches 8-2048)")},
         "e2e": e2e,
         # per step: injector, item scan, two plan kernels, dirty-tile blend, finalise
         "gpu_launches": 6 * args.steps,
@@ -676,7 +697,22 @@ def batching_formats(G, S, dev):
 
 def ssim_campaign(G, S, h, d_flips, nflips, K_views, dev, count=1024):
     """The campaign with the per-(variant, view) SSIM on and off (same upsets):
-    injections/s of each, and the SSIM distribution."""
+    injections/s of each, and the SSIM distribution.  The dirty-tile SSIM runs
+    on 16x16 tiles: another tuned shape is set aside for this section and put
+    back after it."""
+    tile = G.gs_get_tile(h)
+    if tile != (16, 16):
+        G.gs_set_tile(h, 16, 16)
+    try:
+        res = _ssim_campaign(G, S, h, d_flips, nflips, K_views, dev, count)
+    finally:
+        if tile != (16, 16):
+            G.gs_set_tile(h, *tile)
+    res["tiles"] = "16x16"
+    return res
+
+
+def _ssim_campaign(G, S, h, d_flips, nflips, K_views, dev, count):
     import torch
     count = min(count, nflips)
     out = G.device_bytes(count * K_views * 24, dev)
