@@ -352,7 +352,10 @@ GS_API gs_status gs_blend_lists(const gs_record* dev_recs, uint64_t n, const uin
  * others run are admitted as slots and memory free up, and run concurrently on
  * separate streams.  A request larger than the budget left after the resident
  * scenes is refused with GS_ERR_BUSY.  Device buffers in a request must stay
- * valid until gs_server_wait returns for it.  Times are host milliseconds since
+ * valid until gs_server_wait returns for it.  While a scene is registered with
+ * a running server, the caller changes it only through requests: calls that
+ * rebuild or free its state (gs_set_views, gs_set_tile, gs_autotune_tile,
+ * gs_free_scene) race with the workers and must wait until gs_server_destroy.  Times are host milliseconds since
  * the server was created; `arrival_ms` < 0 means "now".
  * ------------------------------------------------------------------------- */
 typedef struct gs_server gs_server;

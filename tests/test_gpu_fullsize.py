@@ -86,6 +86,38 @@ def test_scale_workload_step_matches_oracle(G):
         G.gs_free_scene(h)
 
 
+def test_scale_workload_at_32x8_tiles_matches_oracle(G):
+    """The benchmark workload on 32x8 tiles (a shape the tile autotuner may
+    pick): one batch of 2048 variants x 4 views; 8 sampled variants in view 1
+    against the oracle rendering with the same tiles (PSNR, non-finite flags,
+    footprints exact or attributed), and the sampled records equal full
+    re-renders bit for bit."""
+    sc, cams, flips = S.scale_workload()
+    h = G.gs_load_scene(sc.planes, sc.n, 3, S.FP32)
+    try:
+        G.gs_set_views(h, cams)
+        G.gs_set_tile(h, 32, 8)
+        G.gs_set_batch(h, 2048)
+        step = flips[4096:6144]
+        g = _records(G, h, step, 4)
+        sample = np.arange(7, 2048, 256)
+        o, _, _ = O.campaign(sc.planes, S.FP32, 3, cams[1:2], step[sample], tile=(32, 8), nthreads=O.max_threads())
+        W, H = int(cams[1]["width"]), int(cams[1]["height"])
+        npx = W * H * 3
+        dp = np.abs(_psnr(g[sample, 1]["sse"], npx) - _psnr(o[:, 0]["sse"], npx))
+        assert dp.max() <= PSNR_TOL, dp.max()
+        assert np.array_equal(g[sample, 1]["nonfinite"] > 0, o[:, 0]["nonfinite"] > 0)
+        att = FA.attribute(G, h, sc, cams, step[sample], g[sample, 1]["footprint"], o[:, 0]["footprint"],
+                           views=[1], nthreads=O.max_threads(), tile=(32, 8))
+        print("footprint attribution, 2M Gaussians view 1, 32x8 tiles:", att)
+        assert att["unexplained"] == 0, att
+        f = _records(G, h, step[sample], 4, full=True)
+        for fld in ("sse", "maxabs", "footprint", "nonfinite"):
+            assert np.array_equal(f[fld], g[sample][fld]), fld
+    finally:
+        G.gs_free_scene(h)
+
+
 @pytest.mark.parametrize("fmt,guard", [(S.FP32, -1), (S.FP16, 1), (S.BF16, -1)])
 def test_batching_workload_matches_oracle(G, fmt, guard):
     sc, cams, flips = S.batching_workload(fmt, count=50_000)
