@@ -220,6 +220,15 @@ GS_API gs_status gs_inject_and_render(gs_scene* scene, const gs_flip* dev_flips,
                                int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
 GS_API gs_status gs_inject_and_render_full(gs_scene* scene, const gs_flip* dev_flips, int B, int flips_per_variant,
                                     int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream);
+/* gs_inject_and_render with host buffers: host_flips (B*fpv gs_flip) and
+ * host_out (B*K gs_result) are caller-owned host memory (pinned memory makes
+ * the copies asynchronous DMA; pageable memory works and is slower).  The
+ * library copies the upsets into device staging it owns (grown on demand,
+ * freed with the scene), runs the campaign on `stream`, copies the records
+ * back and synchronises the stream before returning.  Same errors as
+ * gs_inject_and_render. */
+GS_API gs_status gs_inject_and_render_host(gs_scene* scene, const gs_flip* host_flips, int B, int flips_per_variant,
+                                    int guard_mode, uint64_t word_mask, gs_result* host_out, void* stream);
 /* gs_inject_and_render for single-flip variants, also reporting how a
  * sort-first partition is contaminated (Sec. 5 "Cross-node contamination in
  * distributed rendering").  The screen is an 8x8 grid of cells, cell of pixel

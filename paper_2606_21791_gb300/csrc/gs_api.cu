@@ -422,6 +422,8 @@ gs_status gs_free_scene(gs_scene* s) {
     cudaFree(s->dev_err);
     cudaFree(s->dev_clamps);
     cudaFree(s->flip_stage);
+    cudaFree(s->host_io_flips);
+    cudaFree(s->host_io_out);
     cudaFree(s->desc);
     cudaFree(s->item_off);
     cudaFree(s->acc);
@@ -789,6 +791,35 @@ gs_status inject_and_render(gs_scene* s, const gs_flip* dev_flips, int B, int gu
     return GS_OK;
 }
 }  // namespace
+
+gs_status gs_inject_and_render_host(gs_scene* s, const gs_flip* host_flips, int B, int flips_per_variant,
+                                    int guard_mode, uint64_t word_mask, gs_result* host_out, void* stream) {
+    GS_TRY(check_flip_args(s, host_flips, B, flips_per_variant, guard_mode, word_mask));
+    if (!host_out && B > 0) return set_error(GS_ERR_ARG, "host_out is NULL");
+    if (B == 0) return GS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nf = (size_t)B * flips_per_variant, nr = (size_t)B * s->K;
+    if (nf > s->host_io_flips_cap) {
+        cudaFree(s->host_io_flips);
+        s->host_io_flips = nullptr;
+        s->host_io_flips_cap = 0;
+        GS_TRY(dmalloc((void**)&s->host_io_flips, sizeof(gs_flip) * nf));
+        s->host_io_flips_cap = nf;
+    }
+    if (nr > s->host_io_out_cap) {
+        cudaFree(s->host_io_out);
+        s->host_io_out = nullptr;
+        s->host_io_out_cap = 0;
+        GS_TRY(dmalloc((void**)&s->host_io_out, sizeof(gs_result) * nr));
+        s->host_io_out_cap = nr;
+    }
+    GS_CUDA(cudaMemcpyAsync(s->host_io_flips, host_flips, sizeof(gs_flip) * nf, cudaMemcpyHostToDevice, st));
+    GS_TRY(gs_inject_and_render(s, s->host_io_flips, B, flips_per_variant, guard_mode, word_mask, s->host_io_out,
+                                stream));
+    GS_CUDA(cudaMemcpyAsync(host_out, s->host_io_out, sizeof(gs_result) * nr, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GS_OK;
+}
 
 gs_status gs_inject_and_render_full(gs_scene* s, const gs_flip* dev_flips, int B, int flips_per_variant,
                                     int guard_mode, uint64_t word_mask, gs_result* dev_out, void* stream) {

@@ -268,6 +268,9 @@ struct gs_scene {
     int cap_B = 0;
     int cap_flips = 0;
     gs_flip* flip_stage = nullptr;
+    gs_flip* host_io_flips = nullptr;       // device copies of gs_inject_and_render_host's inputs / outputs
+    gs_result* host_io_out = nullptr;
+    size_t host_io_flips_cap = 0, host_io_out_cap = 0;
     gs::DirtyDesc* desc = nullptr;
     uint32_t* item_off = nullptr;
     gs::CmpAcc* acc = nullptr;

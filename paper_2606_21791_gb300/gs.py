@@ -60,6 +60,7 @@ SIGNATURES = {
     "gs_clean_image": (_i32, [_vp, _i32, _vp, _vp]),
     "gs_inject_and_render": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_inject_and_render_full": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
+    "gs_inject_and_render_host": (_i32, [_vp, _vp, _i32, _i32, _i32, _u64, _vp, _vp]),
     "gs_inject_and_render_regions": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp]),
     "gs_inject_and_render_ex": (_i32, [_vp, _vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp]),
     "gs_ssim": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
@@ -284,6 +285,15 @@ def gs_inject_and_render_ex(scene, dev_flips, B: int, guard_mode: int, word_mask
 def gs_ssim(dev_test, dev_clean, H: int, W: int, K: int, dev_out, stream=None):
     """SSIM of K image pairs into dev_out (K float64, device)."""
     _check(load_library().gs_ssim(_ptr(dev_test), _ptr(dev_clean), H, W, K, _ptr(dev_out), _stream(stream)), "gs_ssim")
+
+
+def gs_inject_and_render_host(scene, host_flips, B: int, flips_per_variant: int, guard_mode: int, word_mask: int,
+                              host_out, stream=None):
+    """Host buffers in and out (numpy arrays or pinned torch CPU tensors);
+    returns after the records are in host_out."""
+    _check(load_library().gs_inject_and_render_host(scene, _ptr(host_flips), B, flips_per_variant, guard_mode,
+                                                    word_mask, _ptr(host_out), _stream(stream)),
+           "gs_inject_and_render_host")
 
 
 def gs_inject_and_render_full(scene, dev_flips, B: int, flips_per_variant: int, guard_mode: int, word_mask: int,

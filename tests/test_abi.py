@@ -81,6 +81,7 @@ def test_invalid_arguments_are_refused_before_the_device(lib):
         "gs_set_views": (None, None, 1, None),
         "gs_inject_and_render": (None, None, 1, 1, -1, 1, None, None),
         "gs_inject_and_render_full": (None, None, 1, 1, -1, 1, None, None),
+        "gs_inject_and_render_host": (None, None, 1, 1, -1, 1, None, None),
         "gs_inject_and_render_regions": (None, None, 1, -1, 1, None, None, None),
         "gs_inject_and_render_ex": (None, None, 1, -1, 1, None, None, None, None),
         "gs_set_graphs": (None, 1),

@@ -831,3 +831,28 @@ def test_autotune_tile_and_batch(G):
             G.gs_free_scene(h2)
     finally:
         G.gs_free_scene(h)
+
+
+def test_host_buffer_entry_point_equals_device_one(G):
+    """gs_inject_and_render_host (host upsets in, host records out, the copies
+    inside the call) gives the records of gs_inject_and_render, for single-flip
+    variants (dirty-tile engine) and multi-flip variants (full re-renders),
+    from pageable numpy buffers."""
+    sc = S.make_scene(20000, 3, S.FP32, 101, layout="clusters")
+    cams = S.ring_cameras(2, 200, 152)
+    flips = S.flips_stratified(59 * 32, sc.n, sc.nwords, S.FP32, 102)[:600]
+    h = _load(G, sc)
+    try:
+        G.gs_set_views(h, cams)
+        for fpv in (1, 3):
+            nvar = len(flips) // fpv
+            dev = _campaign_gpu(G, h, flips[:nvar * fpv], 2, fpv=fpv)
+            host = np.zeros(nvar * 2, dtype=G.RESULT_DTYPE)
+            G.gs_inject_and_render_host(h, np.ascontiguousarray(flips[:nvar * fpv]), nvar, fpv, -1,
+                                        S.GUARD_WORDS_DEFAULT, host)
+            host = host.reshape(nvar, 2)
+            for f in ("sse", "maxabs", "footprint", "nonfinite", "clamps"):
+                assert np.array_equal(host[f], dev[f]), (fpv, f)
+        G.gs_inject_and_render_host(h, None, 0, 1, -1, S.GUARD_WORDS_DEFAULT, None)   # B = 0: nothing to do
+    finally:
+        G.gs_free_scene(h)
