@@ -481,6 +481,10 @@ def main():
                                     "warp_steps": work["warp_steps"] / args.steps,
                                     "warp_steps_blending": work["warp_steps_blending"] / args.steps,
                                     "warp_cycle_share": phase_shares(work),
+                                    # of a walk step's 64 pixel slots: those the plan left active, and
+                                    # those still blending (active and not yet stopped)
+                                    "slots_active_per_step": work["active_pixel_steps"] / max(work["warp_steps"], 1),
+                                    "slots_live_per_step": work["evaluations"] / max(work["warp_steps"], 1),
                                     "plan_drops": {k: work[k] / args.steps for k in
                                                    ("dropped_stop_key", "dropped_tile_reach", "dropped_no_reach",
                                                     "dropped_pixel_stop")}},

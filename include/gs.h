@@ -267,9 +267,12 @@ GS_API gs_status gs_set_graphs(gs_scene* scene, int enable);
  * least one of its pixels, [10] 8x8 pixel blocks re-blended, and the SM
  * cycles the dirty-tile blend's warps spend per phase: [11] setting up a block
  * (work queue, plan item, checkpoint, sublist searches), [12] the walk over
- * its entries, [13] the comparison with the clean image and the reductions
- * (graphs are bypassed while counting).  gs_read_work copies those 14 counts
- * into host_counts[14] and resets them (synchronises). */
+ * its entries, [13] the comparison with the clean image and the reductions,
+ * then [14] the pixels the plan left active in the re-blended blocks and [15]
+ * the same weighted by the entries each block's warp walked (so [15] / [8] is
+ * the mean number of a walk step's 64 pixel slots that hold an active pixel)
+ * (graphs are bypassed while counting).  gs_read_work copies those 16 counts
+ * into host_counts[16] and resets them (synchronises). */
 GS_API gs_status gs_count_work(gs_scene* scene, int enable);
 GS_API gs_status gs_read_work(gs_scene* scene, uint64_t* host_counts);
 /* Kernel timing for measurement: while enabled, CUDA events bracket the two
@@ -323,12 +326,12 @@ GS_API gs_status gs_autotune_tile(gs_scene* scene, const gs_flip* dev_flips, int
  * Stage entry points (for stage-isolated checks).
  * gs_preprocess: records of every primitive for one camera (dev_out: n).
  * gs_bin_tiles: per-tile lists front to back.  Input per primitive: depth
- * (float, > 0) and tile rect x0,y0,x1,y1 (int32, half open, already clipped to
- * the grid; empty = not binned).  Output: dev_offsets [tiles_x*tiles_y + 1]
- * exclusive prefix of list lengths and dev_ids [*host_total] primitive indices,
- * sorted by (tile, depth, primitive) via a stable LSD radix sort.  If the total
- * exceeds ids_cap, *host_total is set and GS_ERR_CAPACITY returned.  Blocks
- * until done.
+ * (float, > 0) and tile rect x0,y0,x1,y1 (int32, half open, clipped to the
+ * grid by the call; empty = not binned).  Output: dev_offsets [tiles_x*tiles_y +
+ * 1] exclusive prefix of list lengths and dev_ids [*host_total] primitive
+ * indices, sorted by (tile, depth, primitive) via a stable LSD radix sort.  If
+ * the total exceeds ids_cap, *host_total is set and GS_ERR_CAPACITY returned.
+ * Blocks until done.
  * gs_blend_lists: blend given records and lists into H*W*3 float32.  Both
  * work on 16 x 16 tiles (gs_preprocess uses the scene's tile shape for the
  * records' tile rects).

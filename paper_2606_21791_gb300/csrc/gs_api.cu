@@ -872,7 +872,7 @@ gs_status gs_bin_tiles(const float* dev_depth, const int32_t* dev_rects, uint64_
     int ntiles = tiles_x * tiles_y;
     RenderWork w;
     gs_status rs = alloc_render_work(w, n, std::max<uint64_t>(ids_cap, 1), ntiles);
-    if (rs == GS_OK) rs = launch_rects_to_keys(dev_depth, dev_rects, n, w.dkey[0], w.dval[0], w.rects, st);
+    if (rs == GS_OK) rs = launch_rects_to_keys(dev_depth, dev_rects, n, tiles_x, tiles_y, w.dkey[0], w.dval[0], w.rects, st);
     uint32_t* ids = nullptr;
     if (rs == GS_OK) rs = build_tile_lists(w, n, tiles_x, tiles_y, &ids, st);
     if (rs == GS_OK) rs = launch_ranges_to_offsets(w.ranges, ntiles, dev_offsets, w.total, st);
@@ -1037,7 +1037,7 @@ gs_status gs_count_work(gs_scene* s, int enable) {
 gs_status gs_read_work(gs_scene* s, uint64_t* host_counts) {
     if (!s || !host_counts) return set_error(GS_ERR_ARG, "NULL argument");
     if (!s->work_ctr) return set_error(GS_ERR_STATE, "work counting is off");
-    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 14, cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemcpy(host_counts, s->work_ctr, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost));
     GS_CUDA(cudaMemset(s->work_ctr, 0, sizeof(unsigned long long) * 16));
     return GS_OK;
 }

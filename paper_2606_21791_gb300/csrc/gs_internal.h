@@ -317,8 +317,8 @@ bool valid_camera(const gs_camera& c);
 // k_sort.cu
 gs_status alloc_render_work(RenderWork& w, uint64_t n, uint64_t cap_pairs, int ntiles);
 void free_render_work(RenderWork& w);
-gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, uint32_t* keys, uint32_t* vals,
-                               uint2* prects, cudaStream_t st);
+gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, int tiles_x, int tiles_y,
+                               uint32_t* keys, uint32_t* vals, uint2* prects, cudaStream_t st);
 
 // k_blend.cu (full-frame kernels take the view's camera for its size and tile shape)
 gs_status launch_blend_image(const BlendRec* recs, const uint32_t* ids, const uint2* ranges, const DevCamera& cam,

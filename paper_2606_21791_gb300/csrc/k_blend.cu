@@ -892,9 +892,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 // removed and the corrupted record inserted -- through a ring of kWarpRing
 // chunks of 32 entries in shared memory, filled by cp.async gathers issued
 // kWarpRing - 1 chunks ahead, so the gathers overlap the blend.  Each chunk is
-// culled against the box of the block's active pixels with one ballot and the
-// survivors are walked in list order (the same arithmetic as the full-frame
-// blend).  Active pixels resume from the clean blend's last checkpoint at or
+// culled against the box of the block's pixels that are still blending (active
+// and not stopped; recomputed per chunk) with one ballot and the survivors are
+// walked in list order (the same arithmetic as the full-frame blend).  Active pixels resume from the clean blend's last checkpoint at or
 // before the first changed position; the result is compared with the clean
 // image on the fly.  Warps are independent: no block barrier.
 constexpr int kWarpRing = 2;
@@ -1092,6 +1092,13 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
             const uint32_t base = c * 32u;
             const int cnt = (int)min(32u, Lb - base);
             staged += (uint32_t)cnt;
+            if (c > 0) {   // the box of the pixel centres still blending: a stopped pixel takes no entry
+                const bool la = !pA.done, lb = !pB.done;
+                g.wx0 = (float)__reduce_min_sync(0xffffffffu, (la || lb) ? px : 0x7fffffff) + 0.5f;
+                g.wx1 = (float)__reduce_max_sync(0xffffffffu, (la || lb) ? px : -1) + 0.5f;
+                g.wy0 = (float)__reduce_min_sync(0xffffffffu, la ? pyA : (lb ? pyB : 0x7fffffff)) + 0.5f;
+                g.wy1 = (float)__reduce_max_sync(0xffffffffu, lb ? pyB : (la ? pyA : -1)) + 0.5f;
+            }
             bool pass = false;
             if (lane < cnt) {
                 const float4 a = R.q[slot][0][lane], bb = R.q[slot][1][lane];
@@ -1182,6 +1189,9 @@ __global__ __launch_bounds__(kDirtyWarps * 32, 6) void k_dirty(const ViewPtrs* _
                 atomicAdd(&work[8], (unsigned long long)steps[0]);
                 atomicAdd(&work[9], (unsigned long long)steps[1]);
                 atomicAdd(&work[10], 1ull);
+                const unsigned npix = (unsigned)(__popc(amA) + __popc(amB));
+                atomicAdd(&work[14], (unsigned long long)npix);
+                atomicAdd(&work[15], (unsigned long long)npix * steps[0]);
             }
             t_pro += c1 - c0;
             t_walk += c2 - c1;

@@ -10,8 +10,9 @@
 // passes).  The result equals a stable sort of (tile << 32 | depth bits) keys
 // emitted in primitive order, with depth ties broken by primitive index.
 //
-// One radix pass = histogram kernel (per-block digit counts) + multi-block
-// exclusive scan over (digit, block) + scatter kernel (stable in-block ranking
+// One radix pass = histogram kernel (per-block digit counts) + column scan (one
+// block per digit: its counts over the blocks, and the digit's total) + scatter
+// kernel (the lower digits' totals added per block; stable in-block ranking
 // with warp match/ballot, block-local reorder in shared memory, coalesced
 // write-out).  Item counts may live on the device so the whole pipeline runs
 // without a host round trip.
@@ -56,11 +57,41 @@ __global__ __launch_bounds__(kRT) void k_radix_hist(const uint32_t* __restrict__
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// block d: exclusive scan of digit d's counts over the blocks (in place) and the
+// digit's total; the scatter adds the totals of the lower digits itself
+__global__ __launch_bounds__(kRT) void k_radix_colscan(uint32_t* __restrict__ hist, int nblocks,
+                                                     uint32_t* __restrict__ dtot) {
+    __shared__ uint32_t wsum[kRT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    uint32_t* col = hist + (uint64_t)blockIdx.x * nblocks;
+    const int chunk = (nblocks + kRT - 1) / kRT;
+    const int b = min(tid * chunk, nblocks), e = min(b + chunk, nblocks);
+    uint32_t s = 0;
+    for (int i = b; i < e; i++) s += col[i];
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    uint32_t run = x - s;
+    for (int w = 0; w < wid; w++) run += wsum[w];
+    for (int i = b; i < e; i++) {
+        const uint32_t v = col[i];
+        col[i] = run;
+        run += v;
+    }
+    if (tid == kRT - 1) dtot[blockIdx.x] = run;
+}
+
 template <bool VALS>
 __global__ __launch_bounds__(kRT) void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                       const unsigned long long* dcount, uint64_t scount, int shift,
-                                                      const uint32_t* __restrict__ hist, int nblocks) {
+                                                      const uint32_t* __restrict__ hist, int nblocks,
+                                                      const uint32_t* __restrict__ dtot) {
     // Stable block-local ranking with warp-private digit counters: warp w owns
     // the contiguous items [w * 32 kRI, (w + 1) * 32 kRI) of the block's tile, so
     // ordering by (digit, warp, rank inside the warp) keeps input order.
@@ -70,6 +101,7 @@ __global__ __launch_bounds__(kRT) void k_radix_scatter(const uint32_t* __restric
     __shared__ uint32_t bexcl[256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t wsum[kRT / 32];
+    __shared__ uint32_t dsum[kRT / 32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t count = item_count(dcount, scount);
@@ -125,12 +157,25 @@ __global__ __launch_bounds__(kRT) void k_radix_scatter(const uint32_t* __restric
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) wsum[warp] = x;
+        // start of digit tid in the output: the lower digits' totals
+        const uint32_t dt = dtot[tid];
+        uint32_t dx = dt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, dx, o);
+            if (lane >= o) dx += y;
+        }
+        if (lane == 31) {
+            wsum[warp] = x;
+            dsum[warp] = dx;
+        }
         __syncthreads();
-        uint32_t add = 0;
-        for (int w = 0; w < warp; w++) add += wsum[w];
+        uint32_t add = 0, dadd = 0;
+        for (int w = 0; w < warp; w++) {
+            add += wsum[w];
+            dadd += dsum[w];
+        }
         bexcl[tid] = x - tot + add;
-        gbase[tid] = hist[(uint64_t)tid * nblocks + blockIdx.x];
+        gbase[tid] = hist[(uint64_t)tid * nblocks + blockIdx.x] + dx - dt + dadd;
     }
     __syncthreads();
 #pragma unroll
@@ -381,11 +426,14 @@ __global__ void k_offsets_fixup(uint32_t* offsets, int ntiles, const unsigned lo
     }
 }
 
-__global__ void k_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, uint32_t* keys, uint32_t* vals,
-                                uint2* prect) {
+// rects clipped to the grid [0, tiles_x) x [0, tiles_y) here, so no list index
+// can leave it whatever the caller passes
+__global__ void k_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, int tiles_x, int tiles_y,
+                                uint32_t* keys, uint32_t* vals, uint2* prect) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int x0 = rects[4 * i + 0], y0 = rects[4 * i + 1], x1 = rects[4 * i + 2], y1 = rects[4 * i + 3];
+    const int x0 = min(max(rects[4 * i + 0], 0), tiles_x), y0 = min(max(rects[4 * i + 1], 0), tiles_y);
+    const int x1 = min(max(rects[4 * i + 2], 0), tiles_x), y1 = min(max(rects[4 * i + 3], 0), tiles_y);
     bool vis = x1 > x0 && y1 > y0;
     keys[i] = vis ? __float_as_uint(depth[i]) : 0xffffffffu;
     vals[i] = (uint32_t)i;
@@ -403,16 +451,12 @@ int hist_parts(uint64_t cap) { return (int)div_up((uint64_t)256 * radix_blocks(c
 gs_status radix_sort(uint32_t* k[2], uint32_t* v[2], const unsigned long long* dcount, uint64_t cap, int bits,
                      uint32_t* hist, unsigned long long* hpart, int& cur, cudaStream_t st) {
     const int nblocks = radix_blocks(cap);
-    const uint64_t hlen = (uint64_t)256 * nblocks;
-    const int nparts = hist_parts(cap);
-    unsigned long long* htot = hpart + nparts + 1;   // scratch for the partial scan's totals
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(hpart);   // 256 digit totals
     for (int shift = 0; shift < bits; shift += 8) {
         k_radix_hist<<<nblocks, kRT, 0, st>>>(k[cur], dcount, cap, shift, hist, nblocks);
-        k_scan_partials<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart);
-        k_scan_partials_top<<<1, kScanT, 0, st>>>(hpart, nparts, htot, ~0ull);
-        k_scan_apply<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart, hist);
+        k_radix_colscan<<<256, kRT, 0, st>>>(hist, nblocks, dtot);
         k_radix_scatter<true><<<nblocks, kRT, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], dcount, cap, shift,
-                                                       hist, nblocks);
+                                                       hist, nblocks, dtot);
         cur ^= 1;
     }
     GS_CUDA(cudaGetLastError());
@@ -474,7 +518,7 @@ gs_status alloc_render_work(RenderWork& w, uint64_t n, uint64_t cap_pairs, int n
         const uint64_t big = std::max<uint64_t>(w.cap_pairs, w.n);
         uint64_t hb = std::max<uint64_t>(radix_blocks(big), 1);
         GS_TRY(A((void**)&w.hist, 4 * 256 * hb));
-        GS_TRY(A((void**)&w.hpart, sizeof(unsigned long long) * (hist_parts(big) + 8)));
+        GS_TRY(A((void**)&w.hpart, sizeof(unsigned long long) * std::max(hist_parts(big) + 8, 136)));
     }
     if (grow_t) {
         cudaFree(w.ranges);
@@ -520,6 +564,7 @@ gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, 
     // depth order of the primitives
     GS_TRY(radix_sort(w.dkey, w.dval, nullptr, n, 32, w.hist, w.hpart, cur, st));
     const uint32_t* sorted_ids = w.dval[cur];
+    w.passes[0] = 4;   // 32-bit depth keys, 8 bits a pass
     // tiles per primitive in depth order, exclusive scan, pair count
     unsigned blocks = (unsigned)div_up(std::max<uint64_t>(n, 1), 256);
     k_count_tiles<<<blocks, 256, 0, st>>>(sorted_ids, w.rects, n, w.cnt);
@@ -540,7 +585,6 @@ gs_status build_tile_lists(RenderWork& w, uint64_t n, int tiles_x, int tiles_y, 
     while ((1 << tbits) < ntiles) tbits++;
     int pcur = 0;
     GS_TRY(radix_sort(w.pkey, w.pval, w.total, w.cap_pairs, tbits, w.hist, w.hpart, pcur, st));
-    w.passes[0] = 4;                  // 32-bit depth keys, 8 bits a pass
     w.passes[1] = (tbits + 7) / 8;
     GS_CUDA(cudaMemsetAsync(w.ranges, 0, sizeof(uint2) * ntiles, st));
     k_ranges<<<num_sms() * 8, 256, 0, st>>>(w.pkey[pcur], w.total, w.cap_pairs, w.ranges);
@@ -570,10 +614,10 @@ gs_status launch_ranges_to_offsets(const uint2* ranges, int ntiles, uint32_t* of
     return GS_OK;
 }
 
-gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, uint32_t* keys, uint32_t* vals,
-                               uint2* prects, cudaStream_t st) {
+gs_status launch_rects_to_keys(const float* depth, const int32_t* rects, uint64_t n, int tiles_x, int tiles_y,
+                               uint32_t* keys, uint32_t* vals, uint2* prects, cudaStream_t st) {
     if (n == 0) return GS_OK;
-    k_rects_to_keys<<<(unsigned)div_up(n, 256), 256, 0, st>>>(depth, rects, n, keys, vals, prects);
+    k_rects_to_keys<<<(unsigned)div_up(n, 256), 256, 0, st>>>(depth, rects, n, tiles_x, tiles_y, keys, vals, prects);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

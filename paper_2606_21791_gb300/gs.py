@@ -312,13 +312,13 @@ def gs_count_work(scene, enable: bool):
 
 
 def gs_read_work(scene):
-    c = np.zeros(14, dtype=np.uint64)
+    c = np.zeros(16, dtype=np.uint64)
     _check(load_library().gs_read_work(scene, _ptr(c)), "gs_read_work")
     return {"evaluations": int(c[0]), "tiles": int(c[1]), "entries": int(c[2]), "tiles_unchanged": int(c[3]),
             "dropped_stop_key": int(c[4]), "dropped_tile_reach": int(c[5]), "dropped_no_reach": int(c[6]),
             "dropped_pixel_stop": int(c[7]), "warp_steps": int(c[8]), "warp_steps_blending": int(c[9]),
             "blocks_blended": int(c[10]), "cycles_setup": int(c[11]), "cycles_walk": int(c[12]),
-            "cycles_compare": int(c[13])}
+            "cycles_compare": int(c[13]), "active_pixels": int(c[14]), "active_pixel_steps": int(c[15])}
 
 
 def gs_time_kernels(scene, enable: bool):

@@ -229,12 +229,19 @@ def test_preprocess_parity(G, fmt, degree, layout, n):
 # ---------------------------------------------------------------------------
 # (c) binning + radix sort: bit exact from the same per-primitive input
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("case", ["tiny", "clusters", "ties_and_giants"])
+@pytest.mark.parametrize("case", ["tiny", "clusters", "ties_and_giants", "grid_100x65", "grid_128x72"])
 def test_bin_tiles_bit_exact(G, case):
+    """Lists equal the oracle's bit for bit, from small grids to the benchmark's
+    100 x 65 tiles and a 128 x 72 grid (two pair passes over 13 and 14 tile-id
+    bits)."""
     torch = _torch()
     if case == "tiny":
         sc = S.make_scene(5000, 0, S.FP32, 57)
         cam = S.ring_cameras(1, 256, 256)[0]
+        recs = O.preprocess(sc.planes, S.FP32, 0, cam)
+    elif case in ("grid_100x65", "grid_128x72"):
+        sc = S.make_scene(60000, 0, S.FP32, 59, layout="clusters")
+        cam = S.ring_cameras(1, 1600, 1040)[0] if case == "grid_100x65" else S.ring_cameras(1, 2048, 1152)[0]
         recs = O.preprocess(sc.planes, S.FP32, 0, cam)
     else:
         sc = S.make_scene(60000, 0, S.FP32, 58, layout="clusters")
