@@ -365,8 +365,12 @@ __global__ __launch_bounds__(kPrepThreads) void k_preprocess(const void* planes,
 // primitive's words, XOR the upset in the storage format and optionally guard
 // them (Algorithm 1 applied to the only primitive that can leave its box); then
 // lane k preprocesses the corrupted primitive for view k and describes the
-// dirty tiles: the union of its clean and corrupted tile rects.  The per-view
-// comparison accumulators are zeroed here (guard clamps reported on view 0).
+// dirty tiles: the union of its clean and corrupted tile rects, each cut to the
+// tiles its record's alpha >= 1/255 box reaches.  A record changes no pixel of
+// a tile outside its box, so there it may stay in (clean record) or out of
+// (corrupted record) the tile's merged list without changing a bit.  The
+// per-view comparison accumulators are zeroed here (guard clamps reported on
+// view 0).
 // ---------------------------------------------------------------------------
 struct SharedSrc {
     const float* v;
@@ -374,6 +378,25 @@ struct SharedSrc {
 };
 
 constexpr int kPrepWarps = 8;
+
+// The tiles of a binned rect (packed x0 | y0 << 16, x1 | y1 << 16) that hold a
+// pixel centre of the record's alpha >= 1/255 box, packed the same way ((0, 0):
+// none).  An entry changes no pixel outside that box, so a tile outside it is
+// not dirty for this record.  A NaN or infinite box keeps the whole rect; the
+// pixel bounds take one pixel of slack on each side against rounding.
+__device__ __forceinline__ uint2 alpha_tiles(uint2 rect, const BlendRec& r, int tw, int th) {
+    const float ex = r.ex, ey = r.ey;
+    if (!(ex < INFINITY) || !(ey < INFINITY) || !isfinite(r.mx) || !isfinite(r.my)) return rect;   // no bound
+    if (ex < 0.0f || ey < 0.0f) return make_uint2(0u, 0u);    // -inf: alpha < 1/255 everywhere
+    const float x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
+    // tiles [floor((mx - ex - 1) / tw), floor((mx + ex) / tw)] (clamped in float before converting)
+    const float fx0 = fminf(fmaxf(floorf((r.mx - ex - 1.0f) / (float)tw), x0), x1);
+    const float fx1 = fminf(fmaxf(floorf((r.mx + ex) / (float)tw) + 1.0f, x0), x1);
+    const float fy0 = fminf(fmaxf(floorf((r.my - ey - 1.0f) / (float)th), y0), y1);
+    const float fy1 = fminf(fmaxf(floorf((r.my + ey) / (float)th) + 1.0f, y0), y1);
+    if (!(fx1 > fx0) || !(fy1 > fy0)) return make_uint2(0u, 0u);
+    return make_uint2((uint32_t)fx0 | ((uint32_t)fy0 << 16), (uint32_t)fx1 | ((uint32_t)fy1 << 16));
+}
 
 template <int FMT>
 __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
@@ -426,8 +449,14 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     d.prim = p;
     uint2 rect = make_uint2(0, 0);
     float rad = 0.0f;
-    const bool nv = ok && preprocess_core(SharedSrc{sv[wib]}, sh_degree, cams[k], d.rec, rect, rad);
-    const uint2 orect = ok ? clean_rects[k][p] : make_uint2(0, 0);
+    const bool nvb = ok && preprocess_core(SharedSrc{sv[wib]}, sh_degree, cams[k], d.rec, rect, rad);
+    const uint2 orect_b = ok ? clean_rects[k][p] : make_uint2(0, 0);   // binned rects (contamination cells)
+    const uint2 rect_b = nvb ? rect : make_uint2(0, 0);
+    // dirty tiles: the binned rects cut to the records' alpha boxes
+    if (nvb) rect = alpha_tiles(rect, d.rec, cams[k].tile_w, cams[k].tile_h);
+    const uint2 orect = orect_b.y != 0u ? alpha_tiles(orect_b, clean_recs[k][p], cams[k].tile_w, cams[k].tile_h)
+                                        : orect_b;
+    const bool nv = nvb && (rect.x & 0xffff) < (rect.y & 0xffff) && (rect.x >> 16) < (rect.y >> 16);
     const uint32_t ox0 = orect.x & 0xffff, oy0 = orect.x >> 16, ox1 = orect.y & 0xffff, oy1 = orect.y >> 16;
     const bool ov = ox1 > ox0 && oy1 > oy0;
     uint32_t nx0 = rect.x & 0xffff, ny0 = rect.x >> 16, nx1 = rect.y & 0xffff, ny1 = rect.y >> 16;
@@ -471,8 +500,8 @@ __global__ __launch_bounds__(kPrepWarps * 32) void k_inject_prep(
     // contamination prediction: the cells the primitive's tile rects meet, before
     // and after the upset, when its stored words changed
     const int tw = cams[k].tile_w, th = cams[k].tile_h;
-    z.reg_pred = changed ? rect_cells(orect, cams[k].W, cams[k].H, tw, th) |
-                               rect_cells(make_uint2(nx0 | (ny0 << 16), nx1 | (ny1 << 16)), cams[k].W, cams[k].H, tw, th)
+    z.reg_pred = changed ? rect_cells(orect_b, cams[k].W, cams[k].H, tw, th) |
+                               rect_cells(rect_b, cams[k].W, cams[k].H, tw, th)
                          : 0ull;
     acc[bk] = z;
 }
