@@ -25,6 +25,9 @@
  *   - colour = SH(dir = normalize(mean - camera centre)) + 0.5, clamped at 0 from below;
  *   - blending: skip power > 0, skip alpha < 1/255, cap alpha at 0.99, stop a
  *     pixel before the primitive that would take T below 1e-4; over white;
+ *   - the exponent power = -(ca dx^2 + cc dy^2)/2 - cb dx dy is evaluated in
+ *     fp32 as s = fma(cc dy, dy, ca dx dx), power = fma(-cb dx, dy, -s/2) (the
+ *     paper fixes the quadratic form, not its rounding order);
  *   - non-finite geometry culls; non-finite appearance propagates (no fminf/fmaxf).
  * Parity on every function in this file is pinned by tests against closed forms,
  * invariants, brute force and library routines (see tests/test_oracle_pins.py).
@@ -568,7 +571,12 @@ static void blend_pixel(const or_rec* recs, const uint32_t* list, size_t len, fl
         const or_rec* g = &recs[list[k]];
         float dx = g->mx - pxc;
         float dy = g->my - pyc;
-        float power = -0.5f * (g->ca * dx * dx + g->cc * dy * dy) - g->cb * dx * dy;
+        /* the exponent -(ca dx^2 + cc dy^2) / 2 - cb dx dy in fp32 as two fused
+         * multiply-adds, the other products rounded on their own:
+         * s = fma(cc dy, dy, ca dx dx), power = fma(-cb dx, dy, -s / 2) */
+        float t1 = (g->ca * dx) * dx;
+        float s = fmaf(g->cc * dy, dy, t1);
+        float power = fmaf(-g->cb * dx, dy, -0.5f * s);
         if (power > 0.0f) continue;
         float alpha = g->opac * expf(power);
         if (margin) {

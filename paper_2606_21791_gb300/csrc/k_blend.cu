@@ -121,16 +121,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // Exponent of the Gaussian at offset (dx, dy): -(ca dx^2 + cc dy^2)/2 - cb dx dy,
-// every operation rounded on its own in this order (no contraction), so it is
-// reproducible bit for bit by any fp32 evaluation in the same order -- which
-// matters for near-degenerate conics, where cancellation makes the rounding
-// error large compared with the value.
+// evaluated as s = fma(cc dy, dy, ca dx dx), power = fma(-cb dx, dy, -s/2): each
+// product rounded on its own, each sum fused with its product (one rounding).
+// Every evaluation here (and the oracle's) takes this order, so it is
+// reproducible bit for bit -- which matters for near-degenerate conics, where
+// cancellation makes the rounding error large compared with the value.  No
+// product feeds a separate addition, so the packed two-pixel form in the walk
+// (fp32x2 operations) computes the same bits as this scalar one.
 __device__ __forceinline__ float gauss_power(float ca, float cb, float cc, float dx, float dy) {
     const float t1 = __fmul_rn(__fmul_rn(ca, dx), dx);
-    const float t2 = __fmul_rn(__fmul_rn(cc, dy), dy);
-    const float h = __fmul_rn(-0.5f, __fadd_rn(t1, t2));
-    const float t3 = __fmul_rn(__fmul_rn(cb, dx), dy);
-    return __fsub_rn(h, t3);
+    const float s = __fmaf_rn(__fmul_rn(cc, dy), dy, t1);
+    return __fmaf_rn(__fmul_rn(-cb, dx), dy, __fmul_rn(-0.5f, s));
 }
 
 // alpha of a record at a pixel centre as the blend computes it, before the cap;
@@ -180,7 +181,9 @@ struct EntryQ {
 // capped at 0.99 (NaN kept), stop when T would drop below 1e-4, else
 // C += colour * alpha * T.  Every operation is rounded on its own, so each
 // kernel that inlines it computes the same bits.  Returns whether the pixel
-// stopped at this entry.
+// stopped at this entry.  (Packing the two pixels' steps into fp32x2
+// operations computes the same bits but costs more than it saves: the state
+// has to be packed and the updates selected per pixel.)
 __device__ __forceinline__ bool apply_entry(Pix& p, bool live, bool ok, float a, float cr, float cg, float cb) {
     const bool act = live && ok;
     const float al = a > 0.99f ? 0.99f : a;   // keeps NaN
@@ -198,9 +201,10 @@ __device__ __forceinline__ bool apply_entry(Pix& p, bool live, bool ok, float a,
 
 // Walk the survivors m (bit i: entry c + i) in list order for this lane's two
 // pixels, which share a column (centres (pxc, pyA) and (pxc, pyB)): the x
-// offset and the exponent's terms that depend on it alone (ca dx dx, cb dx) are
-// computed once for both, each operation rounded as gauss_power rounds it, so
-// every pixel gets the bits of a one-pixel evaluation of the same entries.
+// offset and the exponent's terms that depend on it alone (ca dx dx, -cb dx) are
+// computed once for both, the rest of gauss_power's order as packed fp32x2
+// operations over the two pixels, so every pixel gets the bits of a one-pixel
+// evaluation of the same entries.
 // TRACK: record, per pixel, the list index (base + entry) where it stopped.
 // steps (measurement builds only): [0] entries walked by the warp, [1] of them
 // blended by at least one lane.
@@ -209,6 +213,7 @@ __device__ __forceinline__ void walk_survivors2(unsigned m, int c, const Fetch& 
                                                 float pyB, Pix& pA, Pix& pB, unsigned int& nev, uint32_t base,
                                                 unsigned* steps) {
     if (COUNT && steps) steps[0] += __popc(m);
+    const float2 npy = make_float2(-pyA, -pyB);
     while (m) {
         int e[kAlphaGroup];
         bool v[kAlphaGroup], okA[kAlphaGroup], okB[kAlphaGroup];
@@ -224,16 +229,16 @@ __device__ __forceinline__ void walk_survivors2(unsigned m, int c, const Fetch& 
             const EntryQ q = fetch(e[k]);
             const float dx = __fsub_rn(q.q0.x, pxc);
             const float t1 = __fmul_rn(__fmul_rn(q.q0.z, dx), dx);
-            const float bdx = __fmul_rn(q.q0.w, dx);
-            const float dyA = __fsub_rn(q.q0.y, pyA), dyB = __fsub_rn(q.q0.y, pyB);
-            const float hA = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyA), dyA)));
-            const float hB = __fmul_rn(-0.5f, __fadd_rn(t1, __fmul_rn(__fmul_rn(q.cc, dyB), dyB)));
-            const float powA = __fsub_rn(hA, __fmul_rn(bdx, dyA));
-            const float powB = __fsub_rn(hB, __fmul_rn(bdx, dyB));
-            aA[k] = q.opac * ex2_approx(__fmul_rn(powA, kLog2e));
-            aB[k] = q.opac * ex2_approx(__fmul_rn(powB, kLog2e));
-            okA[k] = !(powA > 0.0f) && !(aA[k] < 1.0f / 255.0f);
-            okB[k] = !(powB > 0.0f) && !(aB[k] < 1.0f / 255.0f);
+            const float bdxn = __fmul_rn(-q.q0.w, dx);
+            const float2 dy = __fadd2_rn(make_float2(q.q0.y, q.q0.y), npy);   // my - py, one rounding each
+            const float2 sq = __ffma2_rn(__fmul2_rn(make_float2(q.cc, q.cc), dy), dy, make_float2(t1, t1));
+            const float2 pw = __ffma2_rn(make_float2(bdxn, bdxn), dy, __fmul2_rn(make_float2(-0.5f, -0.5f), sq));
+            const float2 pl = __fmul2_rn(pw, make_float2(kLog2e, kLog2e));
+            const float2 a = __fmul2_rn(make_float2(q.opac, q.opac), make_float2(ex2_approx(pl.x), ex2_approx(pl.y)));
+            aA[k] = a.x;
+            aB[k] = a.y;
+            okA[k] = !(pw.x > 0.0f) && !(a.x < 1.0f / 255.0f);
+            okB[k] = !(pw.y > 0.0f) && !(a.y < 1.0f / 255.0f);
             cr[k] = q.r;
             cg[k] = q.g;
             cb[k] = q.b;
