@@ -23,7 +23,7 @@ namespace gs {
 namespace {
 
 constexpr int kRT = 256;              // radix threads per block
-constexpr int kRI = 8;                // items per thread
+constexpr int kRI = 16;               // items per thread
 constexpr int kRTile = kRT * kRI;     // items per block
 constexpr int kScanT = 1024;
 
