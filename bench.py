@@ -51,8 +51,9 @@ def log(*a):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 2000; the reference arm: 4, each step is seconds of CPU work)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; the reference arm: 1)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-guard-stress", action="store_true", help="skip the 66M-Gaussian guard measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -66,7 +67,13 @@ def parse():
                     help="render tile shape WxH (default: the library's autotuner picks with the batch)")
     ap.add_argument("--gaussians", type=int, default=2_000_000,
                     help="scene size (the 2M default is the benchmark; smaller only for profiling captures)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    ref = args.impl == "reference"
+    if args.steps is None:
+        args.steps = 4 if ref else 2000
+    if args.warmup is None:
+        args.warmup = 1 if ref else 5
+    return args
 
 
 def dist_info():

@@ -125,7 +125,10 @@ GS_API gs_status gs_read_planes(gs_scene* scene, void* dst, int dst_on_device, v
 GS_API gs_status gs_write_planes(gs_scene* scene, const void* src, int src_on_device, void* stream);
 
 /* Read and clear the scene's sticky device error flags (bit 0: a flip site was
- * out of range and skipped).  Synchronises the device. */
+ * out of range and skipped; bit 1: a bounded wait of the full preprocess for
+ * its staged parameter words gave up, so that render's output is incomplete --
+ * the render calls that synchronise report it as GS_ERR_TIMEOUT until the
+ * flags are cleared here).  Synchronises the device. */
 GS_API gs_status gs_scene_errors(gs_scene* scene, uint32_t* host_flags);
 
 /* ---------------------------------------------------------------------------

@@ -114,7 +114,11 @@ gs_status render_lists_sized(gs_scene* s, RenderWork& w, const DevCamera& cam, u
         GS_TRY(alloc_render_work(w, s->n, cap, ntiles));
         GS_TRY(render_lists(s, w, cam, ids, st, ev));
         GS_CUDA(cudaMemcpyAsync(w.host_total, w.total, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        w.host_total[3] = 0ull;
+        GS_CUDA(cudaMemcpyAsync(&w.host_total[3], s->dev_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
         GS_CUDA(cudaStreamSynchronize(st));
+        if (w.host_total[3] & 2ull)
+            return set_error(GS_ERR_TIMEOUT, "a bounded wait of the preprocess gave up (device error word bit 1)");
         if (!w.host_total[1]) {
             *npairs = w.host_total[0];
             return GS_OK;

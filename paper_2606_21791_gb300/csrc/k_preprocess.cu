@@ -295,36 +295,10 @@ __device__ __forceinline__ bool preprocess_core(Src src, int sh_degree, const De
     return true;
 }
 
-constexpr int kPrepThreads = 128;
-
-// A primitive's words, staged in shared memory (this thread's column only).
-template <int FMT>
-struct StagedSrc {
-    const uint32_t (*sw)[kPrepThreads];
-    int t;
-    __device__ float operator()(int w) const { return decode<FMT>(sw[w][t]); }
-};
-
-// full preprocess: records, packed rects, depth-sort keys (invisible: 0xffffffff).
-// One thread per primitive.  Each thread first copies its primitive's stored
-// words into shared memory, eight loads in flight at a time (a warp reads 32
-// consecutive words of one plane per load), then computes from there: the
-// planes stream at full width instead of one dependent load per use.
-template <int FMT>
-__global__ __launch_bounds__(kPrepThreads) void k_preprocess(const void* planes, uint64_t n, int nwords,
-                                                             int sh_degree, DevCamera cam, BlendRec* recs,
-                                                             uint2* rects, uint32_t* keys, uint32_t* vals,
-                                                             gs_record* dbg) {
-    __shared__ uint32_t sw[kMaxWords][kPrepThreads];
-    const int t = threadIdx.x;
-    uint64_t i = (uint64_t)blockIdx.x * kPrepThreads + t;
-    if (i >= n) return;
-#pragma unroll 8
-    for (int w = 0; w < nwords; w++) sw[w][t] = load_bits<FMT>(planes, n, w, i);
-    BlendRec rec;
-    uint2 rect = make_uint2(0, 0);
-    float rad = 0.0f;
-    bool vis = preprocess_core(StagedSrc<FMT>{sw, t}, sh_degree, cam, rec, rect, rad);
+// The outputs of one preprocessed primitive: blend record, packed tile rect,
+// depth-sort key and value (invisible: key 0xffffffff), and the debug record.
+__device__ __forceinline__ void write_prep(uint64_t i, bool vis, BlendRec rec, uint2 rect, float rad, BlendRec* recs,
+                                           uint2* rects, uint32_t* keys, uint32_t* vals, gs_record* dbg) {
     if (!vis) {
         rec = BlendRec{0, 0, 0, 0, 0, 0, -INFINITY, -INFINITY, 0, 0, 0, 0};
         rect = make_uint2(0, 0);
@@ -357,6 +331,150 @@ __global__ __launch_bounds__(kPrepThreads) void k_preprocess(const void* planes,
             g.visible = 1;
         }
         dbg[i] = g;
+    }
+}
+
+constexpr int kPrepThreads = 128;
+
+// A primitive's words, staged in shared memory (this thread's column only).
+template <int FMT>
+struct StagedSrc {
+    const uint32_t (*sw)[kPrepThreads];
+    int t;
+    __device__ float operator()(int w) const { return decode<FMT>(sw[w][t]); }
+};
+
+// full preprocess: records, packed rects, depth-sort keys (invisible: 0xffffffff).
+// One thread per primitive.  Each thread first copies its primitive's stored
+// words into shared memory, eight loads in flight at a time (a warp reads 32
+// consecutive words of one plane per load), then computes from there: the
+// planes stream at full width instead of one dependent load per use.
+template <int FMT>
+__global__ __launch_bounds__(kPrepThreads) void k_preprocess(const void* planes, uint64_t n, int nwords,
+                                                             int sh_degree, DevCamera cam, BlendRec* recs,
+                                                             uint2* rects, uint32_t* keys, uint32_t* vals,
+                                                             gs_record* dbg) {
+    __shared__ uint32_t sw[kMaxWords][kPrepThreads];
+    const int t = threadIdx.x;
+    uint64_t i = (uint64_t)blockIdx.x * kPrepThreads + t;
+    if (i >= n) return;
+#pragma unroll 8
+    for (int w = 0; w < nwords; w++) sw[w][t] = load_bits<FMT>(planes, n, w, i);
+    BlendRec rec;
+    uint2 rect = make_uint2(0, 0);
+    float rad = 0.0f;
+    const bool vis = preprocess_core(StagedSrc<FMT>{sw, t}, sh_degree, cam, rec, rect, rad);
+    write_prep(i, vis, rec, rect, rad, recs, rects, keys, vals, dbg);
+}
+
+// ---------------------------------------------------------------------------
+// Full preprocess with the parameter planes staged by bulk copies (TMA)
+// ---------------------------------------------------------------------------
+// Persistent blocks of 128 threads walk tiles of 128 consecutive primitives.
+// For each tile one thread issues one bulk copy per parameter plane
+// (cp.async.bulk: the tile's 128 words of that plane) into one of two
+// shared-memory stages, completing on the stage's mbarrier, one tile ahead of
+// the tile being computed: a block keeps a whole tile's words (30 KB in fp32)
+// in flight while it computes the previous tile, where the per-thread kernel
+// above keeps eight loads.  A bulk copy needs 16-byte aligned addresses and a
+// size that is a multiple of 16 bytes; plane w of tile t starts at word
+// w n + 128 t, so this kernel runs when n is a multiple of 4 (fp32) or 8
+// (fp16/bf16) and the per-thread kernel otherwise.  Every wait is bounded: a
+// block whose wait gives up sets bit 1 of the scene's device error word, waits
+// (bounded again) for its copies in flight and returns.
+constexpr int kTmaStages = 2;
+constexpr unsigned kWaitLimit = 1u << 20;   // mbarrier polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    for (unsigned it = 0; it < kWaitLimit; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// a primitive's words in a stage: plane w at w * 128 words, this thread's column t
+template <int FMT>
+struct StageSrc {
+    const unsigned char* st;
+    int t;
+    __device__ float operator()(int w) const {
+        if (FMT == GS_FP32) return decode<FMT>(reinterpret_cast<const uint32_t*>(st)[w * kPrepThreads + t]);
+        return decode<FMT>(reinterpret_cast<const unsigned short*>(st)[w * kPrepThreads + t]);
+    }
+};
+
+template <int FMT>
+__global__ __launch_bounds__(kPrepThreads) void k_preprocess_tma(const void* planes, uint64_t n, int nwords,
+                                                                 int sh_degree, DevCamera cam, BlendRec* recs,
+                                                                 uint2* rects, uint32_t* keys, uint32_t* vals,
+                                                                 gs_record* dbg, unsigned int* err) {
+    extern __shared__ __align__(128) unsigned char stage_mem[];
+    __shared__ __align__(8) uint64_t bar[kTmaStages];
+    constexpr unsigned esz = FMT == GS_FP32 ? 4u : 2u;
+    const int t = threadIdx.x;
+    const size_t stage_bytes = (size_t)nwords * kPrepThreads * esz;
+    const uint64_t ntile = (n + kPrepThreads - 1) / kPrepThreads;
+    if (t == 0) {
+        for (int s = 0; s < kTmaStages; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // thread 0: the tile's planes into stage s, completing on bar[s]
+    auto issue = [&](uint64_t tile, int s) {
+        const uint64_t p0 = tile * kPrepThreads;
+        const unsigned bytes = (unsigned)min((uint64_t)kPrepThreads, n - p0) * esz;
+        unsigned char* dst = stage_mem + (size_t)s * stage_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[s])),
+                     "r"(bytes * (unsigned)nwords)
+                     : "memory");
+        for (int w = 0; w < nwords; w++) {
+            const unsigned char* src = static_cast<const unsigned char*>(planes) + ((uint64_t)w * n + p0) * esz;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(dst + (size_t)w * kPrepThreads * esz)),
+                "l"(src), "r"(bytes), "r"(smem_addr(&bar[s]))
+                : "memory");
+        }
+    };
+    uint64_t tile = blockIdx.x;
+    if (t == 0 && tile < ntile) issue(tile, 0);
+    // tile k of this block uses stage k & 1 for the (k >> 1)-th time: mbarrier phase parity (k >> 1) & 1
+    for (int k = 0; tile < ntile; tile += gridDim.x, k++) {
+        const int s = k & 1;
+        const unsigned parity = (unsigned)(k >> 1) & 1u;
+        const uint64_t next = tile + gridDim.x;
+        // stage s ^ 1 was released by the barrier that ended the previous tile
+        if (t == 0 && next < ntile) issue(next, s ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[s], parity);
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) atomicOr(err, 2u);
+            mbar_wait_bounded(&bar[s], parity);   // the block's copies in flight land first
+            if (next < ntile) mbar_wait_bounded(&bar[s ^ 1], (unsigned)((k + 1) >> 1) & 1u);
+            return;
+        }
+        const uint64_t i = tile * kPrepThreads + (uint64_t)t;
+        if (i < n) {
+            BlendRec rec;
+            uint2 rect = make_uint2(0, 0);
+            float rad = 0.0f;
+            const bool vis = preprocess_core(StageSrc<FMT>{stage_mem + (size_t)s * stage_bytes, t}, sh_degree, cam,
+                                             rec, rect, rad);
+            write_prep(i, vis, rec, rect, rad, recs, rects, keys, vals, dbg);
+        }
+        __syncthreads();   // every thread is done with stage s before it is refilled
     }
 }
 
@@ -577,21 +695,33 @@ DevCamera make_dev_camera(const gs_camera& c, int tile_w, int tile_h) {
     return d;
 }
 
+template <int FMT>
+gs_status launch_preprocess_fmt(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects,
+                                uint32_t* keys, uint32_t* vals, gs_record* dbg, cudaStream_t st) {
+    constexpr uint64_t esz = FMT == GS_FP32 ? 4 : 2;
+    if ((s->n * esz) % 16 == 0) {   // every plane of every tile starts on a 16-byte boundary
+        const int smem = (int)(kTmaStages * (uint64_t)s->nwords * kPrepThreads * esz);
+        GS_CUDA(cudaFuncSetAttribute(k_preprocess_tma<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0;
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_preprocess_tma<FMT>, kPrepThreads, smem));
+        const uint64_t ntile = div_up(s->n, kPrepThreads);
+        const unsigned blocks = (unsigned)std::min<uint64_t>(ntile, (uint64_t)std::max(per_sm, 1) * num_sms());
+        k_preprocess_tma<FMT><<<blocks, kPrepThreads, smem, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam,
+                                                                   recs, rects, keys, vals, dbg, s->dev_err);
+    } else {
+        k_preprocess<FMT><<<(unsigned)div_up(s->n, kPrepThreads), kPrepThreads, 0, st>>>(
+            s->planes, s->n, s->nwords, s->sh_degree, cam, recs, rects, keys, vals, dbg);
+    }
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
 gs_status launch_preprocess(const gs_scene* s, const DevCamera& cam, BlendRec* recs, uint2* rects, uint32_t* keys,
                             uint32_t* vals, gs_record* dbg, cudaStream_t st) {
     if (s->n == 0) return GS_OK;
-    const unsigned blocks = (unsigned)div_up(s->n, kPrepThreads);
-    if (s->fmt == GS_FP32)
-        k_preprocess<GS_FP32><<<blocks, kPrepThreads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam, recs,
-                                                               rects, keys, vals, dbg);
-    else if (s->fmt == GS_FP16)
-        k_preprocess<GS_FP16><<<blocks, kPrepThreads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam, recs,
-                                                               rects, keys, vals, dbg);
-    else
-        k_preprocess<GS_BF16><<<blocks, kPrepThreads, 0, st>>>(s->planes, s->n, s->nwords, s->sh_degree, cam, recs,
-                                                               rects, keys, vals, dbg);
-    GS_CUDA(cudaGetLastError());
-    return GS_OK;
+    if (s->fmt == GS_FP32) return launch_preprocess_fmt<GS_FP32>(s, cam, recs, rects, keys, vals, dbg, st);
+    if (s->fmt == GS_FP16) return launch_preprocess_fmt<GS_FP16>(s, cam, recs, rects, keys, vals, dbg, st);
+    return launch_preprocess_fmt<GS_BF16>(s, cam, recs, rects, keys, vals, dbg, st);
 }
 
 gs_status launch_inject_prep(const gs_scene* s, const DevCamera* dev_cams, int K, const gs_flip* flips, int B,

@@ -157,8 +157,9 @@ __global__ __launch_bounds__(kRT) void k_radix_scatter(const uint32_t* __restric
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        // start of digit tid in the output: the lower digits' totals
-        const uint32_t dt = dtot[tid];
+        // start of digit tid in the output: the lower digits' totals (none when the
+        // histogram was scanned as one table over (digit, block))
+        const uint32_t dt = dtot ? dtot[tid] : 0u;
         uint32_t dx = dt;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, dx, o);
@@ -451,10 +452,22 @@ int hist_parts(uint64_t cap) { return (int)div_up((uint64_t)256 * radix_blocks(c
 gs_status radix_sort(uint32_t* k[2], uint32_t* v[2], const unsigned long long* dcount, uint64_t cap, int bits,
                      uint32_t* hist, unsigned long long* hpart, int& cur, cudaStream_t st) {
     const int nblocks = radix_blocks(cap);
-    uint32_t* dtot = reinterpret_cast<uint32_t*>(hpart);   // 256 digit totals
+    // up to 8,192 blocks a column per digit is short enough for one block to scan;
+    // beyond, the table is scanned by all blocks (partials, their scan, apply)
+    const bool by_column = nblocks <= 8192;
+    uint32_t* dtot = by_column ? reinterpret_cast<uint32_t*>(hpart) : nullptr;   // 256 digit totals
+    const uint64_t hlen = (uint64_t)256 * nblocks;
+    const int nparts = hist_parts(cap);
+    unsigned long long* htot = hpart + nparts + 1;   // scratch for the partial scan's totals
     for (int shift = 0; shift < bits; shift += 8) {
         k_radix_hist<<<nblocks, kRT, 0, st>>>(k[cur], dcount, cap, shift, hist, nblocks);
-        k_radix_colscan<<<256, kRT, 0, st>>>(hist, nblocks, dtot);
+        if (by_column) {
+            k_radix_colscan<<<256, kRT, 0, st>>>(hist, nblocks, dtot);
+        } else {
+            k_scan_partials<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart);
+            k_scan_partials_top<<<1, kScanT, 0, st>>>(hpart, nparts, htot, ~0ull);
+            k_scan_apply<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart, hist);
+        }
         k_radix_scatter<true><<<nblocks, kRT, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], dcount, cap, shift,
                                                        hist, nblocks, dtot);
         cur ^= 1;
