@@ -33,14 +33,17 @@ __device__ __forceinline__ uint64_t item_count(const unsigned long long* dcount,
     return c < scount ? c : scount;   // scount is the capacity
 }
 
+// zero_tail: blocks past the item count write zero counts (the whole-table
+// scan reads them; the column scan stops at the last block that holds items)
 __global__ __launch_bounds__(kRT) void k_radix_hist(const uint32_t* __restrict__ keys,
                                                    const unsigned long long* dcount, uint64_t scount, int shift,
-                                                   uint32_t* __restrict__ hist, int nblocks) {
+                                                   uint32_t* __restrict__ hist, int nblocks, int zero_tail) {
     __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
     uint64_t count = item_count(dcount, scount);
     uint64_t base = (uint64_t)blockIdx.x * kRTile;
+    if (!zero_tail && base >= count) return;   // uniform over the block
+    h[threadIdx.x] = 0;
+    __syncthreads();
     // all loads first (kRI in flight per thread), then the shared counts
     uint32_t kk[kRI];
 #pragma unroll
@@ -57,15 +60,18 @@ __global__ __launch_bounds__(kRT) void k_radix_hist(const uint32_t* __restrict__
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// block d: exclusive scan of digit d's counts over the blocks (in place) and the
-// digit's total; the scatter adds the totals of the lower digits itself
+// block d: exclusive scan of digit d's counts over the blocks that hold items
+// (in place; the others hold zeros and their scatter blocks return at once) and
+// the digit's total; the scatter adds the totals of the lower digits itself
 __global__ __launch_bounds__(kRT) void k_radix_colscan(uint32_t* __restrict__ hist, int nblocks,
+                                                     const unsigned long long* dcount, uint64_t scount,
                                                      uint32_t* __restrict__ dtot) {
     __shared__ uint32_t wsum[kRT / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     uint32_t* col = hist + (uint64_t)blockIdx.x * nblocks;
-    const int chunk = (nblocks + kRT - 1) / kRT;
-    const int b = min(tid * chunk, nblocks), e = min(b + chunk, nblocks);
+    const int nb = (int)min((uint64_t)nblocks, (item_count(dcount, scount) + kRTile - 1) / kRTile);
+    const int chunk = (nb + kRT - 1) / kRT;
+    const int b = min(tid * chunk, nb), e = min(b + chunk, nb);
     uint32_t s = 0;
     for (int i = b; i < e; i++) s += col[i];
     uint32_t x = s;
@@ -452,17 +458,18 @@ int hist_parts(uint64_t cap) { return (int)div_up((uint64_t)256 * radix_blocks(c
 gs_status radix_sort(uint32_t* k[2], uint32_t* v[2], const unsigned long long* dcount, uint64_t cap, int bits,
                      uint32_t* hist, unsigned long long* hpart, int& cur, cudaStream_t st) {
     const int nblocks = radix_blocks(cap);
-    // up to 8,192 blocks a column per digit is short enough for one block to scan;
-    // beyond, the table is scanned by all blocks (partials, their scan, apply)
-    const bool by_column = nblocks <= 8192;
+    // up to 16,384 blocks a column per digit is short enough for one block to scan
+    // (only the blocks that hold items are scanned); beyond, the table is scanned
+    // by all blocks (partials, their scan, apply)
+    const bool by_column = nblocks <= 16384;
     uint32_t* dtot = by_column ? reinterpret_cast<uint32_t*>(hpart) : nullptr;   // 256 digit totals
     const uint64_t hlen = (uint64_t)256 * nblocks;
     const int nparts = hist_parts(cap);
     unsigned long long* htot = hpart + nparts + 1;   // scratch for the partial scan's totals
     for (int shift = 0; shift < bits; shift += 8) {
-        k_radix_hist<<<nblocks, kRT, 0, st>>>(k[cur], dcount, cap, shift, hist, nblocks);
+        k_radix_hist<<<nblocks, kRT, 0, st>>>(k[cur], dcount, cap, shift, hist, nblocks, by_column ? 0 : 1);
         if (by_column) {
-            k_radix_colscan<<<256, kRT, 0, st>>>(hist, nblocks, dtot);
+            k_radix_colscan<<<256, kRT, 0, st>>>(hist, nblocks, dcount, cap, dtot);
         } else {
             k_scan_partials<<<nparts, kScanBlockT, 0, st>>>(hist, hlen, hpart);
             k_scan_partials_top<<<1, kScanT, 0, st>>>(hpart, nparts, htot, ~0ull);
