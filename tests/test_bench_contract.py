@@ -41,3 +41,19 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}, "--gpus", "2", "--steps", "1", "--warmup", "1")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_default_steps_per_arm(monkeypatch):
+    """Without --steps/--warmup the GPU arm times 2,000 steps after 5 warm-up
+    steps, the reference arm (seconds of CPU work a step) 4 after 1, so a run
+    with no flags ends within minutes in both arms; given flags win."""
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert (a.steps, a.warmup) == (2000, 5)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference"])
+    a = bench.parse()
+    assert (a.steps, a.warmup) == (4, 1)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "20", "--warmup", "5"])
+    a = bench.parse()
+    assert (a.steps, a.warmup) == (20, 5)
